@@ -1,0 +1,1023 @@
+/*
+ * FP64 CPU oracle for the per-timestep 3D particle-in-cell cycle of a
+ * few-cycle laser pulse driving a dielectric (Smith et al., arXiv 2502.13695).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; the CUDA library never
+ * loads it.
+ *
+ * Plain loops in the order the step is defined, all arithmetic in double:
+ *   particle pass  : TSC gather (Sec. 4.1 "shape function"), relativistic Boris
+ *                    push, Esirkepov charge-conserving deposit, z outflow
+ *   field pass     : Yee update with a Lorentz polarisation current (Sec. 2.3,
+ *                    refraction) advanced by a Crank-Nicolson oscillator step,
+ *                    laser injected through a Silver-Mueller boundary (Sec. 3)
+ *   amplitude      : maximum of |E| over the last optical cycle (Sec. 2.1,
+ *                    rolling window)
+ *   Keldysh rate   : Sec. 2.1, Eqs. for x, W and Q, first 500 terms of Q
+ *   ionisation     : one event per molecule (Sec. 2.1), electron + hole with
+ *                    the Table 1 effective masses (Sec. 3.2)
+ * Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) supplies
+ * every random number, keyed by (seed) with counter (step, cell, slot, stream).
+ *
+ * Parity pins for every function here live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_C 299792458.0
+#define OR_EPS0 8.8541878128e-12
+#define OR_MU0 (1.0 / (OR_EPS0 * OR_C * OR_C))
+#define OR_QE 1.602176634e-19
+#define OR_ME 9.1093837015e-31
+#define OR_HBAR 1.054571817e-34
+#define OR_AMU 1.66053906660e-27
+#define OR_PI 3.14159265358979323846
+
+#define OR_MAX_LAYERS 128
+#define OR_STREAM_POS 1u
+#define OR_STREAM_VEL 2u
+#define OR_STREAM_ION 3u
+
+/* ------------------------------------------------------------------------ */
+/* Configuration (mirrors the library's inputs, declared independently)     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int z0, z1; /* layer occupies z cells [z0, z1) */
+  int ppc;    /* neutral macroparticles per cell */
+  int pad_;
+  double n_index;      /* refractive index at the laser wavelength */
+  double gap_eV;       /* band gap (Table 1) */
+  double me_star;      /* electron effective mass / m_e (Table 1) */
+  double mh_star;      /* hole effective mass / m_e (Table 1) */
+  double n_mol;        /* molecular density [m^-3] */
+  double omega0_eV;    /* Lorentz pole photon energy; INFINITY = static eps */
+  double damping;      /* Lorentz damping [rad/s] */
+  double temp_eV;      /* neutral temperature */
+  double mol_mass_amu; /* molecular mass */
+} or_layer;
+
+typedef struct {
+  int nx, ny, nz, pol;
+  double dx, dy, dz, cfl;
+  double lambda, fwhm, fluence, cep, t_peak;
+  uint64_t seed;
+  int keldysh_terms;
+  int n_layers;
+  or_layer layers[OR_MAX_LAYERS];
+} or_config;
+
+typedef struct {
+  double U_incident, U_kinetic, U_ionization, U_absorbed, frac_absorbed;
+  double U_joule, U_field, N_pairs, n_e_peak, energy_density_peak;
+  double gauss_residual_max, rho_max;
+  double n_electrons_macro, n_holes_macro, step;
+} or_diag;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10                                                             */
+/* ------------------------------------------------------------------------ */
+void or_philox(const uint32_t ctr_in[4], const uint32_t key_in[2],
+               uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+static void philox_draw(uint64_t seed, uint32_t step, uint32_t cell,
+                        uint32_t slot, uint32_t stream, uint32_t out[4]) {
+  uint32_t ctr[4] = {step, cell, slot, stream};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  or_philox(ctr, key, out);
+}
+
+static double u01(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+/* ------------------------------------------------------------------------ */
+/* Complete elliptic integrals, parameter convention (reading K1):           */
+/*   K(m) = int_0^{pi/2} (1 - m sin^2 t)^(-1/2) dt, E(m) likewise.           */
+/* Gauss arithmetic-geometric mean with the Legendre sum (DLMF 19.8.1 and     */
+/* 19.8.6): K = pi / (2 AGM(1, sqrt(1-m))), K - E = K * sum 2^(n-1) c_n^2.    */
+/* The complementary parameter mc = 1 - m is passed separately so that both   */
+/* ends of [0, 1] keep full precision.                                        */
+/* ------------------------------------------------------------------------ */
+void or_ellip_KE(double m, double mc, double *K, double *KmE) {
+  double a = 1.0, b = sqrt(mc);
+  double pw = 0.5, sum = 0.5 * m; /* n = 0 term: 2^-1 c_0^2, c_0^2 = m */
+  for (int it = 0; it < 64; it++) {
+    double an = 0.5 * (a + b);
+    double bn = sqrt(a * b);
+    double cn = 0.5 * (a - b);
+    pw *= 2.0;
+    sum += pw * cn * cn;
+    a = an;
+    b = bn;
+    if (fabs(cn) <= 1e-15 * a) break; /* later terms are below roundoff */
+  }
+  *K = OR_PI / (2.0 * a);
+  *KmE = *K * sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dawson integral  F(z) = exp(-z^2) int_0^z exp(y^2) dy  (Sec. 2.1 Phi).    */
+/*   |z| < 7   : exp(-z^2) * sum_n z^(2n+1) / (n! (2n+1)), which is the      */
+/*               term-by-term integral of exp(y^2); every term is positive,   */
+/*               summed with compensation.                                   */
+/*   |z| >= 7  : asymptotic series (1/2z) sum_k (2k-1)!! / (2 z^2)^k, cut     */
+/*               once a term is below 2^-60 of the sum, which happens before */
+/*               the smallest term (about 1e-20 relative at z = 7).          */
+/* ------------------------------------------------------------------------ */
+double or_dawson(double z) {
+  double az = fabs(z), r;
+  if (az == 0.0) return 0.0;
+  if (az < 7.0) {
+    double z2 = az * az, t = az, s = 0.0, comp = 0.0;
+    for (int n = 0; n < 2000; n++) {
+      double term = t / (2.0 * n + 1.0);
+      double y = term - comp;
+      double ts = s + y;
+      comp = (ts - s) - y;
+      s = ts;
+      if ((double)n > z2 && term < 1e-19 * s) break;
+      t *= z2 / (double)(n + 1);
+    }
+    r = s * exp(-z2);
+  } else {
+    double inv = 1.0 / (2.0 * az * az), term = 1.0, s = 1.0;
+    for (int k = 1; k < 400 && (double)k < az * az; k++) {
+      term *= (2.0 * k - 1.0) * inv;
+      s += term;
+      if (term < 0x1p-60 * s) break;
+    }
+    r = s / (2.0 * az);
+  }
+  return z < 0 ? -r : r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Keldysh photoionisation rate W [m^-3 s^-1], Sec. 2.1 (corrected form).    */
+/*   gamma = omega sqrt(m* Delta) / (e E),  gamma1 = g^2/(1+g^2),            */
+/*   gamma2 = 1/(1+g^2),                                                     */
+/*   x = (2/pi) (Delta / hbar omega) eps(gamma2) / sqrt(gamma1),             */
+/*   W = 2 (2 omega / 9 pi) (m* omega / (hbar sqrt(gamma1)))^(3/2)           */
+/*       Q(gamma, x) exp(-pi floor(x+1) (K(g1) - E(g1)) / E(g2)),            */
+/*   Q = sqrt(pi / (2 K(g2))) sum_{n>=0} exp(-n pi (K(g1)-E(g1))/E(g2))      */
+/*       Phi( sqrt( pi^2 (floor(x+1) - x + n) / (2 K(g2) E(g2)) ) ).          */
+/* The sum takes the first nterms terms (500 in Sec. 2.1).  It stops earlier  */
+/* only once the Dawson argument is past the maximum of Phi (so every later   */
+/* term is smaller) and the current term is below a quarter ulp of the sum,   */
+/* where adding it, or any later term, leaves the double sum unchanged: the    */
+/* result is bit-identical to summing all nterms terms.                       */
+/* ------------------------------------------------------------------------ */
+double or_keldysh_W(double E, double omega, double gap_J, double mstar_kg,
+                    int nterms, int *terms_used) {
+  if (terms_used) *terms_used = 0;
+  if (!(E > 0.0)) return 0.0;
+  double g = omega * sqrt(mstar_kg * gap_J) / (OR_QE * E);
+  double g2 = g * g;
+  if (!(g2 < 1e300)) return 0.0;
+  double gam1 = g2 / (1.0 + g2), gam2 = 1.0 / (1.0 + g2);
+  double K1, KmE1, K2, KmE2;
+  or_ellip_KE(gam1, gam2, &K1, &KmE1);
+  or_ellip_KE(gam2, gam1, &K2, &KmE2);
+  double E2 = K2 - KmE2;
+  double x = (2.0 / OR_PI) * (gap_J / (OR_HBAR * omega)) * E2 / sqrt(gam1);
+  double N = floor(x + 1.0);
+  double a = OR_PI * KmE1 / E2;
+  double cd = OR_PI * OR_PI / (2.0 * K2 * E2);
+  double sum = 0.0;
+  int n;
+  for (n = 0; n < nterms; n++) {
+    double arg = sqrt(cd * (N - x + (double)n));
+    double term = exp(-(double)n * a) * or_dawson(arg);
+    if (arg > 0.9241 && sum > 0.0) {
+      double ulp = nextafter(sum, INFINITY) - sum;
+      if (term < 0.25 * ulp) break;
+    }
+    sum += term;
+  }
+  if (terms_used) *terms_used = n;
+  double Q = sqrt(OR_PI / (2.0 * K2)) * sum;
+  double pref = 2.0 * (2.0 * omega / (9.0 * OR_PI)) *
+                pow(mstar_kg * omega / (OR_HBAR * sqrt(gam1)), 1.5);
+  return pref * Q * exp(-N * a);
+}
+
+/* Probability that one molecule ionises in one step (reading K5):
+ * p = 1 - exp(-(W / n_mol) dt); threshold T = floor(p 2^64), or "always"
+ * when p reaches 1 (reading K16). */
+static void ion_threshold(double W, double n_mol, double dt, uint64_t *T,
+                          uint8_t *always) {
+  double p = -expm1(-(W / n_mol) * dt);
+  if (p >= 1.0) {
+    *T = UINT64_MAX;
+    *always = 1;
+  } else {
+    *T = (uint64_t)floor(ldexp(p, 64));
+    *always = 0;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Relativistic Boris push (u = gamma v), uniform E, B at the particle.      */
+/* ------------------------------------------------------------------------ */
+void or_boris(double qm, double dt, const double E[3], const double B[3],
+              double u[3]) {
+  double h = 0.5 * qm * dt;
+  double um[3] = {u[0] + h * E[0], u[1] + h * E[1], u[2] + h * E[2]};
+  double gm = sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) /
+                             (OR_C * OR_C));
+  double t[3] = {h * B[0] / gm, h * B[1] / gm, h * B[2] / gm};
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double s[3] = {2.0 * t[0] / (1.0 + t2), 2.0 * t[1] / (1.0 + t2),
+                 2.0 * t[2] / (1.0 + t2)};
+  double up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]),
+                  um[1] + (um[2] * t[0] - um[0] * t[2]),
+                  um[2] + (um[0] * t[1] - um[1] * t[0])};
+  double upl[3] = {um[0] + (up[1] * s[2] - up[2] * s[1]),
+                   um[1] + (up[2] * s[0] - up[0] * s[2]),
+                   um[2] + (up[0] * s[1] - up[1] * s[0])};
+  u[0] = upl[0] + h * E[0];
+  u[1] = upl[1] + h * E[1];
+  u[2] = upl[2] + h * E[2];
+}
+
+/* Quadratic (TSC) weights for one axis.  'half' selects the grid of
+ * half-integer nodes.  Returns the node (relative to the particle's cell
+ * index) that carries w[0]; w[1], w[2] sit on the next two nodes. */
+static int tsc(double delta, int half, double w[3]) {
+  int base;
+  double d;
+  if (half) {
+    d = delta - 0.5;
+    base = -1;
+  } else {
+    int s = delta >= 0.5;
+    d = delta - (double)s;
+    base = s - 1;
+  }
+  w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+  w[1] = 0.75 - d * d;
+  w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+  return base;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Simulation state                                                          */
+/* ------------------------------------------------------------------------ */
+enum { FEX, FEY, FEZ, FBX, FBY, FBZ, FJX, FJY, FJZ, FPX, FPY, FPZ, FQX, FQY,
+       FQZ, NCOMP };
+/* staggering (x, y, z) of each E/B/J component: 1 = half-integer position */
+static const int stag_E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+static const int stag_B[3][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+typedef struct {
+  or_config cfg;
+  double dt, omega, alpha, E0, V;
+  int NW, nxy;
+  long nfield, nmat;
+  double *F[NCOMP];
+  int *layer_of_plane, *mplane;
+  double *win, *eamp;
+  uint64_t *T;
+  uint8_t *Talways;
+  uint32_t *alive;
+  /* per layer */
+  double deps[OR_MAX_LAYERS], kosc[OR_MAX_LAYERS], wmac[OR_MAX_LAYERS];
+  double qm[OR_MAX_LAYERS][2], mass[OR_MAX_LAYERS][2];
+  double mstar[OR_MAX_LAYERS], gapJ[OR_MAX_LAYERS], sigv[OR_MAX_LAYERS];
+  int is_static[OR_MAX_LAYERS];
+  /* charged macroparticles */
+  long np, cap;
+  uint64_t *pid;
+  int32_t *pcell;
+  double *poff, *pu;
+  uint32_t *ptag;
+  long step;
+  double U_joule, N_pairs, U_ion, n_events;
+} or_sim;
+
+static long fidx(const or_sim *s, int i, int j, int k) {
+  int nx = s->cfg.nx, ny = s->cfg.ny;
+  i %= nx;
+  if (i < 0) i += nx;
+  j %= ny;
+  if (j < 0) j += ny;
+  return ((long)k * ny + j) * nx + i;
+}
+
+static void grow(or_sim *s, long need) {
+  if (need <= s->cap) return;
+  long nc = s->cap ? s->cap : 1024;
+  while (nc < need) nc *= 2;
+  s->pid = realloc(s->pid, nc * sizeof(uint64_t));
+  s->pcell = realloc(s->pcell, nc * sizeof(int32_t));
+  s->poff = realloc(s->poff, 3 * nc * sizeof(double));
+  s->pu = realloc(s->pu, 3 * nc * sizeof(double));
+  s->ptag = realloc(s->ptag, nc * sizeof(uint32_t));
+  s->cap = nc;
+}
+
+/* Incident field at the z_min plane, Sec. 3 and reading K14: Gaussian
+ * intensity envelope of FWHM tau, E0 from the fluence F = int c eps0 E^2 dt. */
+static double e_inc(const or_sim *s, double t) {
+  double tau = s->cfg.fwhm, tt = t - s->cfg.t_peak;
+  return s->E0 * exp(-2.0 * log(2.0) * tt * tt / (tau * tau)) *
+         cos(s->omega * tt + s->cfg.cep);
+}
+
+or_sim *or_create(const or_config *cfg) {
+  const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+  if (nx < 4 || ny < 4 || nz < 8 || cfg->n_layers < 0 ||
+      cfg->n_layers > OR_MAX_LAYERS)
+    return NULL;
+  or_sim *s = calloc(1, sizeof(or_sim));
+  s->cfg = *cfg;
+  s->nxy = nx * ny;
+  s->nfield = (long)s->nxy * (nz + 1);
+  s->dt = cfg->cfl / (OR_C * sqrt(1.0 / (cfg->dx * cfg->dx) +
+                                  1.0 / (cfg->dy * cfg->dy) +
+                                  1.0 / (cfg->dz * cfg->dz)));
+  s->omega = 2.0 * OR_PI * OR_C / cfg->lambda;
+  s->alpha = OR_C * s->dt / cfg->dz;
+  s->V = cfg->dx * cfg->dy * cfg->dz;
+  s->NW = (int)ceil(cfg->lambda / (OR_C * s->dt));
+  s->E0 = sqrt(2.0 * cfg->fluence /
+               (OR_C * OR_EPS0 * cfg->fwhm * sqrt(OR_PI / (4.0 * log(2.0)))));
+  for (int c = 0; c < NCOMP; c++) s->F[c] = calloc(s->nfield, sizeof(double));
+  s->layer_of_plane = malloc(nz * sizeof(int));
+  s->mplane = malloc(nz * sizeof(int));
+  for (int k = 0; k < nz; k++) s->layer_of_plane[k] = -1;
+  for (int L = 0; L < cfg->n_layers; L++) {
+    const or_layer *ly = &cfg->layers[L];
+    if (ly->z0 < 2 || ly->z1 > nz - 2 || ly->z0 >= ly->z1 || ly->ppc < 1 ||
+        ly->ppc > 32) {
+      free(s);
+      return NULL;
+    }
+    for (int k = ly->z0; k < ly->z1; k++) s->layer_of_plane[k] = L;
+    /* Lorentz pole at the band gap with the strength that gives the stated
+     * index at the laser frequency (reading K9); static eps when the pole is
+     * at infinity (Sec. 2.3). */
+    double n2m1 = ly->n_index * ly->n_index - 1.0;
+    if (isinf(ly->omega0_eV)) {
+      s->is_static[L] = 1;
+      s->deps[L] = n2m1;
+      s->kosc[L] = INFINITY;
+    } else {
+      double w0 = ly->omega0_eV * OR_QE / OR_HBAR;
+      s->is_static[L] = 0;
+      s->deps[L] = n2m1 * (1.0 - s->omega * s->omega / (w0 * w0));
+      s->kosc[L] = w0 * w0;
+    }
+    s->wmac[L] = ly->n_mol * s->V / ly->ppc;
+    s->mass[L][0] = ly->me_star * OR_ME;
+    s->mass[L][1] = ly->mh_star * OR_ME;
+    s->qm[L][0] = -OR_QE / s->mass[L][0];
+    s->qm[L][1] = OR_QE / s->mass[L][1];
+    s->mstar[L] = OR_ME / (1.0 / ly->me_star + 1.0 / ly->mh_star);
+    s->gapJ[L] = ly->gap_eV * OR_QE;
+    s->sigv[L] = sqrt(ly->temp_eV * OR_QE / (ly->mol_mass_amu * OR_AMU));
+  }
+  int nm = 0;
+  for (int k = 0; k < nz; k++)
+    s->mplane[k] = s->layer_of_plane[k] >= 0 ? nm++ : -1;
+  s->nmat = (long)nm * s->nxy;
+  s->win = calloc((size_t)s->NW * (s->nmat ? s->nmat : 1), sizeof(double));
+  s->eamp = calloc(s->nmat ? s->nmat : 1, sizeof(double));
+  s->T = calloc(s->nmat ? s->nmat : 1, sizeof(uint64_t));
+  s->Talways = calloc(s->nmat ? s->nmat : 1, 1);
+  s->alive = calloc(s->nmat ? s->nmat : 1, sizeof(uint32_t));
+  for (int k = 0; k < nz; k++) {
+    int L = s->layer_of_plane[k];
+    if (L < 0) continue;
+    uint32_t bits = cfg->layers[L].ppc == 32
+                        ? 0xFFFFFFFFu
+                        : ((1u << cfg->layers[L].ppc) - 1u);
+    for (int q = 0; q < s->nxy; q++)
+      s->alive[(long)s->mplane[k] * s->nxy + q] = bits;
+  }
+  return s;
+}
+
+void or_destroy(or_sim *s) {
+  if (!s) return;
+  for (int c = 0; c < NCOMP; c++) free(s->F[c]);
+  free(s->layer_of_plane);
+  free(s->mplane);
+  free(s->win);
+  free(s->eamp);
+  free(s->T);
+  free(s->Talways);
+  free(s->alive);
+  free(s->pid);
+  free(s->pcell);
+  free(s->poff);
+  free(s->pu);
+  free(s->ptag);
+  free(s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Particle pass: gather, Boris, move, Esirkepov deposit, z outflow.         */
+/* ------------------------------------------------------------------------ */
+static double gather(const or_sim *s, const double *f, const int st[3], int ci,
+                     int cj, int ck, const double off[3]) {
+  double wx[3], wy[3], wz[3];
+  int bx = tsc(off[0], st[0], wx), by = tsc(off[1], st[1], wy),
+      bz = tsc(off[2], st[2], wz);
+  double acc = 0.0;
+  for (int c = 0; c < 3; c++)
+    for (int b = 0; b < 3; b++)
+      for (int a = 0; a < 3; a++)
+        acc += wx[a] * wy[b] * wz[c] *
+               f[fidx(s, ci + bx + a, cj + by + b, ck + bz + c)];
+  return acc;
+}
+
+/* Integer-node TSC shape of one axis on a 5-node frame starting at
+ * (old nearest node - 2).  shift = new nearest node - old nearest node. */
+static void frame_shape(double delta, int shift, double S[5]) {
+  double w[3];
+  tsc(delta, 0, w);
+  for (int m = 0; m < 5; m++) S[m] = 0.0;
+  S[1 + shift] = w[0];
+  S[2 + shift] = w[1];
+  S[3 + shift] = w[2];
+}
+
+static void esirkepov(or_sim *s, double qw, const int cold[3],
+                      const double dold[3], const int cnew[3],
+                      const double dnew[3]) {
+  const double dl[3] = {s->cfg.dx, s->cfg.dy, s->cfg.dz};
+  double S0[3][5], DS[3][5];
+  int base[3];
+  for (int d = 0; d < 3; d++) {
+    int n0 = cold[d] + (dold[d] >= 0.5);
+    int n1 = cnew[d] + (dnew[d] >= 0.5);
+    double S1[5];
+    frame_shape(dold[d], 0, S0[d]);
+    frame_shape(dnew[d], n1 - n0, S1);
+    for (int m = 0; m < 5; m++) DS[d][m] = S1[m] - S0[d][m];
+    base[d] = n0 - 2;
+  }
+  /* W1 = DSx (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic for W2,
+   * W3 (Esirkepov 2001); J_d accumulates -q w dl_d / (V dt) W_d along d. */
+  for (int d = 0; d < 3; d++) {
+    int e = (d + 1) % 3, f = (d + 2) % 3;
+    double pref = -qw * dl[d] / (s->V * s->dt);
+    double *J = s->F[FJX + d];
+    for (int b = 0; b < 5; b++)
+      for (int c = 0; c < 5; c++) {
+        double wtr = S0[e][b] * S0[f][c] + 0.5 * DS[e][b] * S0[f][c] +
+                     0.5 * S0[e][b] * DS[f][c] +
+                     (1.0 / 3.0) * DS[e][b] * DS[f][c];
+        double run = 0.0;
+        for (int a = 0; a < 5; a++) {
+          run += pref * DS[d][a] * wtr;
+          if (run == 0.0) continue;
+          int idx[3];
+          idx[d] = base[d] + a;
+          idx[e] = base[e] + b;
+          idx[f] = base[f] + c;
+          J[fidx(s, idx[0], idx[1], idx[2])] += run;
+        }
+      }
+  }
+}
+
+void or_particle_pass(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const double dl[3] = {s->cfg.dx, s->cfg.dy, s->cfg.dz};
+  long w = 0;
+  for (long p = 0; p < s->np; p++) {
+    int32_t cell = s->pcell[p];
+    int c[3] = {cell % nx, (cell / nx) % ny, cell / (nx * ny)};
+    double *off = &s->poff[3 * p], *u = &s->pu[3 * p];
+    uint32_t tag = s->ptag[p];
+    int L = (int)(tag >> 1), sp = (int)(tag & 1u);
+    double E[3], B[3];
+    for (int d = 0; d < 3; d++) {
+      E[d] = gather(s, s->F[FEX + d], stag_E[d], c[0], c[1], c[2], off);
+      B[d] = gather(s, s->F[FBX + d], stag_B[d], c[0], c[1], c[2], off);
+    }
+    or_boris(s->qm[L][sp], s->dt, E, B, u);
+    double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) /
+                              (OR_C * OR_C));
+    int cn[3];
+    double dn[3];
+    for (int d = 0; d < 3; d++) {
+      double nd = off[d] + s->dt * u[d] / (g * dl[d]);
+      int cc = c[d];
+      if (nd < 0.0) {
+        nd += 1.0;
+        cc -= 1;
+      }
+      if (nd >= 1.0) {
+        nd -= 1.0;
+        cc += 1;
+      }
+      cn[d] = cc;
+      dn[d] = nd;
+    }
+    double q = sp ? OR_QE : -OR_QE;
+    esirkepov(s, q * s->wmac[L], c, off, cn, dn);
+    if (cn[2] < 2 || cn[2] >= nz - 2) continue; /* outflow: deleted */
+    cn[0] = (cn[0] % nx + nx) % nx;
+    cn[1] = (cn[1] % ny + ny) % ny;
+    s->pid[w] = s->pid[p];
+    s->pcell[w] = (int32_t)(((long)cn[2] * ny + cn[1]) * nx + cn[0]);
+    for (int d = 0; d < 3; d++) {
+      s->poff[3 * w + d] = dn[d];
+      s->pu[3 * w + d] = u[d];
+    }
+    s->ptag[w] = tag;
+    w++;
+  }
+  s->np = w;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field pass: B half step, E with Lorentz polarisation and Silver-Mueller   */
+/* z faces, B half step, J cleared.                                          */
+/* ------------------------------------------------------------------------ */
+static void b_half(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const double h = 0.5 * s->dt, dx = s->cfg.dx, dy = s->cfg.dy,
+               dz = s->cfg.dz;
+  double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
+  double *Bx = s->F[FBX], *By = s->F[FBY], *Bz = s->F[FBZ];
+  for (int k = 0; k <= nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long o = fidx(s, i, j, k);
+        if (k < nz) {
+          Bx[o] -= h * ((Ez[fidx(s, i, j + 1, k)] - Ez[o]) / dy -
+                        (Ey[fidx(s, i, j, k + 1)] - Ey[o]) / dz);
+          By[o] -= h * ((Ex[fidx(s, i, j, k + 1)] - Ex[o]) / dz -
+                        (Ez[fidx(s, i + 1, j, k)] - Ez[o]) / dx);
+        }
+        Bz[o] -= h * ((Ey[fidx(s, i + 1, j, k)] - Ey[o]) / dx -
+                      (Ex[fidx(s, i, j + 1, k)] - Ex[o]) / dy);
+      }
+}
+
+/* One E point: a = dt (c^2 curl B - J / eps0) is the vacuum increment.  In a
+ * Lorentz cell the oscillator P'' + G P' + w0^2 P = w0^2 eps0 deps E is
+ * advanced by the trapezoidal (Crank-Nicolson) rule, coupled implicitly to
+ * E^{n+1} (the explicit leapfrog form is unstable at CFL 0.95 for a 9 eV pole
+ * at 25 nm cells).  p = P/eps0 and q = (dP/dt)/eps0 at integer times; the
+ * polarisation current of Ampere's law is eps0 (p1 - p0)/dt. */
+static double e_point(const or_sim *s, int L, double E0v, double a, double *p,
+                      double *q) {
+  if (L < 0) return E0v + a;
+  double de = s->deps[L];
+  double dp;
+  if (s->is_static[L]) {
+    dp = (2.0 * (de * E0v - *p) + de * a) / (1.0 + de);
+    *p += dp;
+    *q = 0.0;
+  } else {
+    double h = s->dt, k = s->kosc[L], g = s->cfg.layers[L].damping;
+    double num = h * (*q) + 0.5 * h * h * k * (de * E0v - *p) +
+                 0.25 * h * h * k * de * a;
+    double den = 1.0 + 0.25 * h * h * k * (1.0 + de) + 0.5 * g * h;
+    dp = num / den;
+    *q = 2.0 * dp / h - *q;
+    *p += dp;
+  }
+  return E0v + a - dp;
+}
+
+static void e_full(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const double dt = s->dt, c2 = OR_C * OR_C, dx = s->cfg.dx, dy = s->cfg.dy,
+               dz = s->cfg.dz, al = s->alpha;
+  double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
+  double *Bx = s->F[FBX], *By = s->F[FBY], *Bz = s->F[FBZ];
+  double *Jx = s->F[FJX], *Jy = s->F[FJY], *Jz = s->F[FJZ];
+  double einc = e_inc(s, (s->step + 0.5) * dt);
+  double exi = s->cfg.pol == 0 ? einc : 0.0, eyi = s->cfg.pol == 0 ? 0.0 : einc;
+  double joule = 0.0;
+  for (int k = 0; k <= nz; k++) {
+    int L = k < nz ? s->layer_of_plane[k] : -1;
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long o = fidx(s, i, j, k);
+        double dBz_dy = (Bz[o] - Bz[fidx(s, i, j - 1, k)]) / dy;
+        double dBz_dx = (Bz[o] - Bz[fidx(s, i - 1, j, k)]) / dx;
+        double ex0 = Ex[o], ey0 = Ey[o], ex1, ey1;
+        if (k == 0) {
+          ex1 = ((1.0 - al) * ex0 - 2.0 * al * OR_C * By[o] + 4.0 * al * exi +
+                 dt * (c2 * dBz_dy - Jx[o] / OR_EPS0)) /
+                (1.0 + al);
+          ey1 = ((1.0 - al) * ey0 + 2.0 * al * OR_C * Bx[o] + 4.0 * al * eyi -
+                 dt * (c2 * dBz_dx + Jy[o] / OR_EPS0)) /
+                (1.0 + al);
+        } else if (k == nz) {
+          long om = fidx(s, i, j, k - 1);
+          ex1 = ((1.0 - al) * ex0 + 2.0 * al * OR_C * By[om] +
+                 dt * (c2 * dBz_dy - Jx[o] / OR_EPS0)) /
+                (1.0 + al);
+          ey1 = ((1.0 - al) * ey0 - 2.0 * al * OR_C * Bx[om] -
+                 dt * (c2 * dBz_dx + Jy[o] / OR_EPS0)) /
+                (1.0 + al);
+        } else {
+          long om = fidx(s, i, j, k - 1);
+          double ax = dt * (c2 * (dBz_dy - (By[o] - By[om]) / dz) -
+                            Jx[o] / OR_EPS0);
+          double ay = dt * (c2 * ((Bx[o] - Bx[om]) / dz - dBz_dx) -
+                            Jy[o] / OR_EPS0);
+          ex1 = e_point(s, L, ex0, ax, &s->F[FPX][o], &s->F[FQX][o]);
+          ey1 = e_point(s, L, ey0, ay, &s->F[FPY][o], &s->F[FQY][o]);
+        }
+        joule += Jx[o] * 0.5 * (ex0 + ex1) + Jy[o] * 0.5 * (ey0 + ey1);
+        Ex[o] = ex1;
+        Ey[o] = ey1;
+        if (k < nz) {
+          double az = dt * (c2 * ((By[o] - By[fidx(s, i - 1, j, k)]) / dx -
+                                  (Bx[o] - Bx[fidx(s, i, j - 1, k)]) / dy) -
+                            Jz[o] / OR_EPS0);
+          double ez0 = Ez[o];
+          double ez1 = e_point(s, L, ez0, az, &s->F[FPZ][o], &s->F[FQZ][o]);
+          joule += Jz[o] * 0.5 * (ez0 + ez1);
+          Ez[o] = ez1;
+        }
+      }
+  }
+  s->U_joule += joule * dt * s->V;
+}
+
+void or_field_pass(or_sim *s) {
+  b_half(s);
+  e_full(s);
+  b_half(s);
+  for (int d = 0; d < 3; d++) memset(s->F[FJX + d], 0, s->nfield * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Amplitude window (Sec. 2.1, reading K6) and Keldysh threshold per cell.   */
+/* ------------------------------------------------------------------------ */
+void or_window_keldysh_pass(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz, NW = s->NW;
+  double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
+  int slot = (int)(s->step % NW);
+  for (int k = 0; k < nz; k++) {
+    int L = s->layer_of_plane[k];
+    if (L < 0) continue;
+    const or_layer *ly = &s->cfg.layers[L];
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long m = (long)s->mplane[k] * s->nxy + (long)j * nx + i;
+        double ax = 0.25 * (((Ex[fidx(s, i, j, k)] + Ex[fidx(s, i, j + 1, k)]) +
+                             Ex[fidx(s, i, j, k + 1)]) +
+                            Ex[fidx(s, i, j + 1, k + 1)]);
+        double ay = 0.25 * (((Ey[fidx(s, i, j, k)] + Ey[fidx(s, i + 1, j, k)]) +
+                             Ey[fidx(s, i, j, k + 1)]) +
+                            Ey[fidx(s, i + 1, j, k + 1)]);
+        double az = 0.25 * (((Ez[fidx(s, i, j, k)] + Ez[fidx(s, i + 1, j, k)]) +
+                             Ez[fidx(s, i, j + 1, k)]) +
+                            Ez[fidx(s, i + 1, j + 1, k)]);
+        double a = sqrt(ax * ax + ay * ay + az * az);
+        s->win[(long)slot * s->nmat + m] = a;
+        double mx = 0.0;
+        for (int q = 0; q < NW; q++) {
+          double v = s->win[(long)q * s->nmat + m];
+          if (v > mx) mx = v;
+        }
+        s->eamp[m] = mx;
+        double W = or_keldysh_W(mx, s->omega, s->gapJ[L], s->mstar[L],
+                                s->cfg.keldysh_terms, NULL);
+        ion_threshold(W, ly->n_mol, s->dt, &s->T[m], &s->Talways[m]);
+      }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ionisation draws and pair creation (Sec. 2.1 "ionized once", Sec. 3.2).   */
+/* ------------------------------------------------------------------------ */
+static void neutral_state(const or_sim *s, int L, uint32_t cell, uint32_t slot,
+                          double off0[3], double v0[3]) {
+  uint32_t r[4];
+  philox_draw(s->cfg.seed, 0, cell, slot, OR_STREAM_POS, r);
+  off0[0] = u01(r[0]);
+  off0[1] = u01(r[1]);
+  off0[2] = u01(r[2]);
+  philox_draw(s->cfg.seed, 0, cell, slot, OR_STREAM_VEL, r);
+  double sg = s->sigv[L];
+  double r1 = sqrt(-2.0 * log(u01(r[0]))), t1 = 2.0 * OR_PI * u01(r[1]);
+  double r2 = sqrt(-2.0 * log(u01(r[2]))), t2 = 2.0 * OR_PI * u01(r[3]);
+  v0[0] = sg * r1 * cos(t1);
+  v0[1] = sg * r1 * sin(t1);
+  v0[2] = sg * r2 * cos(t2);
+}
+
+void or_ionize_pass(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const double dl[3] = {s->cfg.dx, s->cfg.dy, s->cfg.dz};
+  const double t1 = (double)(s->step + 1) * s->dt;
+  for (int k = 0; k < nz; k++) {
+    int L = s->layer_of_plane[k];
+    if (L < 0) continue;
+    int ppc = s->cfg.layers[L].ppc;
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long m = (long)s->mplane[k] * s->nxy + (long)j * nx + i;
+        uint32_t cell = (uint32_t)(((long)k * ny + j) * nx + i);
+        for (int sl = 0; sl < ppc; sl++) {
+          if (!((s->alive[m] >> sl) & 1u)) continue;
+          double off0[3], v0[3];
+          neutral_state(s, L, cell, (uint32_t)sl, off0, v0);
+          int cc[3] = {i, j, k};
+          double dn[3];
+          for (int d = 0; d < 3; d++) {
+            double nd = off0[d] + v0[d] * t1 / dl[d];
+            int c0 = cc[d];
+            if (nd < 0.0) {
+              nd += 1.0;
+              c0 -= 1;
+            }
+            if (nd >= 1.0) {
+              nd -= 1.0;
+              c0 += 1;
+            }
+            cc[d] = c0;
+            dn[d] = nd;
+          }
+          cc[0] = (cc[0] % nx + nx) % nx;
+          cc[1] = (cc[1] % ny + ny) % ny;
+          uint64_t T = 0;
+          int always = 0;
+          if (cc[2] >= 0 && cc[2] < nz && s->mplane[cc[2]] >= 0) {
+            long m2 = (long)s->mplane[cc[2]] * s->nxy + (long)cc[1] * nx + cc[0];
+            T = s->T[m2];
+            always = s->Talways[m2];
+          }
+          uint32_t r[4];
+          philox_draw(s->cfg.seed, (uint32_t)s->step, cell, (uint32_t)sl,
+                      OR_STREAM_ION, r);
+          uint64_t r64 = ((uint64_t)r[1] << 32) | r[0];
+          if (!(always || r64 < T)) continue;
+          s->alive[m] &= ~(1u << sl);
+          double v2 = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
+          double gm = 1.0 / sqrt(1.0 - v2 / (OR_C * OR_C));
+          grow(s, s->np + 2);
+          uint64_t gid = (uint64_t)cell * (uint64_t)ppc + (uint64_t)sl;
+          int32_t ncell = (int32_t)(((long)cc[2] * ny + cc[1]) * nx + cc[0]);
+          for (int sp = 0; sp < 2; sp++) {
+            long p = s->np++;
+            s->pid[p] = 2 * gid + (uint64_t)sp;
+            s->pcell[p] = ncell;
+            for (int d = 0; d < 3; d++) {
+              s->poff[3 * p + d] = dn[d];
+              s->pu[3 * p + d] = gm * v0[d];
+            }
+            s->ptag[p] = ((uint32_t)L << 1) | (uint32_t)sp;
+          }
+          s->n_events += 1.0;
+          s->N_pairs += s->wmac[L];
+          s->U_ion += s->wmac[L] * s->gapJ[L];
+        }
+      }
+  }
+}
+
+/* Phases of one step: 1 particle, 2 field, 4 window + Keldysh, 8 ionisation,
+ * 16 advance the step counter.  A full step is 31. */
+void or_step_phases(or_sim *s, int mask) {
+  if (mask & 1) or_particle_pass(s);
+  if (mask & 2) or_field_pass(s);
+  if (mask & 4) or_window_keldysh_pass(s);
+  if (mask & 8) or_ionize_pass(s);
+  if (mask & 16) s->step++;
+}
+
+void or_step(or_sim *s, int n) {
+  for (int q = 0; q < n; q++) or_step_phases(s, 31);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (Sec. 4.1 number density, Sec. 4.2 energy density, Sec. 4.3   */
+/* spectra; readings K17, K18).                                              */
+/* ------------------------------------------------------------------------ */
+static void deposit_node(const or_sim *s, double *grid, int ci, int cj, int ck,
+                         const double off[3], double val) {
+  double wx[3], wy[3], wz[3];
+  int bx = tsc(off[0], 0, wx), by = tsc(off[1], 0, wy), bz = tsc(off[2], 0, wz);
+  for (int c = 0; c < 3; c++)
+    for (int b = 0; b < 3; b++)
+      for (int a = 0; a < 3; a++)
+        grid[fidx(s, ci + bx + a, cj + by + b, ck + bz + c)] +=
+            val * wx[a] * wy[b] * wz[c];
+}
+
+/* Charge density at integer nodes with the TSC shape, C/m^3. */
+void or_rho(const or_sim *s, double *rho) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny;
+  memset(rho, 0, s->nfield * sizeof(double));
+  for (long p = 0; p < s->np; p++) {
+    int32_t cell = s->pcell[p];
+    int L = (int)(s->ptag[p] >> 1), sp = (int)(s->ptag[p] & 1u);
+    double q = (sp ? OR_QE : -OR_QE) * s->wmac[L] / s->V;
+    deposit_node(s, rho, cell % nx, (cell / nx) % ny, cell / (nx * ny),
+                 &s->poff[3 * p], q);
+  }
+}
+
+void or_diagnostics(const or_sim *s, or_diag *dg, int n_bins, double e_min_eV,
+                    double e_max_eV, const int region[6], double *spectrum) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  memset(dg, 0, sizeof(*dg));
+  double *ne = calloc(s->nfield, sizeof(double));
+  double *ed = calloc(s->nfield, sizeof(double));
+  double *rho = calloc(s->nfield, sizeof(double));
+  if (spectrum)
+    for (int b = 0; b < n_bins; b++) spectrum[b] = 0.0;
+  double kin = 0.0;
+  for (long p = 0; p < s->np; p++) {
+    int32_t cell = s->pcell[p];
+    int ci = cell % nx, cj = (cell / nx) % ny, ck = cell / (nx * ny);
+    int L = (int)(s->ptag[p] >> 1), sp = (int)(s->ptag[p] & 1u);
+    const double *u = &s->pu[3 * p];
+    double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) /
+                              (OR_C * OR_C));
+    double ek = (g - 1.0) * s->mass[L][sp] * OR_C * OR_C;
+    double w = s->wmac[L];
+    kin += w * ek;
+    deposit_node(s, rho, ci, cj, ck, &s->poff[3 * p],
+                 (sp ? OR_QE : -OR_QE) * w / s->V);
+    if (sp == 0) {
+      dg->n_electrons_macro += 1.0;
+      deposit_node(s, ne, ci, cj, ck, &s->poff[3 * p], w / s->V);
+      deposit_node(s, ed, ci, cj, ck, &s->poff[3 * p], w * ek / s->V);
+      if (spectrum && n_bins > 0 && ci >= region[0] && ci < region[1] &&
+          cj >= region[2] && cj < region[3] && ck >= region[4] &&
+          ck < region[5]) {
+        double ev = ek / OR_QE;
+        if (ev >= e_min_eV && ev < e_max_eV) {
+          int b = (int)floor((ev - e_min_eV) / (e_max_eV - e_min_eV) * n_bins);
+          if (b >= 0 && b < n_bins) spectrum[b] += w;
+        }
+      }
+    } else {
+      dg->n_holes_macro += 1.0;
+    }
+  }
+  double uf = 0.0;
+  for (long o = 0; o < s->nfield; o++) {
+    for (int d = 0; d < 3; d++) {
+      double e = s->F[FEX + d][o], b = s->F[FBX + d][o];
+      uf += 0.5 * OR_EPS0 * e * e + 0.5 * b * b / OR_MU0;
+    }
+    if (ne[o] > dg->n_e_peak) dg->n_e_peak = ne[o];
+    if (ed[o] > dg->energy_density_peak) dg->energy_density_peak = ed[o];
+    if (fabs(rho[o]) > dg->rho_max) dg->rho_max = fabs(rho[o]);
+  }
+  double gmax = 0.0;
+  for (int k = 4; k <= nz - 4; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long o = fidx(s, i, j, k);
+        long ox = fidx(s, i - 1, j, k), oy = fidx(s, i, j - 1, k),
+             oz = fidx(s, i, j, k - 1);
+        double div =
+            ((s->F[FEX][o] + s->F[FPX][o]) - (s->F[FEX][ox] + s->F[FPX][ox])) /
+                s->cfg.dx +
+            ((s->F[FEY][o] + s->F[FPY][o]) - (s->F[FEY][oy] + s->F[FPY][oy])) /
+                s->cfg.dy +
+            ((s->F[FEZ][o] + s->F[FPZ][o]) - (s->F[FEZ][oz] + s->F[FPZ][oz])) /
+                s->cfg.dz;
+        double r = fabs(OR_EPS0 * div - rho[o]);
+        if (r > gmax) gmax = r;
+      }
+  dg->gauss_residual_max = gmax;
+  dg->U_field = uf * s->V;
+  dg->U_kinetic = kin;
+  dg->U_ionization = s->U_ion;
+  dg->U_absorbed = kin + s->U_ion;
+  dg->U_incident = s->cfg.fluence * (nx * s->cfg.dx) * (ny * s->cfg.dy);
+  dg->frac_absorbed = dg->U_absorbed / dg->U_incident;
+  dg->U_joule = s->U_joule;
+  dg->N_pairs = s->N_pairs;
+  dg->step = (double)s->step;
+  free(ne);
+  free(ed);
+  free(rho);
+}
+
+/* ------------------------------------------------------------------------ */
+/* State access for the tests                                               */
+/* ------------------------------------------------------------------------ */
+void or_info(const or_sim *s, double *dt, int *NW, long *nfield, long *nmat,
+             long *np, long *step, double *E0) {
+  *dt = s->dt;
+  *NW = s->NW;
+  *nfield = s->nfield;
+  *nmat = s->nmat;
+  *np = s->np;
+  *step = s->step;
+  *E0 = s->E0;
+}
+
+void or_get_fields(const or_sim *s, double *out) {
+  for (int c = 0; c < NCOMP; c++)
+    memcpy(out + (long)c * s->nfield, s->F[c], s->nfield * sizeof(double));
+}
+
+void or_set_fields(or_sim *s, const double *in) {
+  for (int c = 0; c < NCOMP; c++)
+    memcpy(s->F[c], in + (long)c * s->nfield, s->nfield * sizeof(double));
+}
+
+static const or_sim *g_sort_sim;
+static int cmp_id(const void *a, const void *b) {
+  uint64_t x = g_sort_sim->pid[*(const long *)a],
+           y = g_sort_sim->pid[*(const long *)b];
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Particles in ascending id order. */
+void or_get_particles(const or_sim *s, uint64_t *id, int32_t *cell,
+                      double *off, double *u, uint32_t *tag) {
+  long *ord = malloc((s->np ? s->np : 1) * sizeof(long));
+  for (long p = 0; p < s->np; p++) ord[p] = p;
+  g_sort_sim = s;
+  qsort(ord, s->np, sizeof(long), cmp_id);
+  for (long q = 0; q < s->np; q++) {
+    long p = ord[q];
+    id[q] = s->pid[p];
+    cell[q] = s->pcell[p];
+    for (int d = 0; d < 3; d++) {
+      off[3 * q + d] = s->poff[3 * p + d];
+      u[3 * q + d] = s->pu[3 * p + d];
+    }
+    tag[q] = s->ptag[p];
+  }
+  free(ord);
+}
+
+void or_set_particles(or_sim *s, long n, const uint64_t *id,
+                      const int32_t *cell, const double *off, const double *u,
+                      const uint32_t *tag) {
+  grow(s, n);
+  s->np = n;
+  memcpy(s->pid, id, n * sizeof(uint64_t));
+  memcpy(s->pcell, cell, n * sizeof(int32_t));
+  memcpy(s->poff, off, 3 * n * sizeof(double));
+  memcpy(s->pu, u, 3 * n * sizeof(double));
+  memcpy(s->ptag, tag, n * sizeof(uint32_t));
+}
+
+void or_get_material(const or_sim *s, uint32_t *alive, double *win,
+                     double *eamp, uint64_t *T, uint8_t *Talways) {
+  if (alive) memcpy(alive, s->alive, s->nmat * sizeof(uint32_t));
+  if (win) memcpy(win, s->win, (size_t)s->NW * s->nmat * sizeof(double));
+  if (eamp) memcpy(eamp, s->eamp, s->nmat * sizeof(double));
+  if (T) memcpy(T, s->T, s->nmat * sizeof(uint64_t));
+  if (Talways) memcpy(Talways, s->Talways, s->nmat);
+}
+
+void or_set_material(or_sim *s, const uint32_t *alive, const double *win) {
+  if (alive) memcpy(s->alive, alive, s->nmat * sizeof(uint32_t));
+  if (win) memcpy(s->win, win, (size_t)s->NW * s->nmat * sizeof(double));
+}
+
+void or_get_scalars(const or_sim *s, double out[4]) {
+  out[0] = s->U_joule;
+  out[1] = s->N_pairs;
+  out[2] = s->U_ion;
+  out[3] = s->n_events;
+}
+
+void or_set_scalars(or_sim *s, long step, const double in[4]) {
+  s->step = step;
+  s->U_joule = in[0];
+  s->N_pairs = in[1];
+  s->U_ion = in[2];
+  s->n_events = in[3];
+}
+
+/* Incident field value, for the boundary tests. */
+double or_incident(const or_sim *s, double t) { return e_inc(s, t); }
