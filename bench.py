@@ -1,0 +1,342 @@
+"""Throughput of the per-timestep PIC cycle on GB300.
+
+Workload: bulk fused silica, 128 x 128 x 512 cells at lambda/40, slab z
+128-480 with 8 neutral macroparticles per cell, 5 fs / 2 J cm^-2 pulse, FP32
+fields, push and deposit (the 2000-step bulk-silica configuration).  A step
+is one full PIC step (gather, Boris, deposit, Yee + polarisation, window,
+Keldysh, ionisation, pool maintenance).  The run first advances `--prerun`
+untimed steps so that the pulse is inside the slab and ionising, then
+`--warmup` steps, then times `--steps` steps with CUDA events on the
+simulation's stream.  The state (13.6 GB) is far larger than L2, so no
+flush is needed between steps.
+
+value   = charged-particle pushes per second (all ranks)
+e2e     = the same through the public API with a device->host read of the
+          step's accumulators after every step (no per-step host inputs:
+          the laser and the neutrals are generated on the device)
+roofline= the dominant kernel's algorithmic bytes / its CUDA-event time
+`--impl reference` times the FP64 CPU oracle on a 4 x 4 column of the same
+workload (same z structure, prerun to the same step).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s & cell-updates/s (%HBM roofline); fluence-scan p50/p99 latency"
+UNIT = "particle-steps/s"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2502_13695_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, units):
+    """DRAM bytes per launch from the committed ncu summary, scaled to the
+    units (particles or cells) of this launch; None if the kernel source has
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_unit"] * units
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in self.rows for q in range(4)
+                          if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": reasons}
+
+
+def dist_setup(n_gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, local, ws, dist
+
+
+def allreduce(dist, x, op):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(prerun, steps):
+    """Time the FP64 oracle on a 4 x 4 transverse column of the workload,
+    prerun to the same step; returns (particle-steps/s, cell-updates/s, info)."""
+    import oracle
+    from paper_2502_13695_gb300 import workloads as wl
+    oracle.build()
+    cfg = wl.config2()
+    col = dict(cfg, nx=4, ny=4)
+    s = oracle.Sim(col)
+    s.step(prerun)
+    n0 = s.np
+    t0 = time.perf_counter()
+    psteps = 0
+    for _ in range(steps):
+        psteps += s.np
+        s.step(1)
+    dt = time.perf_counter() - t0
+    ncell = col["nx"] * col["ny"] * col["nz"]
+    return psteps / dt, ncell * steps / dt, dict(
+        sample=f"4x4x512 column of the 128x128x512 silica workload (same z profile), "
+               f"steps {prerun}..{prerun + steps}, {n0} charged macroparticles at start",
+        seconds=dt, cores=1)
+
+
+def run_reference(args, rank, world, dist):
+    if rank != 0:
+        return
+    steps = max(1, args.steps if args.ref_steps is None else args.ref_steps)
+    ps, cu, info = oracle_sample(args.prerun + args.warmup, steps)
+    line = {"metric": METRIC, "value": ps, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * info["seconds"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "silica-128x128x512-fp32 (oracle on a 4x4 column)",
+                       "cell_updates_per_s": cu},
+            "cpu_baseline": {"value": ps, "unit": UNIT, "cores": info["cores"],
+                             "kind": "oracle", "sample": info["sample"]},
+            "e2e": {"value": ps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+ALG_BYTES = {  # FP32 algorithmic bytes per unit
+    "push": ("particle", 60.0),
+    "bhalf": ("field point", 36.0),
+    "efull": ("field point", 60.0),
+    "window": ("material cell", 48.0),
+    "ionize": ("material cell", 16.0),
+    "sort": ("particle", 80.0),
+}
+
+
+def run_native(args, rank, local, world, dist):
+    import torch
+    from paper_2502_13695_gb300 import build, pic, workloads as wl
+    build.build()
+    torch.cuda.set_device(local)
+    cfg = wl.config2()
+    cfg["seed"] = cfg["seed"] + 7919 * rank  # independent replica per rank
+    if args.pool_factor is not None:
+        cfg["pool_factor"] = args.pool_factor
+    sim = pic.Simulation(cfg)
+    st = sim.static
+    sim.step(args.prerun + args.warmup)
+    sim.sync()
+    stream = sim.stream
+    i0, s0 = sim.info(), sim.scalars()
+    sim.profile(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    with Clocks(gpu_index if gpu_index.isdigit() else local) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = sim.profile_read()
+    sim.profile(False)
+    sim.sync()
+    i1, s1 = sim.info(), sim.scalars()
+    psteps = i1["particle_steps"] - i0["particle_steps"]
+    events = s1["n_events"] - s0["n_events"]
+    launches = i1["launches"] - i0["launches"]
+    ms_max = allreduce(dist, ms, _op(dist, "max"))
+    psteps_all = allreduce(dist, psteps, _op(dist, "sum"))
+    events_all = allreduce(dist, events, _op(dist, "sum"))
+    t = ms_max / 1e3
+    ncell = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    cells_all = ncell * args.steps * world
+    alg = (72.0 * ncell + 65.0 * st["nmat"]) * args.steps * world + 60.0 * psteps_all + 64.0 * events_all
+    peak, peak_kind = measured_peaks()
+    # dominant kernel roofline
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    unit_name, per_unit = ALG_BYTES.get(dom, ("step", 0.0))
+    if dom == "push":
+        units = psteps / max(dom_n, 1)
+    elif dom == "sort":
+        units = (i1["n_particles"] + i0["n_particles"]) / 2
+    elif unit_name == "field point":
+        units = st["nfield"]
+    else:
+        units = st["nmat"]
+    bytes_launch = per_unit * units
+    achieved = bytes_launch / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else 0.0
+    # end to end: step + device->host read of the accumulators, every step
+    e2e_steps = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    pe0 = sim.info()["particle_steps"]
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.step(1)
+        sim.scalars()
+    e2e_t = time.perf_counter() - t0
+    pe1 = sim.info()["particle_steps"]
+    e2e_t = allreduce(dist, e2e_t, _op(dist, "max"))
+    e2e_ps = allreduce(dist, pe1 - pe0, _op(dist, "sum")) / e2e_t
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": psteps_all / t, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
+                   "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
+                   "l2": "state larger than L2 (%.1f GB), no flush" % (st["arena_bytes"] / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "cell_updates_per_s": cells_all / t,
+        "hbm_roofline_frac": alg / t / (peak * 1e9),
+        "hbm_alg_bytes_per_step": alg / args.steps / world,
+        "charged_particles": [i0["n_particles"], i1["n_particles"]],
+        "ionisation_events": events,
+        "per_kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "bytes_per_launch": bytes_launch,
+                     "unit_of_work": unit_name, "per_unit_bytes": per_unit,
+                     "traffic": ncu_traffic(dom, units)},
+        "e2e": {"value": e2e_ps, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 40},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        ps, cu, info = oracle_sample(args.prerun, args.cpu_steps)
+        line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": info["cores"],
+                                "kind": "oracle", "sample": info["sample"],
+                                "cell_updates_per_s": cu}
+    print(json.dumps(line), flush=True)
+
+
+def _op(dist, name):
+    if dist is None:
+        return None
+    return {"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[name]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prerun", type=int, default=700)
+    ap.add_argument("--pool-factor", type=float, default=None,
+                    help="charged-slot capacity / neutrals (default: the workload's 3.0)")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--ref-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        run_reference(args, rank, world, None)
+        return
+    rank, local, world, dist = dist_setup(args.gpus)
+    try:
+        run_native(args, rank, local, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * pic.h - C ABI of the GB300 (sm_103a) particle-in-cell library for few-cycle
+ * laser pulses driving dielectrics (Smith et al., arXiv 2502.13695).
+ *
+ * One time step (pic_step) advances, entirely in CUDA kernels on one GPU:
+ *   - field gather with quadratic (TSC) weights, relativistic Boris push,
+ *     charge-conserving Esirkepov current deposition (Sec. 1: macroparticles
+ *     advanced by the Lorentz force; Sec. 4.1: shape function);
+ *   - the Yee update of E and B with the dielectric's polarisation current
+ *     (Sec. 2.3, refraction), the laser entering through the z_min boundary
+ *     and outflow faces (Sec. 3, Sec. 3.1);
+ *   - the per-cell maximum of |E| over the last optical cycle (Sec. 2.1,
+ *     rolling window) and the Keldysh photoionisation rate (Sec. 2.1, Eqs.
+ *     for x, W and Q);
+ *   - counter-based Philox4x32-10 draws keyed by (seed, step, cell, slot) that
+ *     ionise each molecule at most once (Sec. 2.1) into an electron and a
+ *     hole with the Table 1 effective masses (Sec. 3.2).
+ *
+ * Conventions
+ *   - Units are SI.  Cell (i, j, k) spans [i dx, (i+1) dx) x ...; linear cell
+ *     id c = (k ny + j) nx + i.  The laser travels along +z; x and y are
+ *     periodic; z has absorbing (Silver-Mueller) faces, the laser enters at
+ *     z = 0.  Charged particles that come within two cells of a z face leave.
+ *   - Field arrays have nx * ny * (nz + 1) entries (z planes 0..nz); a
+ *     component at a half-integer z position k + 1/2 is stored at plane k and
+ *     plane nz is unused for it.  Staggering (Yee): Ex (i+1/2, j, k),
+ *     Ey (i, j+1/2, k), Ez (i, j, k+1/2), Bx (i, j+1/2, k+1/2),
+ *     By (i+1/2, j, k+1/2), Bz (i+1/2, j+1/2, k); J like E.
+ *   - Polarisation state is stored in field units: P/eps0 [V/m] and
+ *     (dP/dt)/eps0 [V/(m s)], at the E points.
+ *   - A field point on plane k belongs to cell (i, j, k); a layer [z0, z1)
+ *     makes the E points of planes z0 .. z1-1 polarisable.
+ *
+ * Errors: every call returns PIC_OK (0) or a negative PIC_E* code and sets a
+ * thread-local message readable with pic_last_error().  No call aborts the
+ * process or traps the GPU.  Device-detected errors (pool overflow) are
+ * latched in the handle and reported by the next pic_sync / pic_diagnostics
+ * / state read.  A handle is not thread-safe.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL (-1)   /* bad sizes, layer outside the grid, CFL > 1 ... */
+#define PIC_ENOMEM (-2)   /* device memory or caller arena too small */
+#define PIC_EPOOL (-3)    /* ionisation outgrew the charged-particle pool */
+#define PIC_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define PIC_ECUDA (-5)    /* any CUDA runtime error */
+#define PIC_ESTATE (-6)   /* call not valid in the handle's current state */
+
+#define PIC_FP64 0
+#define PIC_FP32 1
+#define PIC_MAX_LAYERS 128
+
+/* Step phases for pic_step_phases (a full step is PIC_PHASE_ALL). */
+#define PIC_PHASE_PARTICLES 1 /* gather, Boris, move, deposit, z outflow */
+#define PIC_PHASE_FIELDS 2    /* B half step, E (+ polarisation), B half */
+#define PIC_PHASE_WINDOW 4    /* |E| window and Keldysh threshold per cell */
+#define PIC_PHASE_IONIZE 8    /* ionisation draws and pair creation */
+#define PIC_PHASE_ADVANCE 16  /* step counter += 1 */
+#define PIC_PHASE_ALL 31
+
+typedef struct pic_ctx *pic_handle;
+
+/* Grid and numerical parameters. */
+typedef struct {
+  int nx, ny, nz;      /* cells; nx, ny >= 4, nz >= 8 */
+  int precision;       /* PIC_FP64 or PIC_FP32 (fields, push, deposit) */
+  double dx, dy, dz;   /* cell sizes [m] */
+  double cfl;          /* dt = cfl / (c sqrt(1/dx^2+1/dy^2+1/dz^2)), 0 < cfl <= 1
+                          (Sec. 3.1 uses 0.95) */
+  double pool_factor;  /* charged-slot capacity = pool_factor * neutrals + 1024 */
+  int keldysh_terms;   /* terms of the Q series cap (Sec. 2.1: 500) */
+  int sort_interval;   /* steps between cell sorts of the pool (0: 16) */
+} pic_grid;
+
+/* One dielectric layer: z cells [z0, z1) over the whole transverse plane.
+ * Table 1 (Sec. 3.2) supplies gap, masses and density; the Lorentz pole
+ * (omega0_eV, INFINITY for a static permittivity) and the index fix the
+ * polarisation; temp_eV and mol_mass_amu the neutrals' thermal velocity. */
+typedef struct {
+  int z0, z1;         /* 2 <= z0 < z1 <= nz - 2, layers must not overlap */
+  int ppc;            /* neutral macroparticles per cell, 1..32 */
+  int reserved;
+  double n_index;     /* refractive index at the laser wavelength */
+  double gap_eV;      /* band gap Delta */
+  double me_star;     /* electron effective mass / m_e */
+  double mh_star;     /* hole effective mass / m_e */
+  double n_mol;       /* molecular density [m^-3] */
+  double omega0_eV;   /* Lorentz pole photon energy, INFINITY = static eps */
+  double damping;     /* Lorentz damping rate [rad/s] */
+  double temp_eV;     /* neutral temperature */
+  double mol_mass_amu;/* molecular mass */
+} pic_layer;
+
+typedef struct {
+  int n_layers;             /* 0..PIC_MAX_LAYERS */
+  int reserved;
+  const pic_layer *layers;  /* host array, copied by pic_create */
+} pic_material;
+
+/* Laser (Sec. 3): plane wave along +z, Gaussian intensity envelope of
+ * intensity FWHM fwhm, peak fluence F = int c eps0 E^2 dt at z = 0. */
+typedef struct {
+  double lambda;   /* wavelength [m] */
+  double fwhm;     /* intensity FWHM [s] */
+  double fluence;  /* [J/m^2] */
+  double cep;      /* carrier-envelope phase [rad] */
+  double t_peak;   /* time of the envelope peak at z = 0 [s] */
+  int pol;         /* 0: E along x, 1: E along y */
+  int reserved;
+} pic_pulse;
+
+/* Sizes and derived constants of a configuration (pic_query / pic_info). */
+typedef struct {
+  double dt;                 /* time step [s] */
+  double E0;                 /* laser peak field [V/m] */
+  int NW;                    /* samples in the amplitude window (one cycle) */
+  int n_mplanes;             /* z planes that hold material */
+  long long nfield;          /* nx * ny * (nz + 1) */
+  long long nmat;            /* material cells */
+  long long n_neutrals;      /* initial neutral macroparticles */
+  long long capacity;        /* charged-particle slots */
+  long long n_particles;     /* charged-particle slots in use (pic_info) */
+  long long step;            /* steps taken (pic_info) */
+  size_t arena_bytes;        /* device bytes pic_create needs */
+  long long launches;        /* kernels launched on the handle so far (pic_info) */
+  double particle_steps;     /* charged-particle pushes done so far (pic_info) */
+} pic_info;
+
+/* Kernel classes reported by pic_profile_read. */
+#define PIC_PROF_PUSH 0    /* gather + Boris + deposit */
+#define PIC_PROF_BHALF 1   /* both B half steps */
+#define PIC_PROF_EFULL 2   /* E + polarisation + boundaries */
+#define PIC_PROF_WINDOW 3  /* amplitude window + Keldysh */
+#define PIC_PROF_IONIZE 4  /* ionisation draws + pair appends */
+#define PIC_PROF_SORT 5    /* pool sort (all its kernels) */
+#define PIC_PROF_OTHER 6   /* step counter */
+#define PIC_PROF_N 7
+
+/* FP64 diagnostics (Sec. 4.1 number density, Sec. 4.2 energy density,
+ * Sec. 4.3 spectra).  Inputs: n_bins, e_min_eV, e_max_eV, region, spectrum;
+ * everything else is output. */
+typedef struct {
+  double U_incident;         /* F * transverse area [J] */
+  double U_kinetic;          /* sum w (gamma - 1) m c^2 over carriers [J] */
+  double U_ionization;       /* sum over events w * gap [J] */
+  double U_absorbed;         /* U_kinetic + U_ionization [J] */
+  double frac_absorbed;      /* U_absorbed / U_incident */
+  double U_joule;            /* time integral of sum J.E dV [J] */
+  double U_field;            /* sum (eps0 E^2 + B^2 / mu0) / 2 dV [J] */
+  double N_pairs;            /* real electron-hole pairs created */
+  double n_e_peak;           /* max over nodes of TSC electron density [m^-3] */
+  double energy_density_peak;/* max over nodes of TSC electron energy density [J/m^3] */
+  double gauss_residual_max; /* max |eps0 div(E + P/eps0) - rho| on planes 4..nz-4 [C/m^3] */
+  double rho_max;            /* max |rho| [C/m^3] */
+  double n_electrons_macro;  /* electron macroparticles */
+  double n_holes_macro;      /* hole macroparticles */
+  long long step;            /* steps taken */
+  int n_bins;                /* spectrum bins (0: no spectrum) */
+  int reserved;
+  double e_min_eV, e_max_eV; /* spectrum range, uniform bins */
+  int region[6];             /* cell box [i0, i1) x [j0, j1) x [k0, k1) */
+  int reserved2[2];
+  double *spectrum;          /* caller-owned host array of n_bins: real
+                                electrons per bin (electron kinetic energy) */
+} pic_diag;
+
+/* Sizes of a configuration without creating it.  Returns PIC_EINVAL for an
+ * invalid configuration. */
+int pic_query(const pic_grid *grid, const pic_material *mat,
+              const pic_pulse *pulse, pic_info *out);
+
+/* Create a simulation: validate, lay out the device state, initialise the
+ * neutrals (Philox streams, no host RNG) and zero the fields.
+ *   stream      : cudaStream_t to run on (NULL: the legacy default stream)
+ *   d_arena     : caller-owned device memory of >= arena_bytes (pic_query),
+ *                 256-byte aligned, or NULL to let the library cudaMalloc it
+ *   arena_bytes : size of d_arena (ignored when d_arena is NULL)
+ * The caller keeps ownership of d_arena and must keep it alive until
+ * pic_destroy. */
+int pic_create(const pic_grid *grid, const pic_material *mat,
+               const pic_pulse *pulse, uint64_t seed, void *stream,
+               void *d_arena, size_t arena_bytes, pic_handle *out);
+
+/* Enqueue n_steps full steps on the handle's stream (asynchronous). */
+int pic_step(pic_handle h, int n_steps);
+
+/* Enqueue selected phases of the current step (PIC_PHASE_* mask). */
+int pic_step_phases(pic_handle h, int mask);
+
+/* Wait for the handle's stream; report latched device errors. */
+int pic_sync(pic_handle h);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch (enable != 0 starts a fresh record, 0 stops recording).
+ * pic_profile_read synchronises and returns, per PIC_PROF_* class, the summed
+ * device milliseconds and launch counts since the last enable. */
+int pic_profile(pic_handle h, int enable);
+int pic_profile_read(pic_handle h, double ms[PIC_PROF_N], long long launches[PIC_PROF_N]);
+
+/* Synchronous FP64 diagnostics of the current state. */
+int pic_diagnostics(pic_handle h, pic_diag *inout);
+
+int pic_info_get(pic_handle h, pic_info *out);
+int pic_destroy(pic_handle h);
+const char *pic_last_error(void);
+
+/* ---- state access (synchronous; host pointers; used for per-step parity
+ *      and checkpointing) ------------------------------------------------- */
+
+/* 15 * nfield doubles: Ex Ey Ez Bx By Bz Jx Jy Jz Px Py Pz Qx Qy Qz, each in
+ * the field layout above; P and Q are P/eps0 and (dP/dt)/eps0 and are zero
+ * outside material planes. */
+int pic_get_fields(pic_handle h, double *dst);
+int pic_set_fields(pic_handle h, const double *src);
+
+/* Charged particles in slot order (unsorted).  *n receives the count; with
+ * any array NULL only the count is returned.  off and u are n x 3 (offset in
+ * [0,1) within the cell; u = gamma v [m/s]); tag = (birth layer << 1) |
+ * species (0 electron, 1 hole); id = 2 gid (+1 for the hole) with
+ * gid = birth cell * ppc + slot. */
+int pic_get_particles(pic_handle h, long long *n, uint64_t *id, int32_t *cell,
+                      double *off, double *u, uint32_t *tag);
+int pic_set_particles(pic_handle h, long long n, const uint64_t *id,
+                      const int32_t *cell, const double *off, const double *u,
+                      const uint32_t *tag);
+
+/* Per material cell m = mplane(k) nx ny + j nx + i: alive neutral bitmask,
+ * window amplitude of the last window phase, and the ionisation threshold
+ * T = floor(p 2^64) (UINT64_MAX: p = 1).  Any pointer may be NULL. */
+int pic_get_material(pic_handle h, uint32_t *alive, double *eamp, uint64_t *T);
+
+/* Load alive bits and the raw amplitude history: win is NW x nmat, slot q
+ * holding the most recent sample whose index is q mod NW (samples are
+ * numbered by the step that wrote them).  Either pointer may be NULL. */
+int pic_set_material(pic_handle h, const uint32_t *alive, const double *win);
+
+/* Accumulators: [U_joule, N_pairs, U_ionization, events]. */
+int pic_get_scalars(pic_handle h, long long *step, double out[4]);
+int pic_set_scalars(pic_handle h, long long step, const double in[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

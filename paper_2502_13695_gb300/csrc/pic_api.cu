@@ -1,0 +1,1036 @@
+// C ABI of the GB300 PIC library (declared in include/pic.h): validation,
+// device memory layout, step scheduling, diagnostics and state access.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_kernels.cuh"
+
+using namespace pg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define PIC_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(PIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kSpecMax = 65536;
+constexpr int kThreads = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Everything derived from the inputs, shared by pic_query and pic_create.
+struct Plan {
+  pic_grid g;
+  std::vector<pic_layer> layers;
+  pic_pulse pulse;
+  int rsz;  // bytes per real
+  double dt, omega, E0, V;
+  int NW, n_mplanes;
+  long long nxy, nfield, ncell, nmat, n_neutrals, cap;
+  std::vector<int> lop, mplane, kplane;
+  int nb_scan, diag_blocks_p, diag_blocks_g;
+  // arena offsets
+  size_t off_E[3], off_B[3], off_J[3], off_P[3], off_Q[3];
+  size_t off_lop, off_mplane, off_kplane, off_lk, off_lr;
+  size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
+  size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
+  size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
+  size_t off_ne, off_ed, off_rho, off_spec, off_part;
+  size_t total;
+};
+
+int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_pulse *pulse,
+                      Plan &P) {
+  if (!grid || !mat || !pulse) return fail(PIC_EINVAL, "null configuration pointer");
+  const pic_grid &g = *grid;
+  if (g.nx < 4 || g.ny < 4 || g.nz < 8) return fail(PIC_EINVAL, "grid needs nx, ny >= 4, nz >= 8");
+  if (!(g.dx > 0 && g.dy > 0 && g.dz > 0)) return fail(PIC_EINVAL, "cell sizes must be > 0");
+  if (!(g.cfl > 0 && g.cfl <= 1.0)) return fail(PIC_EINVAL, "cfl must be in (0, 1]");
+  if (g.precision != PIC_FP64 && g.precision != PIC_FP32)
+    return fail(PIC_EINVAL, "unknown precision");
+  if (!(g.pool_factor >= 0)) return fail(PIC_EINVAL, "pool_factor must be >= 0");
+  if (g.keldysh_terms < 0 || g.sort_interval < 0) return fail(PIC_EINVAL, "negative count");
+  if (mat->n_layers < 0 || mat->n_layers > PIC_MAX_LAYERS || (mat->n_layers && !mat->layers))
+    return fail(PIC_EINVAL, "bad layer count");
+  if (!(pulse->lambda > 0 && pulse->fwhm > 0 && pulse->fluence >= 0) ||
+      (pulse->pol != 0 && pulse->pol != 1))
+    return fail(PIC_EINVAL, "bad pulse");
+  P.g = g;
+  if (P.g.keldysh_terms == 0) P.g.keldysh_terms = 500;
+  if (P.g.sort_interval == 0) P.g.sort_interval = 16;
+  P.pulse = *pulse;
+  P.layers.assign(mat->layers, mat->layers + mat->n_layers);
+  P.rsz = g.precision == PIC_FP64 ? 8 : 4;
+  P.nxy = (long long)g.nx * g.ny;
+  P.ncell = P.nxy * g.nz;
+  P.nfield = P.nxy * (g.nz + 1);
+  if (P.ncell >= (1ll << 31)) return fail(PIC_EINVAL, "grid has >= 2^31 cells");
+  P.dt = g.cfl / (kC * std::sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy) + 1.0 / (g.dz * g.dz)));
+  P.omega = 2.0 * kPi * kC / pulse->lambda;
+  P.V = g.dx * g.dy * g.dz;
+  P.NW = (int)std::ceil(pulse->lambda / (kC * P.dt));
+  P.E0 = std::sqrt(2.0 * pulse->fluence /
+                   (kC * kEps0 * pulse->fwhm * std::sqrt(kPi / (4.0 * std::log(2.0)))));
+  P.lop.assign(g.nz, -1);
+  P.n_neutrals = 0;
+  for (int L = 0; L < mat->n_layers; ++L) {
+    const pic_layer &ly = mat->layers[L];
+    if (ly.z0 < 2 || ly.z1 > g.nz - 2 || ly.z0 >= ly.z1)
+      return fail(PIC_EINVAL, "layer " + std::to_string(L) + " must satisfy 2 <= z0 < z1 <= nz-2");
+    if (ly.ppc < 1 || ly.ppc > 32) return fail(PIC_EINVAL, "ppc must be in 1..32");
+    if (!(ly.n_index >= 1 && ly.gap_eV > 0 && ly.me_star > 0 && ly.mh_star > 0 && ly.n_mol > 0 &&
+          ly.omega0_eV > 0 && ly.damping >= 0 && ly.temp_eV >= 0 && ly.mol_mass_amu > 0))
+      return fail(PIC_EINVAL, "layer " + std::to_string(L) + " has a non-physical parameter");
+    if (std::isfinite(ly.omega0_eV) && ly.omega0_eV * kQe / kHbar <= P.omega)
+      return fail(PIC_EINVAL, "Lorentz pole must lie above the laser frequency");
+    for (int k = ly.z0; k < ly.z1; ++k) {
+      if (P.lop[k] >= 0) return fail(PIC_EINVAL, "layers overlap");
+      P.lop[k] = L;
+    }
+    P.n_neutrals += (long long)(ly.z1 - ly.z0) * P.nxy * ly.ppc;
+  }
+  P.mplane.assign(g.nz, -1);
+  P.kplane.clear();
+  for (int k = 0; k < g.nz; ++k)
+    if (P.lop[k] >= 0) {
+      P.mplane[k] = (int)P.kplane.size();
+      P.kplane.push_back(k);
+    }
+  P.n_mplanes = (int)P.kplane.size();
+  P.nmat = (long long)P.n_mplanes * P.nxy;
+  P.cap = (long long)std::ceil(g.pool_factor * (double)P.n_neutrals) + 1024;
+  if (P.cap >= (1ll << 31)) return fail(PIC_EINVAL, "particle pool of >= 2^31 slots");
+  P.nb_scan = (int)((P.ncell + kScanChunk - 1) / kScanChunk);
+  P.diag_blocks_p = 152 * 8;
+  P.diag_blocks_g = (int)((P.nfield + kThreads - 1) / kThreads);
+  // arena layout
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  const size_t R = P.rsz;
+  for (int d = 0; d < 3; ++d) P.off_E[d] = take(P.nfield * R);
+  for (int d = 0; d < 3; ++d) P.off_B[d] = take(P.nfield * R);
+  for (int d = 0; d < 3; ++d) P.off_J[d] = take(P.nfield * R);
+  for (int d = 0; d < 3; ++d) P.off_P[d] = take(P.nmat * R);
+  for (int d = 0; d < 3; ++d) P.off_Q[d] = take(P.nmat * R);
+  P.off_lop = take(g.nz * sizeof(int));
+  P.off_mplane = take(g.nz * sizeof(int));
+  P.off_kplane = take(std::max(1, P.n_mplanes) * sizeof(int));
+  P.off_lk = take(std::max(1, mat->n_layers) * sizeof(LayerK));
+  P.off_lr = take(std::max(1, mat->n_layers) * std::max(sizeof(LayerR<double>), sizeof(LayerR<float>)));
+  P.off_win = take((size_t)P.NW * P.nmat * R);
+  P.off_pm = take(P.nmat * R);
+  P.off_eamp = take(P.nmat * R);
+  P.off_ckey = take(P.nmat * R);
+  P.off_T = take(P.nmat * 8);
+  P.off_alive = take(P.nmat * 4);
+  P.off_leave = take(P.nmat * 4);
+  for (int b = 0; b < 2; ++b) {
+    P.off_pc[b] = take(P.cap * 4);
+    for (int d = 0; d < 3; ++d) P.off_po[b][d] = take(P.cap * R);
+    for (int d = 0; d < 3; ++d) P.off_pu[b][d] = take(P.cap * R);
+    P.off_pt[b] = take(P.cap * 4);
+    P.off_pid[b] = take(P.cap * 8);
+  }
+  P.off_cnt = take(P.ncell * 4);
+  P.off_bsum = take((size_t)P.nb_scan * 4);
+  P.off_total = take(8);
+  P.off_nslots = take(8);
+  P.off_step = take(8);
+  P.off_acc = take(8 * 8);
+  P.off_err = take(16);
+  P.off_ne = take(P.nfield * 8);
+  P.off_ed = take(P.nfield * 8);
+  P.off_rho = take(P.nfield * 8);
+  P.off_spec = take(kSpecMax * 8);
+  P.off_part = take((size_t)std::max(3 * P.diag_blocks_p, 5 * P.diag_blocks_g) * 8);
+  P.total = o;
+  return PIC_OK;
+}
+
+// Per-layer constants (double) and the amplitude below which the Keldysh
+// threshold is zero: the largest E of a 1% geometric grid up to which every
+// grid value has p 2^64 < 1/16 (W grows like E^(2N) there, N >= 3, so the
+// values between grid points stay below 1).
+std::vector<LayerK> layer_constants(const Plan &P) {
+  std::vector<LayerK> out;
+  for (const pic_layer &ly : P.layers) {
+    LayerK k{};
+    const bool st = !std::isfinite(ly.omega0_eV);
+    const double n2m1 = ly.n_index * ly.n_index - 1.0;
+    k.is_static = st;
+    if (st) {
+      k.deps = n2m1;
+      k.w0sq = 0.0;
+    } else {
+      const double w0 = ly.omega0_eV * kQe / kHbar;
+      k.deps = n2m1 * (1.0 - P.omega * P.omega / (w0 * w0));
+      k.w0sq = w0 * w0;
+    }
+    k.damping = ly.damping;
+    k.ppc = ly.ppc;
+    k.wmac = ly.n_mol * P.V / ly.ppc;
+    k.mass[0] = ly.me_star * kMe;
+    k.mass[1] = ly.mh_star * kMe;
+    k.qm[0] = -kQe / k.mass[0];
+    k.qm[1] = kQe / k.mass[1];
+    const double mstar = kMe / (1.0 / ly.me_star + 1.0 / ly.mh_star);
+    k.gapJ = ly.gap_eV * kQe;
+    k.kG = P.omega * std::sqrt(mstar * k.gapJ) / kQe;
+    k.kX = (2.0 / kPi) * k.gapJ / (kHbar * P.omega);
+    k.kP = 2.0 * (2.0 * P.omega / (9.0 * kPi)) * std::pow(mstar * P.omega / kHbar, 1.5) * P.dt /
+           ly.n_mol;
+    k.sigv = std::sqrt(ly.temp_eV * kQe / (ly.mol_mass_amu * kAmu));
+    double e = 1e3, last_ok = 0.0;
+    k.e_skip = 0.0;
+    for (int it = 0; it < 4000; ++it, e *= 1.01) {
+      const double p = keldysh_probability<double>(e, k, P.g.keldysh_terms);
+      if (p * 18446744073709551616.0 >= 1.0 / 16.0) break;
+      last_ok = e;
+    }
+    k.e_skip = last_ok;
+    out.push_back(k);
+  }
+  return out;
+}
+
+template <class R>
+std::vector<LayerR<R>> layer_working(const Plan &P, const std::vector<LayerK> &lk) {
+  std::vector<LayerR<R>> out;
+  const double h = P.dt;
+  const double dl[3] = {P.g.dx, P.g.dy, P.g.dz};
+  for (const LayerK &k : lk) {
+    LayerR<R> r{};
+    r.deps = R(k.deps);
+    r.is_static = k.is_static;
+    r.ppc = k.ppc;
+    if (k.is_static) {
+      r.inv_den = R(1.0 / (1.0 + k.deps));
+    } else {
+      r.cn_g = R(h);
+      r.cn_a = R(0.5 * h * h * k.w0sq);
+      r.cn_b = R(0.25 * h * h * k.w0sq * k.deps);
+      r.inv_den = R(1.0 / (1.0 + 0.25 * h * h * k.w0sq * (1.0 + k.deps) + 0.5 * k.damping * h));
+      r.two_over_h = R(2.0 / h);
+    }
+    for (int s = 0; s < 2; ++s) {
+      const double q = s ? kQe : -kQe;
+      r.qmdt2[s] = R(0.5 * k.qm[s] * h);
+      for (int d = 0; d < 3; ++d) r.jpref[s][d] = R(-q * k.wmac * dl[d] / (P.V * h));
+      r.inv_mass_c2[s] = R(1.0 / (k.mass[s] * kC * kC));
+    }
+    r.kG = R(k.kG);
+    r.kX = R(k.kX);
+    r.kP = R(k.kP);
+    r.e_skip = R(k.e_skip);
+    r.sig_v = R(k.sigv);
+    out.push_back(r);
+  }
+  return out;
+}
+
+}  // namespace
+
+struct pic_ctx {
+  Plan P;
+  std::vector<LayerK> lk;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  bool own_arena = false;
+  uint64_t seed = 0;
+  long long step = 0;
+  int since_sort = 0;
+  Ctx<double> c64{};
+  Ctx<float> c32{};
+  bool fp64 = true;
+  int sticky = PIC_OK;
+  long long launches = 0;
+  // profiling: (class, start, stop) event triples, reused across reads
+  bool profiling = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  size_t used = 0;
+  int open_cls = -1;
+};
+
+namespace {
+
+template <class R>
+Ctx<R> &ctx_of(pic_ctx *h);
+template <>
+Ctx<double> &ctx_of<double>(pic_ctx *h) { return h->c64; }
+template <>
+Ctx<float> &ctx_of<float>(pic_ctx *h) { return h->c32; }
+
+template <class R>
+void bind(pic_ctx *h) {
+  const Plan &P = h->P;
+  char *A = h->arena;
+  Ctx<R> &X = ctx_of<R>(h);
+  Dev<R> &D = X.d;
+  D.nx = P.g.nx;
+  D.ny = P.g.ny;
+  D.nz = P.g.nz;
+  D.nxy = (int)P.nxy;
+  D.nfield = P.nfield;
+  D.nmat = P.nmat;
+  D.ncell = P.ncell;
+  D.NW = P.NW;
+  D.keldysh_terms = P.g.keldysh_terms;
+  D.n_layers = (int)P.layers.size();
+  D.pol = P.pulse.pol;
+  D.dt = R(P.dt);
+  D.idx = R(1.0 / P.g.dx);
+  D.idy = R(1.0 / P.g.dy);
+  D.idz = R(1.0 / P.g.dz);
+  D.alpha = R(kC * P.dt / P.g.dz);
+  D.c2dt = R(kC * kC * P.dt);
+  D.dtdx = R(P.dt / P.g.dx);
+  D.dtdy = R(P.dt / P.g.dy);
+  D.dtdz = R(P.dt / P.g.dz);
+  D.dt_d = P.dt;
+  D.V_d = P.V;
+  D.dx_d = P.g.dx;
+  D.dy_d = P.g.dy;
+  D.dz_d = P.g.dz;
+  D.E0 = P.E0;
+  D.omega = P.omega;
+  D.fwhm = P.pulse.fwhm;
+  D.t_peak = P.pulse.t_peak;
+  D.cep = P.pulse.cep;
+  for (int d = 0; d < 3; ++d) {
+    D.E[d] = (R *)(A + P.off_E[d]);
+    D.B[d] = (R *)(A + P.off_B[d]);
+    D.J[d] = (R *)(A + P.off_J[d]);
+    D.P[d] = (R *)(A + P.off_P[d]);
+    D.Q[d] = (R *)(A + P.off_Q[d]);
+  }
+  D.layer_of_plane = (const int *)(A + P.off_lop);
+  D.mplane = (const int *)(A + P.off_mplane);
+  D.kplane = (const int *)(A + P.off_kplane);
+  D.layers = (const LayerK *)(A + P.off_lk);
+  D.win = (R *)(A + P.off_win);
+  D.pm = (R *)(A + P.off_pm);
+  D.eamp = (R *)(A + P.off_eamp);
+  D.ckey = (R *)(A + P.off_ckey);
+  D.T = (unsigned long long *)(A + P.off_T);
+  D.alive = (uint32_t *)(A + P.off_alive);
+  D.leave_step = (uint32_t *)(A + P.off_leave);
+  D.pcell = (int32_t *)(A + P.off_pc[0]);
+  for (int d = 0; d < 3; ++d) {
+    D.po[d] = (R *)(A + P.off_po[0][d]);
+    D.pu[d] = (R *)(A + P.off_pu[0][d]);
+    X.ao[d] = (R *)(A + P.off_po[1][d]);
+    X.au[d] = (R *)(A + P.off_pu[1][d]);
+  }
+  D.ptag = (uint32_t *)(A + P.off_pt[0]);
+  D.pid = (unsigned long long *)(A + P.off_pid[0]);
+  X.acell = (int32_t *)(A + P.off_pc[1]);
+  X.atag = (uint32_t *)(A + P.off_pt[1]);
+  X.aid = (unsigned long long *)(A + P.off_pid[1]);
+  D.cap = (unsigned long long)P.cap;
+  D.nslots = (unsigned long long *)(A + P.off_nslots);
+  D.step = (long long *)(A + P.off_step);
+  D.acc = (double *)(A + P.off_acc);
+  D.err = (int *)(A + P.off_err);
+  D.seed = h->seed;
+  X.lr = (const LayerR<R> *)(A + P.off_lr);
+}
+
+int grid_blocks(long long n) { return (int)std::max<long long>(1, (n + kThreads - 1) / kThreads); }
+constexpr int kPersistentBlocks = 152 * 8;
+
+// Event pair around a group of launches of one class (no-op unless profiling).
+void prof_begin(pic_ctx *h, int cls) {
+  if (!h->profiling) return;
+  if (h->used == h->recs.size()) {
+    pic_ctx::Rec r{cls, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    h->recs.push_back(r);
+  }
+  h->recs[h->used].cls = cls;
+  cudaEventRecord(h->recs[h->used].a, h->stream);
+  h->open_cls = cls;
+}
+
+void prof_end(pic_ctx *h) {
+  if (!h->profiling || h->open_cls < 0) return;
+  cudaEventRecord(h->recs[h->used].b, h->stream);
+  h->used++;
+  h->open_cls = -1;
+}
+
+template <class R>
+int sort_pool(pic_ctx *h) {
+  Ctx<R> &X = ctx_of<R>(h);
+  const Plan &P = h->P;
+  cudaStream_t s = h->stream;
+  unsigned int *cnt = (unsigned int *)(h->arena + P.off_cnt);
+  unsigned int *bsum = (unsigned int *)(h->arena + P.off_bsum);
+  unsigned long long *total = (unsigned long long *)(h->arena + P.off_total);
+  prof_begin(h, PIC_PROF_SORT);
+  PIC_CUDA(cudaMemsetAsync(cnt, 0, P.ncell * 4, s));
+  k_hist<<<kPersistentBlocks, kThreads, 0, s>>>(X.d.pcell, X.d.nslots, X.d.cap, cnt);
+  k_scan_reduce<<<P.nb_scan, kScanThreads, 0, s>>>(cnt, P.ncell, bsum);
+  k_scan_blocks<<<1, kScanThreads, 0, s>>>(bsum, P.nb_scan, total);
+  k_scan_final<<<P.nb_scan, kScanThreads, 0, s>>>(cnt, P.ncell, bsum);
+  k_scatter<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, cnt);
+  k_set_slots<<<1, 1, 0, s>>>(X.d.nslots, total);
+  prof_end(h);
+  h->launches += 6;
+  std::swap(X.d.pcell, X.acell);
+  for (int d = 0; d < 3; ++d) {
+    std::swap(X.d.po[d], X.ao[d]);
+    std::swap(X.d.pu[d], X.au[d]);
+  }
+  std::swap(X.d.ptag, X.atag);
+  std::swap(X.d.pid, X.aid);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+template <class R>
+int enqueue(pic_ctx *h, int mask) {
+  Ctx<R> &X = ctx_of<R>(h);
+  const Plan &P = h->P;
+  cudaStream_t s = h->stream;
+  if (mask & PIC_PHASE_PARTICLES) {
+    prof_begin(h, PIC_PROF_PUSH);
+    k_push<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
+    prof_end(h);
+    h->launches += 1;
+  }
+  if (mask & PIC_PHASE_FIELDS) {
+    prof_begin(h, PIC_PROF_BHALF);
+    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
+    prof_end(h);
+    prof_begin(h, PIC_PROF_EFULL);
+    k_efull<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X);
+    prof_end(h);
+    prof_begin(h, PIC_PROF_BHALF);
+    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
+    prof_end(h);
+    h->launches += 3;
+  }
+  if (P.nmat > 0) {
+    if (mask & PIC_PHASE_WINDOW) {
+      prof_begin(h, PIC_PROF_WINDOW);
+      k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+      prof_end(h);
+      h->launches += 1;
+    }
+    if (mask & PIC_PHASE_IONIZE) {
+      prof_begin(h, PIC_PROF_IONIZE);
+      k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+      prof_end(h);
+      h->launches += 1;
+    }
+  }
+  if (mask & PIC_PHASE_ADVANCE) {
+    prof_begin(h, PIC_PROF_OTHER);
+    k_advance<<<1, 1, 0, s>>>(X.d.step);
+    prof_end(h);
+    h->launches += 1;
+    h->step++;
+    if (++h->since_sort >= P.g.sort_interval) {
+      h->since_sort = 0;
+      const int rc = sort_pool<R>(h);
+      if (rc) return rc;
+    }
+  }
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+int enqueue_any(pic_ctx *h, int mask) { return h->fp64 ? enqueue<double>(h, mask) : enqueue<float>(h, mask); }
+
+template <class R>
+int init_state(pic_ctx *h) {
+  const Plan &P = h->P;
+  cudaStream_t s = h->stream;
+  PIC_CUDA(cudaMemsetAsync(h->arena, 0, P.total, s));
+  PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, s));
+  PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_mplane, P.mplane.data(), P.mplane.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, s));
+  if (!P.kplane.empty())
+    PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_kplane, P.kplane.data(),
+                             P.kplane.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!h->lk.empty()) {
+    PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lk, h->lk.data(), h->lk.size() * sizeof(LayerK),
+                             cudaMemcpyHostToDevice, s));
+    std::vector<LayerR<R>> lr = layer_working<R>(P, h->lk);
+    PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lr, lr.data(), lr.size() * sizeof(LayerR<R>),
+                             cudaMemcpyHostToDevice, s));
+    PIC_CUDA(cudaStreamSynchronize(s));  // lr is a host temporary
+  }
+  if (P.nmat > 0) k_init_material<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(ctx_of<R>(h));
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaStreamSynchronize(s));
+  return PIC_OK;
+}
+
+int check_sticky(pic_ctx *h) {
+  int e = 0;
+  const Plan &P = h->P;
+  PIC_CUDA(cudaMemcpyAsync(&e, h->arena + P.off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  if (e & kErrPool) h->sticky = PIC_EPOOL;
+  if (h->sticky == PIC_EPOOL)
+    return fail(PIC_EPOOL, "ionisation outgrew the charged-particle pool (raise pool_factor)");
+  return PIC_OK;
+}
+
+template <class R>
+void to_double(const std::vector<char> &raw, size_t n, double *dst) {
+  const R *src = (const R *)raw.data();
+  for (size_t q = 0; q < n; ++q) dst[q] = (double)src[q];
+}
+
+template <class R>
+void from_double(const double *src, size_t n, std::vector<char> &raw) {
+  raw.resize(n * sizeof(R));
+  R *d = (R *)raw.data();
+  for (size_t q = 0; q < n; ++q) d[q] = (R)src[q];
+}
+
+int copy_in(pic_ctx *h, size_t off, const void *src, size_t bytes) {
+  PIC_CUDA(cudaMemcpyAsync(h->arena + off, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int copy_out(pic_ctx *h, size_t off, void *dst, size_t bytes) {
+  PIC_CUDA(cudaMemcpyAsync(dst, h->arena + off, bytes, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+// device offset of a pointer inside the arena
+size_t off_of(pic_ctx *h, const void *p) { return (size_t)((const char *)p - h->arena); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Exported entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *pic_last_error(void) { return g_err.c_str(); }
+
+int pic_query(const pic_grid *grid, const pic_material *mat, const pic_pulse *pulse,
+              pic_info *out) {
+  Plan P;
+  const int rc = validate_and_plan(grid, mat, pulse, P);
+  if (rc) return rc;
+  if (!out) return fail(PIC_EINVAL, "null output");
+  std::memset(out, 0, sizeof(*out));
+  out->dt = P.dt;
+  out->E0 = P.E0;
+  out->NW = P.NW;
+  out->n_mplanes = P.n_mplanes;
+  out->nfield = P.nfield;
+  out->nmat = P.nmat;
+  out->n_neutrals = P.n_neutrals;
+  out->capacity = P.cap;
+  out->arena_bytes = P.total;
+  return PIC_OK;
+}
+
+int pic_create(const pic_grid *grid, const pic_material *mat, const pic_pulse *pulse,
+               uint64_t seed, void *stream, void *d_arena, size_t arena_bytes, pic_handle *out) {
+  if (!out) return fail(PIC_EINVAL, "null handle pointer");
+  *out = nullptr;
+  pic_ctx *h = new pic_ctx();
+  int rc = validate_and_plan(grid, mat, pulse, h->P);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  h->seed = seed;
+  h->stream = (cudaStream_t)stream;
+  h->fp64 = h->P.g.precision == PIC_FP64;
+  h->lk = layer_constants(h->P);
+  if (d_arena) {
+    if (arena_bytes < h->P.total || ((uintptr_t)d_arena % kAlign)) {
+      delete h;
+      return fail(PIC_ENOMEM, "caller arena smaller than " + std::to_string(h->P.total) +
+                                  " bytes or not 256-byte aligned");
+    }
+    h->arena = (char *)d_arena;
+  } else {
+    cudaError_t e = cudaMalloc((void **)&h->arena, h->P.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(PIC_ENOMEM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+    }
+    h->own_arena = true;
+  }
+  bind<double>(h);
+  bind<float>(h);
+  rc = h->fp64 ? init_state<double>(h) : init_state<float>(h);
+  if (rc) {
+    if (h->own_arena) cudaFree(h->arena);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_profile(pic_handle h, int enable) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  h->profiling = enable != 0;
+  h->used = 0;
+  h->open_cls = -1;
+  return PIC_OK;
+}
+
+int pic_profile_read(pic_handle h, double ms[PIC_PROF_N], long long launches[PIC_PROF_N]) {
+  if (!h || !ms || !launches) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < PIC_PROF_N; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  for (size_t q = 0; q < h->used; ++q) {
+    float t = 0.f;
+    PIC_CUDA(cudaEventElapsedTime(&t, h->recs[q].a, h->recs[q].b));
+    ms[h->recs[q].cls] += t;
+    launches[h->recs[q].cls] += 1;
+  }
+  h->used = 0;
+  return PIC_OK;
+}
+
+int pic_destroy(pic_handle h) {
+  if (!h) return PIC_OK;
+  cudaStreamSynchronize(h->stream);
+  for (auto &r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (h->own_arena) cudaFree(h->arena);
+  delete h;
+  return PIC_OK;
+}
+
+int pic_step(pic_handle h, int n_steps) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  if (n_steps < 0) return fail(PIC_EINVAL, "negative step count");
+  if (h->sticky) return fail(h->sticky, "handle holds a device error");
+  for (int q = 0; q < n_steps; ++q) {
+    const int rc = enqueue_any(h, PIC_PHASE_ALL);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_step_phases(pic_handle h, int mask) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  if (mask & ~PIC_PHASE_ALL) return fail(PIC_EINVAL, "unknown phase bits");
+  if (h->sticky) return fail(h->sticky, "handle holds a device error");
+  return enqueue_any(h, mask);
+}
+
+int pic_sync(pic_handle h) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return check_sticky(h);
+}
+
+int pic_info_get(pic_handle h, pic_info *out) {
+  if (!h || !out) return fail(PIC_EINVAL, "null pointer");
+  const Plan &P = h->P;
+  std::memset(out, 0, sizeof(*out));
+  out->dt = P.dt;
+  out->E0 = P.E0;
+  out->NW = P.NW;
+  out->n_mplanes = P.n_mplanes;
+  out->nfield = P.nfield;
+  out->nmat = P.nmat;
+  out->n_neutrals = P.n_neutrals;
+  out->capacity = P.cap;
+  out->arena_bytes = P.total;
+  unsigned long long ns = 0;
+  const int rc = copy_out(h, P.off_nslots, &ns, 8);
+  if (rc) return rc;
+  out->n_particles = (long long)std::min<unsigned long long>(ns, P.cap);
+  out->step = h->step;
+  out->launches = h->launches;
+  double acc[5];
+  const int rc2 = copy_out(h, P.off_acc, acc, sizeof(acc));
+  if (rc2) return rc2;
+  out->particle_steps = acc[4];
+  return PIC_OK;
+}
+
+int pic_diagnostics(pic_handle h, pic_diag *dg) {
+  if (!h || !dg) return fail(PIC_EINVAL, "null pointer");
+  if (dg->n_bins < 0 || dg->n_bins > kSpecMax) return fail(PIC_EINVAL, "n_bins out of range");
+  if (dg->n_bins > 0 && (!dg->spectrum || !(dg->e_max_eV > dg->e_min_eV)))
+    return fail(PIC_EINVAL, "spectrum needs a buffer and e_max > e_min");
+  int rc = check_sticky(h);
+  if (rc) return rc;
+  const Plan &P = h->P;
+  cudaStream_t s = h->stream;
+  char *A = h->arena;
+  double *ne = (double *)(A + P.off_ne), *ed = (double *)(A + P.off_ed),
+         *rho = (double *)(A + P.off_rho), *spec = (double *)(A + P.off_spec),
+         *part = (double *)(A + P.off_part);
+  PIC_CUDA(cudaMemsetAsync(ne, 0, P.nfield * 8, s));
+  PIC_CUDA(cudaMemsetAsync(ed, 0, P.nfield * 8, s));
+  PIC_CUDA(cudaMemsetAsync(rho, 0, P.nfield * 8, s));
+  PIC_CUDA(cudaMemsetAsync(spec, 0, kSpecMax * 8, s));
+  const int4 r0 = make_int4(dg->region[0], dg->region[1], dg->region[2], dg->region[3]);
+  const int2 r1 = make_int2(dg->region[4], dg->region[5]);
+  std::vector<double> pp(3 * P.diag_blocks_p), pg5(5 * P.diag_blocks_g);
+  if (h->fp64) {
+    k_diag_particles<double><<<P.diag_blocks_p, kThreads, 0, s>>>(
+        h->c64, ne, ed, rho, spec, dg->n_bins, dg->e_min_eV, dg->e_max_eV, r0, r1, part);
+  } else {
+    k_diag_particles<float><<<P.diag_blocks_p, kThreads, 0, s>>>(
+        h->c32, ne, ed, rho, spec, dg->n_bins, dg->e_min_eV, dg->e_max_eV, r0, r1, part);
+  }
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaMemcpyAsync(pp.data(), part, pp.size() * 8, cudaMemcpyDeviceToHost, s));
+  PIC_CUDA(cudaStreamSynchronize(s));
+  if (h->fp64)
+    k_diag_grid<double><<<P.diag_blocks_g, kThreads, 0, s>>>(h->c64, ne, ed, rho, part);
+  else
+    k_diag_grid<float><<<P.diag_blocks_g, kThreads, 0, s>>>(h->c32, ne, ed, rho, part);
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaMemcpyAsync(pg5.data(), part, pg5.size() * 8, cudaMemcpyDeviceToHost, s));
+  double acc[4];
+  PIC_CUDA(cudaMemcpyAsync(acc, A + P.off_acc, 32, cudaMemcpyDeviceToHost, s));
+  if (dg->n_bins > 0)
+    PIC_CUDA(cudaMemcpyAsync(dg->spectrum, spec, dg->n_bins * 8, cudaMemcpyDeviceToHost, s));
+  PIC_CUDA(cudaStreamSynchronize(s));
+  double kin = 0, nel = 0, nho = 0;
+  for (int b = 0; b < P.diag_blocks_p; ++b) {
+    kin += pp[3 * b];
+    nel += pp[3 * b + 1];
+    nho += pp[3 * b + 2];
+  }
+  double uf = 0, mne = 0, med = 0, mrho = 0, mg = 0;
+  for (int b = 0; b < P.diag_blocks_g; ++b) {
+    uf += pg5[5 * b];
+    mne = std::max(mne, pg5[5 * b + 1]);
+    med = std::max(med, pg5[5 * b + 2]);
+    mrho = std::max(mrho, pg5[5 * b + 3]);
+    mg = std::max(mg, pg5[5 * b + 4]);
+  }
+  dg->U_incident = P.pulse.fluence * (P.g.nx * P.g.dx) * (P.g.ny * P.g.dy);
+  dg->U_kinetic = kin;
+  dg->U_ionization = acc[2];
+  dg->U_absorbed = kin + acc[2];
+  dg->frac_absorbed = dg->U_incident > 0 ? dg->U_absorbed / dg->U_incident : 0.0;
+  dg->U_joule = acc[0];
+  dg->U_field = uf * P.V;
+  dg->N_pairs = acc[1];
+  dg->n_e_peak = mne;
+  dg->energy_density_peak = med;
+  dg->gauss_residual_max = mg;
+  dg->rho_max = mrho;
+  dg->n_electrons_macro = nel;
+  dg->n_holes_macro = nho;
+  dg->step = h->step;
+  return PIC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// State access
+// ---------------------------------------------------------------------------
+namespace {
+template <class R>
+int get_fields_t(pic_ctx *h, double *dst) {
+  const Plan &P = h->P;
+  Ctx<R> &X = ctx_of<R>(h);
+  std::vector<char> raw(std::max(P.nfield, P.nmat) * sizeof(R));
+  R *const *arrs[3] = {X.d.E, X.d.B, X.d.J};
+  for (int g3 = 0; g3 < 3; ++g3)
+    for (int d = 0; d < 3; ++d) {
+      int rc = copy_out(h, off_of(h, arrs[g3][d]), raw.data(), P.nfield * sizeof(R));
+      if (rc) return rc;
+      to_double<R>(raw, P.nfield, dst + (size_t)(3 * g3 + d) * P.nfield);
+    }
+  std::vector<double> tmp(P.nmat);
+  R *const *pq[2] = {X.d.P, X.d.Q};
+  for (int g2 = 0; g2 < 2; ++g2)
+    for (int d = 0; d < 3; ++d) {
+      double *out = dst + (size_t)(9 + 3 * g2 + d) * P.nfield;
+      std::fill(out, out + P.nfield, 0.0);
+      if (!P.nmat) continue;
+      int rc = copy_out(h, off_of(h, pq[g2][d]), raw.data(), P.nmat * sizeof(R));
+      if (rc) return rc;
+      to_double<R>(raw, P.nmat, tmp.data());
+      for (int mp = 0; mp < P.n_mplanes; ++mp)
+        std::memcpy(out + (size_t)P.kplane[mp] * P.nxy, tmp.data() + (size_t)mp * P.nxy,
+                    P.nxy * sizeof(double));
+    }
+  return PIC_OK;
+}
+
+template <class R>
+int set_fields_t(pic_ctx *h, const double *src) {
+  const Plan &P = h->P;
+  Ctx<R> &X = ctx_of<R>(h);
+  std::vector<char> raw;
+  R *const *arrs[3] = {X.d.E, X.d.B, X.d.J};
+  for (int g3 = 0; g3 < 3; ++g3)
+    for (int d = 0; d < 3; ++d) {
+      from_double<R>(src + (size_t)(3 * g3 + d) * P.nfield, P.nfield, raw);
+      int rc = copy_in(h, off_of(h, arrs[g3][d]), raw.data(), raw.size());
+      if (rc) return rc;
+    }
+  std::vector<double> tmp(P.nmat);
+  R *const *pq[2] = {X.d.P, X.d.Q};
+  for (int g2 = 0; g2 < 2; ++g2)
+    for (int d = 0; d < 3; ++d) {
+      if (!P.nmat) continue;
+      const double *in = src + (size_t)(9 + 3 * g2 + d) * P.nfield;
+      for (int mp = 0; mp < P.n_mplanes; ++mp)
+        std::memcpy(tmp.data() + (size_t)mp * P.nxy, in + (size_t)P.kplane[mp] * P.nxy,
+                    P.nxy * sizeof(double));
+      from_double<R>(tmp.data(), P.nmat, raw);
+      int rc = copy_in(h, off_of(h, pq[g2][d]), raw.data(), raw.size());
+      if (rc) return rc;
+    }
+  return PIC_OK;
+}
+
+template <class R>
+int get_particles_t(pic_ctx *h, long long *n, uint64_t *id, int32_t *cell, double *off, double *u,
+                    uint32_t *tag) {
+  const Plan &P = h->P;
+  Ctx<R> &X = ctx_of<R>(h);
+  unsigned long long ns = 0;
+  int rc = copy_out(h, P.off_nslots, &ns, 8);
+  if (rc) return rc;
+  ns = std::min<unsigned long long>(ns, P.cap);
+  std::vector<int32_t> c(ns);
+  if (ns) {
+    rc = copy_out(h, off_of(h, X.d.pcell), c.data(), ns * 4);
+    if (rc) return rc;
+  }
+  long long live = 0;
+  for (unsigned long long q = 0; q < ns; ++q) live += c[q] >= 0;
+  *n = live;
+  if (!id || !cell || !off || !u || !tag) return PIC_OK;
+  std::vector<char> raw(std::max<size_t>(ns, 1) * sizeof(R));
+  std::vector<double> tmp(ns);
+  std::vector<double> o3(3 * ns), u3(3 * ns);
+  for (int d = 0; d < 3; ++d) {
+    if (!ns) break;
+    rc = copy_out(h, off_of(h, X.d.po[d]), raw.data(), ns * sizeof(R));
+    if (rc) return rc;
+    to_double<R>(raw, ns, tmp.data());
+    for (unsigned long long q = 0; q < ns; ++q) o3[3 * q + d] = tmp[q];
+    rc = copy_out(h, off_of(h, X.d.pu[d]), raw.data(), ns * sizeof(R));
+    if (rc) return rc;
+    to_double<R>(raw, ns, tmp.data());
+    for (unsigned long long q = 0; q < ns; ++q) u3[3 * q + d] = tmp[q];
+  }
+  std::vector<uint32_t> t(ns);
+  std::vector<unsigned long long> ids(ns);
+  if (ns) {
+    rc = copy_out(h, off_of(h, X.d.ptag), t.data(), ns * 4);
+    if (rc) return rc;
+    rc = copy_out(h, off_of(h, X.d.pid), ids.data(), ns * 8);
+    if (rc) return rc;
+  }
+  long long w = 0;
+  for (unsigned long long q = 0; q < ns; ++q) {
+    if (c[q] < 0) continue;
+    id[w] = ids[q];
+    cell[w] = c[q];
+    for (int d = 0; d < 3; ++d) {
+      off[3 * w + d] = o3[3 * q + d];
+      u[3 * w + d] = u3[3 * q + d];
+    }
+    tag[w] = t[q];
+    ++w;
+  }
+  return PIC_OK;
+}
+
+template <class R>
+int set_particles_t(pic_ctx *h, long long n, const uint64_t *id, const int32_t *cell,
+                    const double *off, const double *u, const uint32_t *tag) {
+  const Plan &P = h->P;
+  Ctx<R> &X = ctx_of<R>(h);
+  if (n < 0 || n > P.cap) return fail(PIC_EINVAL, "particle count exceeds the pool");
+  for (long long q = 0; q < n; ++q) {
+    if (cell[q] < 0 || cell[q] >= P.ncell) return fail(PIC_EINVAL, "particle cell out of range");
+    const int k = (int)(cell[q] / P.nxy);
+    if (k < 2 || k >= P.g.nz - 2) return fail(PIC_EINVAL, "particle inside the z outflow band");
+    if ((int)(tag[q] >> 1) >= (int)P.layers.size()) return fail(PIC_EINVAL, "tag names no layer");
+    for (int d = 0; d < 3; ++d)
+      if (!(off[3 * q + d] >= 0.0 && off[3 * q + d] < 1.0))
+        return fail(PIC_EINVAL, "particle offset outside [0, 1)");
+  }
+  std::vector<double> tmp(std::max<long long>(n, 1));
+  std::vector<char> raw;
+  int rc;
+  for (int d = 0; d < 3; ++d) {
+    for (long long q = 0; q < n; ++q) tmp[q] = off[3 * q + d];
+    from_double<R>(tmp.data(), n, raw);
+    if (n && (rc = copy_in(h, off_of(h, X.d.po[d]), raw.data(), raw.size()))) return rc;
+    for (long long q = 0; q < n; ++q) tmp[q] = u[3 * q + d];
+    from_double<R>(tmp.data(), n, raw);
+    if (n && (rc = copy_in(h, off_of(h, X.d.pu[d]), raw.data(), raw.size()))) return rc;
+  }
+  if (n) {
+    if ((rc = copy_in(h, off_of(h, X.d.pcell), cell, n * 4))) return rc;
+    if ((rc = copy_in(h, off_of(h, X.d.ptag), tag, n * 4))) return rc;
+    if ((rc = copy_in(h, off_of(h, X.d.pid), id, n * 8))) return rc;
+  }
+  unsigned long long ns = (unsigned long long)n;
+  return copy_in(h, P.off_nslots, &ns, 8);
+}
+
+template <class R>
+int get_material_t(pic_ctx *h, uint32_t *alive, double *eamp, uint64_t *T) {
+  const Plan &P = h->P;
+  if (!P.nmat) return PIC_OK;
+  int rc;
+  if (alive && (rc = copy_out(h, P.off_alive, alive, P.nmat * 4))) return rc;
+  if (T && (rc = copy_out(h, P.off_T, T, P.nmat * 8))) return rc;
+  if (eamp) {
+    std::vector<char> raw(P.nmat * sizeof(R));
+    if ((rc = copy_out(h, P.off_eamp, raw.data(), raw.size()))) return rc;
+    to_double<R>(raw, P.nmat, eamp);
+  }
+  return PIC_OK;
+}
+
+// Raw history -> block form: after sample t = step - 1 with position
+// s = t mod NW, slots 0..s keep this block's samples, slots above s the
+// suffix maxima of the previous block, pm the prefix max of this block.
+template <class R>
+int set_material_t(pic_ctx *h, const uint32_t *alive, const double *win) {
+  const Plan &P = h->P;
+  if (!P.nmat) return PIC_OK;
+  int rc;
+  if (alive && (rc = copy_in(h, P.off_alive, alive, P.nmat * 4))) return rc;
+  if (win) {
+    const int NW = P.NW;
+    std::vector<double> W(win, win + (size_t)NW * P.nmat), pm(P.nmat, 0.0);
+    if (h->step > 0) {
+      const int s = (int)((h->step - 1) % NW);
+      for (long long m = 0; m < P.nmat; ++m) {
+        double run = 0.0;
+        for (int q = NW - 1; q > s; --q) {
+          run = std::max(run, W[(size_t)q * P.nmat + m]);
+          W[(size_t)q * P.nmat + m] = run;
+        }
+        double pre = 0.0;
+        for (int q = 0; q <= s; ++q) pre = std::max(pre, W[(size_t)q * P.nmat + m]);
+        if (s == NW - 1) {
+          double r2 = 0.0;
+          for (int q = NW - 1; q >= 0; --q) {
+            r2 = std::max(r2, W[(size_t)q * P.nmat + m]);
+            W[(size_t)q * P.nmat + m] = r2;
+          }
+        }
+        pm[m] = pre;
+      }
+    }
+    std::vector<char> raw;
+    from_double<R>(W.data(), W.size(), raw);
+    if ((rc = copy_in(h, P.off_win, raw.data(), raw.size()))) return rc;
+    from_double<R>(pm.data(), pm.size(), raw);
+    if ((rc = copy_in(h, P.off_pm, raw.data(), raw.size()))) return rc;
+  }
+  // thresholds are recomputed at the next window phase
+  std::vector<double> inval(P.nmat, -1.0);
+  std::vector<char> raw;
+  from_double<R>(inval.data(), inval.size(), raw);
+  return copy_in(h, P.off_ckey, raw.data(), raw.size());
+}
+}  // namespace
+
+extern "C" {
+
+int pic_get_fields(pic_handle h, double *dst) {
+  if (!h || !dst) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? get_fields_t<double>(h, dst) : get_fields_t<float>(h, dst);
+}
+
+int pic_set_fields(pic_handle h, const double *src) {
+  if (!h || !src) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? set_fields_t<double>(h, src) : set_fields_t<float>(h, src);
+}
+
+int pic_get_particles(pic_handle h, long long *n, uint64_t *id, int32_t *cell, double *off,
+                      double *u, uint32_t *tag) {
+  if (!h || !n) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? get_particles_t<double>(h, n, id, cell, off, u, tag)
+                 : get_particles_t<float>(h, n, id, cell, off, u, tag);
+}
+
+int pic_set_particles(pic_handle h, long long n, const uint64_t *id, const int32_t *cell,
+                      const double *off, const double *u, const uint32_t *tag) {
+  if (!h || (n > 0 && (!id || !cell || !off || !u || !tag))) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? set_particles_t<double>(h, n, id, cell, off, u, tag)
+                 : set_particles_t<float>(h, n, id, cell, off, u, tag);
+}
+
+int pic_get_material(pic_handle h, uint32_t *alive, double *eamp, uint64_t *T) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? get_material_t<double>(h, alive, eamp, T) : get_material_t<float>(h, alive, eamp, T);
+}
+
+int pic_set_material(pic_handle h, const uint32_t *alive, const double *win) {
+  if (!h) return fail(PIC_EINVAL, "null handle");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  return h->fp64 ? set_material_t<double>(h, alive, win) : set_material_t<float>(h, alive, win);
+}
+
+int pic_get_scalars(pic_handle h, long long *step, double out[4]) {
+  if (!h || !out) return fail(PIC_EINVAL, "null pointer");
+  if (step) *step = h->step;
+  return copy_out(h, h->P.off_acc, out, 32);
+}
+
+int pic_set_scalars(pic_handle h, long long step, const double in[4]) {
+  if (!h || !in || step < 0) return fail(PIC_EINVAL, "bad arguments");
+  int rc = copy_in(h, h->P.off_acc, in, 32);
+  if (rc) return rc;
+  h->step = step;
+  return copy_in(h, h->P.off_step, &step, 8);
+}
+
+}  // extern "C"

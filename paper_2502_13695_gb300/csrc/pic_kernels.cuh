@@ -1,0 +1,907 @@
+// Kernels of one PIC step on sm_103a.  Every step of the hot path runs here:
+//   k_push      gather (TSC) + relativistic Boris + move + Esirkepov deposit
+//   k_bhalf     B half step (Faraday)
+//   k_efull     E step with the Lorentz polarisation current (trapezoidal
+//               oscillator), Silver-Mueller z faces with the laser source,
+//               Joule work, J cleared
+//   k_window    cell-centred |E|, exact sliding maximum over one optical
+//               cycle (van Herk / Gil-Werman blocks), Keldysh threshold with
+//               a per-cell cache and an exact low-field skip
+//   k_ionize    Philox draws per alive neutral, electron + hole appends
+//   k_hist / k_scan* / k_scatter   counting sort of the pool by cell
+//   k_diag_*    FP64 diagnostics
+#pragma once
+#include "pic_device.cuh"
+
+namespace pg {
+
+// Per-layer constants in the working precision (no double math in kernels).
+template <class R>
+struct LayerR {
+  R deps, cn_a, cn_b, cn_g, inv_den, two_over_h;  // trapezoidal oscillator
+  int is_static, ppc;
+  R qmdt2[2];   // q dt / (2 m)
+  R jpref[2][3];// -q w dl_d / (V dt) per species and axis
+  R kG, kX, kP, e_skip;
+  R sig_v;
+  R inv_mass_c2[2];
+};
+
+template <class R>
+struct Ctx {
+  Dev<R> d;
+  const LayerR<R> *lr;
+  // the other half of the double-buffered pool (sorting)
+  int32_t *acell;
+  R *ao[3], *au[3];
+  uint32_t *atag;
+  unsigned long long *aid;
+};
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class R>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double part[32];
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += part[q];
+  return tot;
+}
+
+
+template <class R>
+__device__ __forceinline__ void shape_int(R d, R w[3], int &b) {
+  const int s = d >= R(0.5);
+  const R e = d - R(s);
+  b = s - 1;
+  const R hm = R(0.5) - e, hp = R(0.5) + e;
+  w[0] = R(0.5) * hm * hm;
+  w[1] = R(0.75) - e * e;
+  w[2] = R(0.5) * hp * hp;
+}
+
+template <class R>
+__device__ __forceinline__ void shape_half(R d, R w[3]) {
+  const R e = d - R(0.5);
+  const R hm = R(0.5) - e, hp = R(0.5) + e;
+  w[0] = R(0.5) * hm * hm;
+  w[1] = R(0.75) - e * e;
+  w[2] = R(0.5) * hp * hp;
+}
+
+// sum_c wz[c] sum_b wy[b] sum_a wx[a] f[z_c, y_b, x_a]
+template <class R>
+__device__ __forceinline__ R gather27(const R *__restrict__ f, int nx, int ny, const int xs[3],
+                                      const int ys[3], const int zs[3], const R wx[3],
+                                      const R wy[3], const R wz[3]) {
+  R acc = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R accy = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R *row = f + ((long long)zs[c] * ny + ys[b]) * nx;
+      const R accx = wx[0] * __ldg(row + xs[0]) + wx[1] * __ldg(row + xs[1]) +
+                     wx[2] * __ldg(row + xs[2]);
+      accy += wy[b] * accx;
+    }
+    acc += wz[c] * accy;
+  }
+  return acc;
+}
+
+template <class R>
+__device__ __forceinline__ void atomic_add(R *p, R v) {
+  atomicAdd(p, v);
+}
+
+// Esirkepov deposit on a 4-node frame per axis (moves are below one cell).
+template <class R>
+__device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], const int co[3],
+                                          const R oo[3], const int cn[3], const R on[3]) {
+  R S0[3][4], DS[3][4], A[3][4];
+  int base[3], nn[3], nf[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R wo[3], wn[3];
+    int bo, bn;
+    shape_int(oo[d], wo, bo);
+    shape_int(on[d], wn, bn);
+    const int i0o = co[d] + bo + 1, i0n = cn[d] + bn + 1;
+    const int s = i0n - i0o;
+    const int fo = s < 0 ? 1 : 0, fn = s > 0 ? 1 : 0;
+    base[d] = i0o - 1 - fo;
+    nn[d] = 3 + (s != 0);
+    nf[d] = 2 + (s != 0);
+    R S1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      S0[d][q] = R(0);
+      S1[q] = R(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      S0[d][q + fo] = wo[q];
+      S1[q + fn] = wn[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      DS[d][q] = S1[q] - S0[d][q];
+      A[d][q] = S0[d][q] + R(0.5) * DS[d][q];
+    }
+  }
+  const int nx = D.nx, ny = D.ny;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int e = (d + 1) % 3, f = (d + 2) % 3;
+    R *__restrict__ J = D.J[d];
+    for (int b = 0; b < nn[e]; ++b)
+      for (int c = 0; c < nn[f]; ++c) {
+        const R M = A[e][b] * A[f][c] + DS[e][b] * DS[f][c] * R(1.0 / 12.0);
+        if (M == R(0)) continue;
+        R run = R(0);
+        for (int a = 0; a < nf[d]; ++a) {
+          run += DS[d][a];
+          const R v = jpref[d] * run * M;
+          if (v == R(0)) continue;
+          int id3[3];
+          id3[d] = base[d] + a;
+          id3[e] = base[e] + b;
+          id3[f] = base[f] + c;
+          const long long o = ((long long)id3[2] * ny + wrap(id3[1], ny)) * nx + wrap(id3[0], nx);
+          atomic_add(J + o, v);
+        }
+      }
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_push(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const unsigned long long n = min(*D.nslots, D.cap);
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const R dl_inv[3] = {D.idx, D.idy, D.idz};
+  const R c2inv = R(1.0 / (kC * kC));
+  double pushed = 0.0;
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    const int cell = D.pcell[p];
+    if (cell < 0) continue;
+    pushed += 1.0;
+    const int ci = cell % nx, t = cell / nx, cj = t % ny, ck = t / ny;
+    R off[3] = {D.po[0][p], D.po[1][p], D.po[2][p]};
+    R u[3] = {D.pu[0][p], D.pu[1][p], D.pu[2][p]};
+    const uint32_t tag = D.ptag[p];
+    const LayerR<R> &L = X.lr[tag >> 1];
+    const int sp = tag & 1u;
+    // shapes: integer grid (weights + node indices) and half-integer grid
+    R wi[3][3], wh[3][3];
+    int xi[3], xh[3], yi[3], yh[3], zi[3], zh[3];
+    {
+      int b;
+      shape_int(off[0], wi[0], b);
+      shape_half(off[0], wh[0]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        xi[a] = wrap(ci + b + a, nx);
+        xh[a] = wrap(ci - 1 + a, nx);
+      }
+      shape_int(off[1], wi[1], b);
+      shape_half(off[1], wh[1]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        yi[a] = wrap(cj + b + a, ny);
+        yh[a] = wrap(cj - 1 + a, ny);
+      }
+      shape_int(off[2], wi[2], b);
+      shape_half(off[2], wh[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        zi[a] = ck + b + a;
+        zh[a] = ck - 1 + a;
+      }
+    }
+    const R Ex = gather27(D.E[0], nx, ny, xh, yi, zi, wh[0], wi[1], wi[2]);
+    const R Ey = gather27(D.E[1], nx, ny, xi, yh, zi, wi[0], wh[1], wi[2]);
+    const R Ez = gather27(D.E[2], nx, ny, xi, yi, zh, wi[0], wi[1], wh[2]);
+    const R Bx = gather27(D.B[0], nx, ny, xi, yh, zh, wi[0], wh[1], wh[2]);
+    const R By = gather27(D.B[1], nx, ny, xh, yi, zh, wh[0], wi[1], wh[2]);
+    const R Bz = gather27(D.B[2], nx, ny, xh, yh, zi, wh[0], wh[1], wi[2]);
+    // relativistic Boris rotation between two half electric kicks
+    const R h = L.qmdt2[sp];
+    R um[3] = {u[0] + h * Ex, u[1] + h * Ey, u[2] + h * Ez};
+    const R gm = sqrt(R(1) + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) * c2inv);
+    const R hg = h / gm;
+    const R tv[3] = {hg * Bx, hg * By, hg * Bz};
+    const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+    const R sf = R(2) / (R(1) + t2);
+    const R sv[3] = {sf * tv[0], sf * tv[1], sf * tv[2]};
+    const R up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]), um[1] + (um[2] * tv[0] - um[0] * tv[2]),
+                     um[2] + (um[0] * tv[1] - um[1] * tv[0])};
+    u[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + h * Ex;
+    u[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + h * Ey;
+    u[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * Ez;
+    const R g = sqrt(R(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * c2inv);
+    const R dtg = D.dt / g;
+    const int co[3] = {ci, cj, ck};
+    int cn[3];
+    R on[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R nd = off[d] + dtg * u[d] * dl_inv[d];
+      int cc = co[d];
+      if (nd < R(0)) {
+        nd += R(1);
+        cc -= 1;
+      }
+      if (nd >= R(1)) {
+        nd -= R(1);
+        cc += 1;
+      }
+      cn[d] = cc;
+      on[d] = nd;
+    }
+    esirkepov(D, L.jpref[sp], co, off, cn, on);
+    if (cn[2] < 2 || cn[2] >= nz - 2) {
+      D.pcell[p] = -1;  // outflow through a z face
+      continue;
+    }
+    D.pcell[p] = (cn[2] * ny + wrap(cn[1], ny)) * nx + wrap(cn[0], nx);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      D.po[d][p] = on[d];
+      D.pu[d][p] = u[d];
+    }
+  }
+  const double tot = block_sum<R>(pushed);
+  if (threadIdx.x == 0 && tot != 0.0) atomicAdd(D.acc + 4, tot);
+}
+
+// ---------------------------------------------------------------------------
+// Fields
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= D.nfield) return;
+  const int nx = D.nx, nxy = D.nxy;
+  const int k = (int)(o / nxy);
+  const int r = (int)(o - (long long)k * nxy);
+  const int j = r / nx, i = r - j * nx;
+  const long long oi = (i == nx - 1) ? o - (nx - 1) : o + 1;
+  const long long oj = (j == D.ny - 1) ? o - (long long)(D.ny - 1) * nx : o + nx;
+  const R h = R(0.5) * D.dt;
+  const R *Ex = D.E[0], *Ey = D.E[1], *Ez = D.E[2];
+  if (k < D.nz) {
+    const R ez = Ez[o], ey = Ey[o], ex = Ex[o];
+    D.B[0][o] -= h * ((Ez[oj] - ez) * D.idy - (Ey[o + nxy] - ey) * D.idz);
+    D.B[1][o] -= h * ((Ex[o + nxy] - ex) * D.idz - (Ez[oi] - ez) * D.idx);
+  }
+  D.B[2][o] -= h * ((Ey[oi] - Ey[o]) * D.idx - (Ex[oj] - Ex[o]) * D.idy);
+}
+
+template <class R>
+__device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) {
+  R dp;
+  if (L.is_static) {
+    dp = (R(2) * (L.deps * e0 - p) + L.deps * a) * L.inv_den;
+    q = R(0);
+  } else {
+    // trapezoidal oscillator coupled implicitly to E^{n+1}
+    dp = (L.cn_g * q + L.cn_a * (L.deps * e0 - p) + L.cn_b * a) * L.inv_den;
+    q = L.two_over_h * dp - q;
+  }
+  p += dp;
+  return e0 + a - dp;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double joule = 0.0;
+  if (o < D.nfield) {
+    const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
+    const int k = (int)(o / nxy);
+    const int r = (int)(o - (long long)k * nxy);
+    const int j = r / nx, i = r - j * nx;
+    const long long omi = (i == 0) ? o + (nx - 1) : o - 1;
+    const long long omj = (j == 0) ? o + (long long)(ny - 1) * nx : o - nx;
+    const R *Bx = D.B[0], *By = D.B[1], *Bz = D.B[2];
+    const R c2dt = D.c2dt, dtie = R(D.dt_d / kEps0);
+    const R bz = Bz[o];
+    const R dBz_dy = (bz - Bz[omj]) * D.idy;
+    const R dBz_dx = (bz - Bz[omi]) * D.idx;
+    const R jx = D.J[0][o], jy = D.J[1][o];
+    const R ex0 = D.E[0][o], ey0 = D.E[1][o];
+    R ex1, ey1;
+    const int L = k < nz ? D.layer_of_plane[k] : -1;
+    const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
+    if (k == 0 || k == nz) {
+      const R al = D.alpha, cc = R(kC);
+      const R inv = R(1) / (R(1) + al);
+      if (k == 0) {
+        // incident field at t^{n+1/2}, computed in double
+        const double t = ((double)(*D.step) + 0.5) * D.dt_d - D.t_peak;
+        const double env = exp(-2.0 * 0.69314718055994531 * t * t / (D.fwhm * D.fwhm));
+        const double einc = D.E0 * env * cos(D.omega * t + D.cep);
+        const R exi = D.pol == 0 ? R(einc) : R(0), eyi = D.pol == 0 ? R(0) : R(einc);
+        ex1 = ((R(1) - al) * ex0 - R(2) * al * cc * By[o] + R(4) * al * exi +
+               (c2dt * dBz_dy - dtie * jx)) * inv;
+        ey1 = ((R(1) - al) * ey0 + R(2) * al * cc * Bx[o] + R(4) * al * eyi -
+               (c2dt * dBz_dx + dtie * jy)) * inv;
+      } else {
+        const long long om = o - nxy;
+        ex1 = ((R(1) - al) * ex0 + R(2) * al * cc * By[om] + (c2dt * dBz_dy - dtie * jx)) * inv;
+        ey1 = ((R(1) - al) * ey0 - R(2) * al * cc * Bx[om] - (c2dt * dBz_dx + dtie * jy)) * inv;
+      }
+    } else {
+      const long long om = o - nxy;
+      const R ax = c2dt * (dBz_dy - (By[o] - By[om]) * D.idz) - dtie * jx;
+      const R ay = c2dt * ((Bx[o] - Bx[om]) * D.idz - dBz_dx) - dtie * jy;
+      if (m >= 0) {
+        const LayerR<R> &Ly = X.lr[L];
+        R px = D.P[0][m], qx = D.Q[0][m], py = D.P[1][m], qy = D.Q[1][m];
+        ex1 = e_point(Ly, ex0, ax, px, qx);
+        ey1 = e_point(Ly, ey0, ay, py, qy);
+        D.P[0][m] = px;
+        D.Q[0][m] = qx;
+        D.P[1][m] = py;
+        D.Q[1][m] = qy;
+      } else {
+        ex1 = ex0 + ax;
+        ey1 = ey0 + ay;
+      }
+    }
+    joule += (double)(jx * R(0.5) * (ex0 + ex1)) + (double)(jy * R(0.5) * (ey0 + ey1));
+    D.E[0][o] = ex1;
+    D.E[1][o] = ey1;
+    D.J[0][o] = R(0);
+    D.J[1][o] = R(0);
+    if (k < nz) {
+      const R jz = D.J[2][o];
+      const R az = c2dt * ((By[o] - By[omi]) * D.idx - (Bx[o] - Bx[omj]) * D.idy) - dtie * jz;
+      const R ez0 = D.E[2][o];
+      R ez1;
+      if (m >= 0) {
+        R pz = D.P[2][m], qz = D.Q[2][m];
+        ez1 = e_point(X.lr[L], ez0, az, pz, qz);
+        D.P[2][m] = pz;
+        D.Q[2][m] = qz;
+      } else {
+        ez1 = ez0 + az;
+      }
+      joule += (double)(jz * R(0.5) * (ez0 + ez1));
+      D.E[2][o] = ez1;
+      D.J[2][o] = R(0);
+    }
+  }
+  const double tot = block_sum<R>(joule);
+  if (threadIdx.x == 0 && tot != 0.0) atomicAdd(D.acc + 0, tot * D.dt_d * D.V_d);
+}
+
+// ---------------------------------------------------------------------------
+// Amplitude window + Keldysh threshold, one thread per material cell
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= D.nmat) return;
+  const int nx = D.nx, ny = D.ny, nxy = D.nxy;
+  const int mp = (int)(m / nxy);
+  const int r = (int)(m - (long long)mp * nxy);
+  const int j = r / nx, i = r - j * nx;
+  const int k = D.kplane[mp];
+  const long long o = (long long)k * nxy + r;
+  const long long oi = (i == nx - 1) ? o - (nx - 1) : o + 1;
+  const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
+  const long long oij = (j == ny - 1) ? oi - (long long)(ny - 1) * nx : oi + nx;
+  const R *Ex = D.E[0], *Ey = D.E[1], *Ez = D.E[2];
+  const R ax = R(0.25) * (((Ex[o] + Ex[oj]) + Ex[o + nxy]) + Ex[oj + nxy]);
+  const R ay = R(0.25) * (((Ey[o] + Ey[oi]) + Ey[o + nxy]) + Ey[oi + nxy]);
+  const R az = R(0.25) * (((Ez[o] + Ez[oi]) + Ez[oj]) + Ez[oij]);
+  const R a = sqrt(ax * ax + ay * ay + az * az);
+  // sliding maximum: slots <= s hold this block's samples, slots > s the
+  // suffix maxima of the previous block; pm is the running block prefix max
+  const int NW = D.NW;
+  const int s = (int)(*D.step % NW);
+  R *__restrict__ W = D.win + m;
+  const long long st = D.nmat;
+  W[s * st] = a;
+  const R pm = s == 0 ? a : fmax(D.pm[m], a);
+  D.pm[m] = pm;
+  const R amp = s + 1 < NW ? fmax(pm, W[(s + 1) * st]) : pm;
+  if (s == NW - 1) {
+    R run = W[(NW - 1) * st];
+    for (int q = NW - 2; q >= 0; --q) {
+      run = fmax(run, W[q * st]);
+      W[q * st] = run;
+    }
+  }
+  D.eamp[m] = amp;
+  const LayerR<R> &L = X.lr[D.layer_of_plane[k]];
+  unsigned long long T;
+  if (!(amp >= L.e_skip)) {
+    T = 0ull;
+  } else if (D.ckey[m] == amp) {
+    return;  // threshold cached for this exact amplitude
+  } else {
+    T = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms);
+  }
+  if (D.T[m] != T) D.T[m] = T;
+  D.ckey[m] = amp;
+}
+
+// ---------------------------------------------------------------------------
+// Ionisation: one thread per material (birth) cell.  A neutral is force-free,
+// at x0 + v0 t with x0, v0 regenerated from Philox; it is drawn against the
+// threshold of the cell it occupies at t^{n+1}.  Until leave_step no neutral
+// of the cell can have crossed a face (|v0| < 7 sigma bounds Box-Muller), so
+// the birth cell's threshold decides without regenerating any state.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Neutral {
+  int cell[3];
+  R off[3];
+  R u[3];
+};
+
+template <class R>
+__device__ __forceinline__ void neutral_pos(const Dev<R> &D, uint32_t c, uint32_t s, R off0[3]) {
+  const uint4 w = draw(D.seed, 0u, c, s, kStreamPos);
+  const R top = R(1) - Eps<R>::v();
+  off0[0] = fmin(unit_open<R>(w.x), top);
+  off0[1] = fmin(unit_open<R>(w.y), top);
+  off0[2] = fmin(unit_open<R>(w.z), top);
+}
+
+template <class R>
+__device__ __forceinline__ void neutral_vel(const Dev<R> &D, R sig, uint32_t c, uint32_t s, R v[3]) {
+  const uint4 w = draw(D.seed, 0u, c, s, kStreamVel);
+  const R r1 = sqrt(R(-2) * log(unit_open<R>(w.x)));
+  const R r2 = sqrt(R(-2) * log(unit_open<R>(w.z)));
+  R s1, c1, s2, c2;
+  sincospi(R(2) * unit_open<R>(w.y), &s1, &c1);
+  sincospi(R(2) * unit_open<R>(w.w), &s2, &c2);
+  v[0] = sig * r1 * c1;
+  v[1] = sig * r1 * s1;
+  v[2] = sig * r2 * c2;
+}
+
+// Position at time t of neutral (c, s) born in cell (i, j, k); false if it
+// left the grid along z.
+template <class R>
+__device__ __forceinline__ bool neutral_at(const Dev<R> &D, R sig, int i, int j, int k, uint32_t c,
+                                           uint32_t s, R t, Neutral<R> &nu) {
+  R off0[3], v[3];
+  neutral_pos(D, c, s, off0);
+  neutral_vel(D, sig, c, s, v);
+  const R il[3] = {D.idx, D.idy, D.idz};
+  int cc[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R nd = off0[d] + v[d] * t * il[d];
+    if (nd < R(0)) {
+      nd += R(1);
+      cc[d] -= 1;
+    }
+    if (nd >= R(1)) {
+      nd -= R(1);
+      cc[d] += 1;
+    }
+    nu.off[d] = nd;
+  }
+  nu.cell[0] = wrap(cc[0], D.nx);
+  nu.cell[1] = wrap(cc[1], D.ny);
+  nu.cell[2] = cc[2];
+  const R v2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * R(1.0 / (kC * kC));
+  const R gm = R(1) / sqrt(R(1) - v2);
+  nu.u[0] = gm * v[0];
+  nu.u[1] = gm * v[1];
+  nu.u[2] = gm * v[2];
+  return cc[2] >= 0 && cc[2] < D.nz;
+}
+
+template <class R>
+__device__ __forceinline__ unsigned long long threshold_at(const Dev<R> &D, int i, int j, int k) {
+  if (k < 0 || k >= D.nz) return 0ull;
+  const int mp = D.mplane[k];
+  if (mp < 0) return 0ull;
+  return D.T[(long long)mp * D.nxy + (long long)j * D.nx + i];
+}
+
+__device__ __forceinline__ bool ionises(unsigned long long r64, unsigned long long T) {
+  return T == ~0ull || r64 < T;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool active = m < D.nmat;
+  const long long step = *D.step;
+  uint32_t alive = 0, ion = 0;
+  int i = 0, j = 0, k = 0, L = 0;
+  uint32_t c = 0;
+  R t1 = R(0);
+  bool fast = true;
+  if (active) alive = D.alive[m];
+  if (alive) {
+    const int nx = D.nx, nxy = D.nxy;
+    const int mp = (int)(m / nxy);
+    const int r = (int)(m - (long long)mp * nxy);
+    j = r / nx;
+    i = r - j * nx;
+    k = D.kplane[mp];
+    L = D.layer_of_plane[k];
+    c = (uint32_t)((long long)k * nxy + r);
+    t1 = R((double)(step + 1) * D.dt_d);
+    fast = (unsigned long long)(step + 1) < (unsigned long long)D.leave_step[m];
+    const unsigned long long Town = D.T[m];
+    if (fast && Town == 0ull) alive = 0;
+    const R sig = X.lr[L].sig_v;
+    for (uint32_t bits = alive; bits; bits &= bits - 1) {
+      const uint32_t s = __ffs(bits) - 1;
+      unsigned long long Tuse = Town;
+      if (!fast) {
+        Neutral<R> nu;
+        Tuse = neutral_at(D, sig, i, j, k, c, s, t1, nu)
+                   ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+                   : 0ull;
+      }
+      if (Tuse == 0ull) continue;
+      const uint4 w = draw(D.seed, (uint32_t)step, c, s, kStreamIon);
+      const unsigned long long r64 = ((unsigned long long)w.y << 32) | w.x;
+      if (ionises(r64, Tuse)) ion |= 1u << s;
+    }
+  }
+  // warp-aggregated reservation of pool slots
+  const int npair = __popc(ion);
+  int incl = npair;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, sft);
+    if (lane >= sft) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long basew = 0;
+  if (lane == 31 && total) basew = atomicAdd(D.nslots, 2ull * (unsigned long long)total);
+  basew = __shfl_sync(0xffffffffu, basew, 31);
+  if (!npair) return;
+  unsigned long long slot = basew + 2ull * (unsigned long long)(incl - npair);
+  const LayerR<R> &Ly = X.lr[L];
+  const int ppc = Ly.ppc;
+  uint32_t done = 0;
+  for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
+    const uint32_t s = __ffs(bits) - 1;
+    if (slot + 1 >= D.cap) {
+      atomicOr(D.err, kErrPool);
+      break;
+    }
+    Neutral<R> nu;
+    neutral_at(D, Ly.sig_v, i, j, k, c, s, t1, nu);
+    const int ncell = (nu.cell[2] * D.ny + nu.cell[1]) * D.nx + nu.cell[0];
+    const unsigned long long gid = (unsigned long long)c * ppc + s;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      const unsigned long long q = slot + sp;
+      D.pid[q] = 2ull * gid + sp;
+      D.pcell[q] = ncell;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        D.po[d][q] = nu.off[d];
+        D.pu[d][q] = nu.u[d];
+      }
+      D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
+    }
+    done |= 1u << s;
+  }
+  D.alive[m] = alive & ~done;
+  const double nd = (double)__popc(done);
+  const LayerK &LK = D.layers[L];
+  atomicAdd(D.acc + 1, nd * LK.wmac);
+  atomicAdd(D.acc + 2, nd * LK.wmac * LK.gapJ);
+  atomicAdd(D.acc + 3, nd);
+}
+
+// First step index at which any neutral of a cell could have left it.
+template <class R>
+__global__ void k_init_material(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= D.nmat) return;
+  const int nx = D.nx, nxy = D.nxy;
+  const int mp = (int)(m / nxy);
+  const int r = (int)(m - (long long)mp * nxy);
+  const int k = D.kplane[mp];
+  const LayerK &L = D.layers[D.layer_of_plane[k]];
+  const uint32_t c = (uint32_t)((long long)k * nxy + r);
+  const int ppc = L.ppc;
+  D.alive[m] = ppc >= 32 ? 0xFFFFFFFFu : ((1u << ppc) - 1u);
+  double tmin = 1e300;
+  const double dl[3] = {D.dx_d, D.dy_d, D.dz_d};
+  for (int s = 0; s < ppc; ++s) {
+    const uint4 w = draw(D.seed, 0u, c, (uint32_t)s, kStreamPos);
+    const double o3[3] = {unit_open<double>(w.x), unit_open<double>(w.y), unit_open<double>(w.z)};
+    for (int d = 0; d < 3; ++d) tmin = fmin(tmin, fmin(o3[d], 1.0 - o3[d]) * dl[d]);
+  }
+  const double vmax = 7.0 * L.sigv;
+  double steps = vmax > 0.0 ? floor(tmin / vmax / D.dt_d) : 4e9;
+  D.leave_step[m] = steps >= 4e9 ? 0xFFFFFFFFu : (uint32_t)steps;
+  D.pm[m] = R(0);
+  D.eamp[m] = R(0);
+  D.ckey[m] = R(-1);
+  D.T[m] = 0ull;
+  (void)nx;
+}
+
+__global__ void k_advance(long long *step) { *step += 1; }
+
+// ---------------------------------------------------------------------------
+// Counting sort of the pool by cell (dead slots dropped)
+// ---------------------------------------------------------------------------
+__global__ void k_hist(const int32_t *__restrict__ cell, const unsigned long long *nslots,
+                       unsigned long long cap, unsigned int *cnt) {
+  const unsigned long long n = min(*nslots, cap);
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    const int c = cell[p];
+    if (c >= 0) atomicAdd(cnt + c, 1u);
+  }
+}
+
+constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int &total) {
+  __shared__ unsigned int warp_tot[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned int incl = v;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += t;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned int x = lane < nw ? warp_tot[lane] : 0u;
+    unsigned int xi = x;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, xi, s);
+      if (lane >= s) xi += t;
+    }
+    if (lane < nw) warp_tot[lane] = xi - x;
+    if (lane == nw - 1) warp_tot[31] = xi;
+  }
+  __syncthreads();
+  const unsigned int excl = warp_tot[w] + incl - v;
+  total = warp_tot[31];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const unsigned int *cnt, long long n,
+                                                               unsigned int *bsum) {
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  unsigned int s = 0;
+  for (int q = 0; q < kScanItems; ++q) {
+    const long long idx = base + (long long)q * kScanThreads + threadIdx.x;
+    if (idx < n) s += cnt[idx];
+  }
+  unsigned int tot;
+  block_excl_scan(s, tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(unsigned int *bsum, int nb,
+                                                               unsigned long long *total_out) {
+  unsigned int carry = 0;
+  for (int base = 0; base < nb; base += kScanThreads) {
+    const int idx = base + threadIdx.x;
+    const unsigned int v = idx < nb ? bsum[idx] : 0u;
+    unsigned int tot;
+    const unsigned int ex = block_excl_scan(v, tot);
+    if (idx < nb) bsum[idx] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, long long n,
+                                                              const unsigned int *bsum) {
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  unsigned int v[kScanItems];
+  unsigned int s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = base + q < n ? cnt[base + q] : 0u;
+    s += v[q];
+  }
+  unsigned int tot;
+  unsigned int ex = block_excl_scan(s, tot) + bsum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    if (base + q < n) cnt[base + q] = ex;
+    ex += v[q];
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor) {
+  const Dev<R> &D = X.d;
+  const unsigned long long n = min(*D.nslots, D.cap);
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    const int c = D.pcell[p];
+    if (c < 0) continue;
+    const unsigned int q = atomicAdd(cursor + c, 1u);
+    X.acell[q] = c;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      X.ao[d][q] = D.po[d][p];
+      X.au[d][q] = D.pu[d][p];
+    }
+    X.atag[q] = D.ptag[p];
+    X.aid[q] = D.pid[p];
+  }
+}
+
+__global__ void k_set_slots(unsigned long long *nslots, const unsigned long long *total) {
+  *nslots = *total;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (FP64): per-particle deposits and sums, per-node reductions.
+// Block partials are reduced on the host in a fixed order.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(256) k_diag_particles(Ctx<R> X, double *ne, double *ed,
+                                                         double *rho, double *spec, int nbins,
+                                                         double emin, double emax, int4 r0,
+                                                         int2 r1, double *partials) {
+  const Dev<R> &D = X.d;
+  const unsigned long long n = min(*D.nslots, D.cap);
+  const int nx = D.nx, ny = D.ny;
+  double kin = 0.0, nel = 0.0, nho = 0.0;
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    const int cell = D.pcell[p];
+    if (cell < 0) continue;
+    const int ci = cell % nx, t = cell / nx, cj = t % ny, ck = t / ny;
+    const uint32_t tag = D.ptag[p];
+    const LayerK &L = D.layers[tag >> 1];
+    const int sp = tag & 1u;
+    const double ux = D.pu[0][p], uy = D.pu[1][p], uz = D.pu[2][p];
+    const double g = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double ek = (g - 1.0) * L.mass[sp] * kC * kC;
+    kin += L.wmac * ek;
+    const double q = (sp ? kQe : -kQe) * L.wmac / D.V_d;
+    double w[3][3];
+    int b[3];
+    const double o3[3] = {(double)D.po[0][p], (double)D.po[1][p], (double)D.po[2][p]};
+    for (int d = 0; d < 3; ++d) {
+      const int s = o3[d] >= 0.5;
+      const double e = o3[d] - s;
+      b[d] = s - 1;
+      w[d][0] = 0.5 * (0.5 - e) * (0.5 - e);
+      w[d][1] = 0.75 - e * e;
+      w[d][2] = 0.5 * (0.5 + e) * (0.5 + e);
+    }
+    const bool el = sp == 0;
+    const double vne = L.wmac / D.V_d, ved = L.wmac * ek / D.V_d;
+    for (int c = 0; c < 3; ++c)
+      for (int bb = 0; bb < 3; ++bb)
+        for (int a = 0; a < 3; ++a) {
+          const long long o = ((long long)(ck + b[2] + c) * ny + wrap(cj + b[1] + bb, ny)) * nx +
+                              wrap(ci + b[0] + a, nx);
+          const double wt = w[0][a] * w[1][bb] * w[2][c];
+          atomicAdd(rho + o, q * wt);
+          if (el) {
+            atomicAdd(ne + o, vne * wt);
+            atomicAdd(ed + o, ved * wt);
+          }
+        }
+    if (el) {
+      nel += 1.0;
+      if (nbins > 0 && ci >= r0.x && ci < r0.y && cj >= r0.z && cj < r0.w && ck >= r1.x &&
+          ck < r1.y) {
+        const double ev = ek / kQe;
+        if (ev >= emin && ev < emax) {
+          const int bin = (int)floor((ev - emin) / (emax - emin) * nbins);
+          if (bin >= 0 && bin < nbins) atomicAdd(spec + bin, L.wmac);
+        }
+      }
+    } else {
+      nho += 1.0;
+    }
+  }
+  const double a = block_sum<R>(kin);
+  __syncthreads();
+  const double bq = block_sum<R>(nel);
+  __syncthreads();
+  const double cq = block_sum<R>(nho);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = a;
+    partials[3 * blockIdx.x + 1] = bq;
+    partials[3 * blockIdx.x + 2] = cq;
+  }
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double part[32];
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, s));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot = fmax(tot, part[q]);
+  return tot;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_diag_grid(Ctx<R> X, const double *ne, const double *ed,
+                                                    const double *rho, double *partials) {
+  const Dev<R> &D = X.d;
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double uf = 0.0, mne = 0.0, med = 0.0, mrho = 0.0, mg = 0.0;
+  if (o < D.nfield) {
+    const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
+    const int k = (int)(o / nxy);
+    const int r = (int)(o - (long long)k * nxy);
+    const int j = r / nx, i = r - j * nx;
+    for (int d = 0; d < 3; ++d) {
+      const double e = D.E[d][o], b = D.B[d][o];
+      uf += 0.5 * kEps0 * e * e + 0.5 * b * b / kMu0;
+    }
+    mne = ne[o];
+    med = ed[o];
+    mrho = fabs(rho[o]);
+    if (k >= 4 && k <= nz - 4) {
+      const long long omi = (i == 0) ? o + (nx - 1) : o - 1;
+      const long long omj = (j == 0) ? o + (long long)(ny - 1) * nx : o - nx;
+      const long long omk = o - nxy;
+      auto pol = [&](int d, long long oo, int kk) -> double {
+        const int mp = D.mplane[kk];
+        if (mp < 0) return 0.0;
+        return (double)D.P[d][(long long)mp * nxy + (oo - (long long)kk * nxy)];
+      };
+      const double dxv = ((double)D.E[0][o] + pol(0, o, k)) - ((double)D.E[0][omi] + pol(0, omi, k));
+      const double dyv = ((double)D.E[1][o] + pol(1, o, k)) - ((double)D.E[1][omj] + pol(1, omj, k));
+      const double dzv =
+          ((double)D.E[2][o] + pol(2, o, k)) - ((double)D.E[2][omk] + pol(2, omk, k - 1));
+      const double div = dxv / D.dx_d + dyv / D.dy_d + dzv / D.dz_d;
+      mg = fabs(kEps0 * div - rho[o]);
+    }
+  }
+  const double v0 = block_sum<R>(uf);
+  __syncthreads();
+  const double v1 = block_max(mne);
+  __syncthreads();
+  const double v2 = block_max(med);
+  __syncthreads();
+  const double v3 = block_max(mrho);
+  __syncthreads();
+  const double v4 = block_max(mg);
+  if (threadIdx.x == 0) {
+    double *p = partials + 5 * blockIdx.x;
+    p[0] = v0;
+    p[1] = v1;
+    p[2] = v2;
+    p[3] = v3;
+    p[4] = v4;
+  }
+}
+
+}  // namespace pg

@@ -1,0 +1,200 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on seeded synthetic inputs.
+
+FP64 mode: rel-L2 <= 1e-12 per field component per step, identical
+ionisation decisions (alive bits and particle ids), particle positions and
+momenta to roundoff.  FP32 mode: rel-L2 <= 2e-5 per step against the oracle
+stepping the same state, decision flips bounded by the probability mass that
+FP32 rounding can move.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2502_13695_gb300 import workloads as wl
+from parity_util import (assert_fields_close, assert_particles_close, field_errors,
+                         oracle_state_for_gpu, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def pic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2502_13695_gb300 import build, pic as picmod
+    build.build()
+    return picmod
+
+
+def _pair(pic, oracle_mod, cfg):
+    return pic.Simulation(cfg), oracle_mod.Sim(cfg)
+
+
+def test_particle_pass_fp64(pic, oracle_mod):
+    cfg = wl.grid(12, 10, 24, 25e-9, [wl.layer(8, 16, wl.SILICA, 2, 0.0)],
+                  wl.pulse(5e-15, 1.0, 6e-15), seed=3, precision="fp64")
+    g, o = _pair(pic, oracle_mod, cfg)
+    F = wl.random_fields(cfg, seed=5, e_amp=3e10, b_amp=100.0)
+    P = wl.random_particles(cfg, 3000, seed=9, u_max=2.5e8, z_margin=2)
+    for s in (g, o):
+        s.set_fields(F)
+        s.set_particles(P)
+    g.phases(1)
+    o.phases(1)
+    Fg, Fo = g.fields(), o.fields()
+    assert_fields_close(Fg, Fo, TOL64, comps=range(6, 9), what="deposit")
+    assert np.array_equal(Fg[:6], Fo[:6])
+    pg, po = g.particles(), o.particles()
+    assert len(po["id"]) < 3000  # some crossed into the outflow band
+    assert_particles_close(pg, po, cfg, 1e-12, 1e-13, "push")
+
+
+def test_field_pass_fp64_with_laser_and_polarisation(pic, oracle_mod):
+    cfg = wl.small_slab(nx=8, ny=6, nz=32, z0=10, z1=22, precision="fp64")
+    g, o = _pair(pic, oracle_mod, cfg)
+    F = wl.random_fields(cfg, seed=12, e_amp=2e10, b_amp=80.0, j_amp=1e15)
+    # polarisation state only on material planes
+    pol = np.zeros_like(F[9:15])
+    rng = np.random.default_rng(4)
+    pol[:, 10:22] = rng.uniform(-1, 1, pol[:, 10:22].shape) * np.array([1e9] * 3 + [1e24] * 3)[:, None, None, None]
+    F[9:15] = pol
+    for s in (g, o):
+        s.set_scalars(40)
+        s.set_fields(F)
+    g.phases(2)
+    o.phases(2)
+    assert_fields_close(g.fields(), o.fields(), TOL64, what="field pass")
+    assert g.scalars()["U_joule"] == pytest.approx(o.scalars()["U_joule"], rel=1e-12)
+
+
+def _oracle_run(oracle_mod, cfg, steps):
+    s = oracle_mod.Sim(cfg)
+    s.step(steps)
+    return s
+
+
+def test_window_keldysh_and_ionisation_fp64(pic, oracle_mod):
+    cfg = wl.small_slab(precision="fp64")
+    o = _oracle_run(oracle_mod, cfg, 45)
+    assert o.np > 0
+    g = pic.Simulation(cfg)
+    g.load_state(oracle_state_for_gpu(o))
+    g.phases(4)
+    o.phases(4)
+    mg, mo = g.material(), o.material()
+    assert np.max(np.abs(mg["eamp"] - mo["eamp"])) <= 1e-15 * np.max(mo["eamp"])
+    Tg, To = mg["T"].astype(np.float64), mo["T"].astype(np.float64)
+    hot = To > 0
+    assert hot.sum() > 100
+    assert np.all(Tg[~hot] == 0)
+    assert np.max(np.abs(Tg[hot] / To[hot] - 1)) < 1e-12
+    g.phases(8)
+    o.phases(8)
+    assert np.array_equal(g.material()["alive"], o.material()["alive"])
+    assert_particles_close(g.particles(), o.particles(), cfg, 1e-13, 1e-13, "new pairs")
+
+
+@pytest.mark.parametrize("static", [False, True])
+def test_full_run_fp64_matches_step_by_step(pic, oracle_mod, static):
+    cfg = wl.small_slab(precision="fp64", static=static)
+    g, o = _pair(pic, oracle_mod, cfg)
+    worst = 0.0
+    for block in range(4):
+        g.step(15)
+        o.step(15)
+        errs = field_errors(g.fields(), o.fields())
+        worst = max(worst, max(errs.values()))
+        assert worst <= TOL64, (block, errs)
+        assert np.array_equal(g.material()["alive"], o.material()["alive"]), block
+        pg, po = g.particles(), o.particles()
+        assert_particles_close(pg, po, cfg, 1e-11, 1e-11, f"block {block}")
+    assert len(po["id"]) > 300
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("U_kinetic", "U_ionization", "U_absorbed", "U_joule", "U_field", "N_pairs",
+              "n_e_peak", "energy_density_peak", "rho_max"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-10), k
+
+
+def test_fp32_single_steps_from_oracle_states(pic, oracle_mod):
+    cfg64 = wl.small_slab(precision="fp64")
+    cfg32 = dict(cfg64, precision="fp32")
+    o = oracle_mod.Sim(cfg64)
+    flips_total, draws_total, slack = 0, 0, 0.0
+    for stop in (20, 40, 60):
+        o.step(stop - o.step_index)
+        st = oracle_state_for_gpu(o)
+        g = pic.Simulation(cfg32)
+        g.load_state(st)
+        g.step(1)
+        o2 = oracle_mod.Sim(cfg64)
+        o2.set_scalars(st["scalars"]["step"], st["scalars"]["U_joule"], st["scalars"]["N_pairs"],
+                       st["scalars"]["U_ion"], st["scalars"]["n_events"])
+        o2.set_fields(st["fields"])
+        o2.set_particles(st["particles"])
+        o2.set_material(st["material"]["alive"], st["material"]["win"])
+        o2.step(1)
+        Fg, Fo = g.fields(), o2.fields()
+        for name, sl in (("E", slice(0, 3)), ("B", slice(3, 6)), ("P", slice(9, 12)),
+                         ("Q", slice(12, 15))):
+            err = rel_l2(Fg[sl], Fo[sl])
+            assert err <= TOL32, (stop, name, err, field_errors(Fg, Fo))
+        ag, ao = g.material()["alive"], o2.material()["alive"]
+        flips = int(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(ag, ao)))
+        flips_total += flips
+        draws_total += int(sum(bin(int(a)).count("1") for a in st["material"]["alive"]))
+        g.close()
+    # FP32 moves each probability by ~1e-6 relative; flips are rare
+    assert flips_total <= 3 + 1e-4 * draws_total
+
+
+def test_vacuum_box_matches(pic, oracle_mod):
+    cfg = wl.vacuum_box(nx=4, ny=4, nz=48)
+    g, o = _pair(pic, oracle_mod, cfg)
+    g.step(80)
+    o.step(80)
+    assert_fields_close(g.fields(), o.fields(), TOL64, comps=range(6), what="vacuum")
+    assert g.particles()["id"].size == 0
+
+
+def test_pool_overflow_reports_epool(pic):
+    cfg = wl.small_slab(precision="fp32", fluence=20.0)
+    cfg["pool_factor"] = 0.0  # 1024 spare slots only
+    g = pic.Simulation(cfg)
+    assert g.static["capacity"] == 1024
+    g.step(30)
+    try:
+        g.sync()
+        raised = None
+    except pic.PicError as e:
+        raised = e
+    if raised is None:
+        info = g.info()
+        m = g.material()
+        pytest.fail(f"no PIC_EPOOL: particles {info['n_particles']} cap {info['capacity']} "
+                    f"events {g.scalars()['n_events']} max eamp {m['eamp'].max()} "
+                    f"max T {m['T'].max()}")
+    assert raised.code == pic.PIC_EPOOL
+
+
+def test_config1_full_run_fp64_and_fp32(pic, oracle_mod):
+    cfg = wl.config1()
+    o = oracle_mod.Sim(cfg)
+    o.step(cfg["steps"])
+    do = o.diagnostics()
+    g = pic.Simulation(cfg)
+    g.step(cfg["steps"])
+    dg = g.diagnostics()
+    assert_fields_close(g.fields(), o.fields(), 1e-11, what="config1 fp64 200 steps")
+    for k in ("frac_absorbed", "n_e_peak", "U_kinetic", "N_pairs"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-9), k
+    g32 = pic.Simulation(dict(cfg, precision="fp32"))
+    g32.step(cfg["steps"])
+    d32 = g32.diagnostics()
+    assert d32["frac_absorbed"] == pytest.approx(do["frac_absorbed"], rel=0.02)
+    assert d32["n_e_peak"] == pytest.approx(do["n_e_peak"], rel=0.02)
+    assert do["N_pairs"] > 0 and do["frac_absorbed"] > 0.01
