@@ -191,7 +191,7 @@ def run_reference(args, rank, world, dist):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-ALG_BYTES = {  # FP32 algorithmic bytes per unit
+ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
     "push": ("particle", 60.0),
     "bhalf": ("field point", 36.0),
     "efull": ("field point", 60.0),
