@@ -53,6 +53,7 @@ struct Plan {
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
   size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
+  size_t off_work, off_work_n;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t total;
 };
@@ -153,6 +154,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
     P.off_pt[b] = take(P.cap * 4);
     P.off_pid[b] = take(P.cap * 8);
   }
+  P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
+  P.off_work_n = take(16);
   P.off_cnt = take(P.ncell * 4);
   P.off_bsum = take((size_t)P.nb_scan * 4);
   P.off_total = take(8);
@@ -359,6 +362,8 @@ void bind(pic_ctx *h) {
   D.err = (int *)(A + P.off_err);
   D.seed = h->seed;
   X.lr = (const LayerR<R> *)(A + P.off_lr);
+  X.work = (int *)(A + P.off_work);
+  X.work_n = (int *)(A + P.off_work_n);
 }
 
 int grid_blocks(long long n) { return (int)std::max<long long>(1, (n + kThreads - 1) / kThreads); }
@@ -440,9 +445,11 @@ int enqueue(pic_ctx *h, int mask) {
   if (P.nmat > 0) {
     if (mask & PIC_PHASE_WINDOW) {
       prof_begin(h, PIC_PROF_WINDOW);
+      PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
       k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+      k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
       prof_end(h);
-      h->launches += 1;
+      h->launches += 2;
     }
     if (mask & PIC_PHASE_IONIZE) {
       prof_begin(h, PIC_PROF_IONIZE);

@@ -36,6 +36,9 @@ struct Ctx {
   R *ao[3], *au[3];
   uint32_t *atag;
   unsigned long long *aid;
+  // material cells whose Keldysh threshold must be recomputed this step
+  int *work;
+  int *work_n;
 };
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -102,11 +105,15 @@ __device__ __forceinline__ void atomic_add(R *p, R v) {
 }
 
 // Esirkepov deposit on a 4-node frame per axis (moves are below one cell).
+// All loops are unrolled with compile-time indices so the frame arrays stay in
+// registers; frame sizes enter only as predicates.
 template <class R>
 __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], const int co[3],
                                           const R oo[3], const int cn[3], const R on[3]) {
-  R S0[3][4], DS[3][4], A[3][4];
-  int base[3], nn[3], nf[3];
+  R DS[3][4], A[3][4];
+  int nn[3], nf[3];
+  int node[3][4];
+  const int nx = D.nx, ny = D.ny;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R wo[3], wn[3];
@@ -115,49 +122,47 @@ __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], con
     shape_int(on[d], wn, bn);
     const int i0o = co[d] + bo + 1, i0n = cn[d] + bn + 1;
     const int s = i0n - i0o;
-    const int fo = s < 0 ? 1 : 0, fn = s > 0 ? 1 : 0;
-    base[d] = i0o - 1 - fo;
+    const bool lo = s < 0, hi = s > 0;
+    const int base = i0o - 1 - (lo ? 1 : 0);
     nn[d] = 3 + (s != 0);
     nf[d] = 2 + (s != 0);
-    R S1[4];
+    // S0 at frame offset lo, S1 at offset hi
+    const R S0[4] = {lo ? R(0) : wo[0], lo ? wo[0] : wo[1], lo ? wo[1] : wo[2], lo ? wo[2] : R(0)};
+    const R S1[4] = {hi ? R(0) : wn[0], hi ? wn[0] : wn[1], hi ? wn[1] : wn[2], hi ? wn[2] : R(0)};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      S0[d][q] = R(0);
-      S1[q] = R(0);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      S0[d][q + fo] = wo[q];
-      S1[q + fn] = wn[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      DS[d][q] = S1[q] - S0[d][q];
-      A[d][q] = S0[d][q] + R(0.5) * DS[d][q];
+      DS[d][q] = S1[q] - S0[q];
+      A[d][q] = S0[q] + R(0.5) * DS[d][q];
+      const int g = base + q;
+      node[d][q] = d == 0 ? wrap(g, nx) : (d == 1 ? wrap(g, ny) : g);
     }
   }
-  const int nx = D.nx, ny = D.ny;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int e = (d + 1) % 3, f = (d + 2) % 3;
     R *__restrict__ J = D.J[d];
-    for (int b = 0; b < nn[e]; ++b)
-      for (int c = 0; c < nn[f]; ++c) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (b >= nn[e] || c >= nn[f]) continue;
         const R M = A[e][b] * A[f][c] + DS[e][b] * DS[f][c] * R(1.0 / 12.0);
         if (M == R(0)) continue;
         R run = R(0);
-        for (int a = 0; a < nf[d]; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
           run += DS[d][a];
+          if (a >= nf[d]) continue;
           const R v = jpref[d] * run * M;
           if (v == R(0)) continue;
           int id3[3];
-          id3[d] = base[d] + a;
-          id3[e] = base[e] + b;
-          id3[f] = base[f] + c;
-          const long long o = ((long long)id3[2] * ny + wrap(id3[1], ny)) * nx + wrap(id3[0], nx);
-          atomic_add(J + o, v);
+          id3[d] = node[d][a];
+          id3[e] = node[e][b];
+          id3[f] = node[f][c];
+          atomic_add(J + ((long long)id3[2] * ny + id3[1]) * nx + id3[0], v);
         }
       }
+    }
   }
 }
 
@@ -305,7 +310,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
   const Dev<R> &D = X.d;
   const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double joule = 0.0;
+  R joule = R(0);
   if (o < D.nfield) {
     const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
     const int k = (int)(o / nxy);
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
         ey1 = ey0 + ay;
       }
     }
-    joule += (double)(jx * R(0.5) * (ex0 + ex1)) + (double)(jy * R(0.5) * (ey0 + ey1));
+    joule += jx * R(0.5) * (ex0 + ex1) + jy * R(0.5) * (ey0 + ey1);
     D.E[0][o] = ex1;
     D.E[1][o] = ey1;
     D.J[0][o] = R(0);
@@ -377,12 +382,12 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
       } else {
         ez1 = ez0 + az;
       }
-      joule += (double)(jz * R(0.5) * (ez0 + ez1));
+      joule += jz * R(0.5) * (ez0 + ez1);
       D.E[2][o] = ez1;
       D.J[2][o] = R(0);
     }
   }
-  const double tot = block_sum<R>(joule);
+  const double tot = block_sum<R>((double)joule);
   if (threadIdx.x == 0 && tot != 0.0) atomicAdd(D.acc + 0, tot * D.dt_d * D.V_d);
 }
 
@@ -427,16 +432,34 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
   }
   D.eamp[m] = amp;
   const LayerR<R> &L = X.lr[D.layer_of_plane[k]];
-  unsigned long long T;
   if (!(amp >= L.e_skip)) {
-    T = 0ull;
-  } else if (D.ckey[m] == amp) {
-    return;  // threshold cached for this exact amplitude
-  } else {
-    T = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms);
+    if (D.T[m] != 0ull) D.T[m] = 0ull;
+    D.ckey[m] = amp;
+    return;
   }
-  if (D.T[m] != T) D.T[m] = T;
-  D.ckey[m] = amp;
+  if (D.ckey[m] == amp) return;  // threshold cached for this exact amplitude
+  // cache miss: queue the cell for k_keldysh (warp-aggregated append)
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(act) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(X.work_n, __popc(act));
+  base = __shfl_sync(act, base, leader);
+  X.work[base + __popc(act & ((1u << lane) - 1u))] = (int)m;
+}
+
+// Keldysh thresholds of the queued cells, one thread per cell.
+template <class R>
+__global__ void __launch_bounds__(256) k_keldysh(Ctx<R> X) {
+  const Dev<R> &D = X.d;
+  const int n = *X.work_n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const long long m = X.work[q];
+    const int k = D.kplane[(int)(m / D.nxy)];
+    const R amp = D.eamp[m];
+    D.T[m] = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms);
+    D.ckey[m] = amp;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -551,10 +574,20 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
       const uint32_t s = __ffs(bits) - 1;
       unsigned long long Tuse = Town;
       if (!fast) {
-        Neutral<R> nu;
-        Tuse = neutral_at(D, sig, i, j, k, c, s, t1, nu)
-                   ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-                   : 0ull;
+        // only a neutral that starts within the largest possible displacement
+        // of a face (|v| < 7 sigma) may sit in another cell at t^{n+1}
+        R off0[3];
+        neutral_pos(D, c, s, off0);
+        const R reach = R(7) * sig * t1;
+        const bool near = fmin(off0[0], R(1) - off0[0]) <= reach * D.idx ||
+                          fmin(off0[1], R(1) - off0[1]) <= reach * D.idy ||
+                          fmin(off0[2], R(1) - off0[2]) <= reach * D.idz;
+        if (near) {
+          Neutral<R> nu;
+          Tuse = neutral_at(D, sig, i, j, k, c, s, t1, nu)
+                     ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+                     : 0ull;
+        }
       }
       if (Tuse == 0ull) continue;
       const uint4 w = draw(D.seed, (uint32_t)step, c, s, kStreamIon);

@@ -166,7 +166,7 @@ def test_pool_overflow_reports_epool(pic):
     cfg["pool_factor"] = 0.0  # 1024 spare slots only
     g = pic.Simulation(cfg)
     assert g.static["capacity"] == 1024
-    g.step(30)
+    g.step(100)
     try:
         g.sync()
         raised = None
