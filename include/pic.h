@@ -12,7 +12,7 @@
  *   - the per-cell maximum of |E| over the last optical cycle (Sec. 2.1,
  *     rolling window) and the Keldysh photoionisation rate (Sec. 2.1, Eqs.
  *     for x, W and Q);
- *   - counter-based Philox4x32-10 draws keyed by (seed, step, cell, slot) that
+ *   - counter-based Philox4x32-10 draws keyed by (seed, step, cell, slot pair) that
  *     ionise each molecule at most once (Sec. 2.1) into an electron and a
  *     hole with the Table 1 effective masses (Sec. 3.2).
  *

@@ -19,7 +19,8 @@
  *   ionisation     : one event per molecule (Sec. 2.1), electron + hole with
  *                    the Table 1 effective masses (Sec. 3.2)
  * Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) supplies
- * every random number, keyed by (seed) with counter (step, cell, slot, stream).
+ * every random number, keyed by (seed) with counter (step, cell, slot, stream);
+ * the ionisation stream gives two slots one block (slot >> 1).
  *
  * Parity pins for every function here live in tests/test_oracle_*.py.
  */
@@ -775,10 +776,13 @@ void or_ionize_pass(or_sim *s) {
             T = s->T[m2];
             always = s->Talways[m2];
           }
+          /* slots 2q and 2q+1 share the Philox block (step, cell, q, ION):
+           * words 0,1 form slot 2q's 64-bit uniform, words 2,3 slot 2q+1's */
           uint32_t r[4];
-          philox_draw(s->cfg.seed, (uint32_t)s->step, cell, (uint32_t)sl,
+          philox_draw(s->cfg.seed, (uint32_t)s->step, cell, (uint32_t)(sl >> 1),
                       OR_STREAM_ION, r);
-          uint64_t r64 = ((uint64_t)r[1] << 32) | r[0];
+          int hw = (sl & 1) ? 2 : 0;
+          uint64_t r64 = ((uint64_t)r[hw + 1] << 32) | r[hw];
           if (!(always || r64 < T)) continue;
           s->alive[m] &= ~(1u << sl);
           double v2 = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];

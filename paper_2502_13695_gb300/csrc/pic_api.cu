@@ -48,7 +48,7 @@ struct Plan {
   std::vector<int> lop, mplane, kplane;
   int nb_scan, diag_blocks_p, diag_blocks_g;
   // arena offsets
-  size_t off_E[3], off_B[3], off_J[3], off_P[3], off_Q[3];
+  size_t off_E[3], off_B[3], off_J4, off_P[3], off_Q[3];
   size_t off_lop, off_mplane, off_kplane, off_lk, off_lr;
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
@@ -132,7 +132,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   const size_t R = P.rsz;
   for (int d = 0; d < 3; ++d) P.off_E[d] = take(P.nfield * R);
   for (int d = 0; d < 3; ++d) P.off_B[d] = take(P.nfield * R);
-  for (int d = 0; d < 3; ++d) P.off_J[d] = take(P.nfield * R);
+  P.off_J4 = take(P.nfield * 4 * R);
   for (int d = 0; d < 3; ++d) P.off_P[d] = take(P.nmat * R);
   for (int d = 0; d < 3; ++d) P.off_Q[d] = take(P.nmat * R);
   P.off_lop = take(g.nz * sizeof(int));
@@ -328,10 +328,10 @@ void bind(pic_ctx *h) {
   for (int d = 0; d < 3; ++d) {
     D.E[d] = (R *)(A + P.off_E[d]);
     D.B[d] = (R *)(A + P.off_B[d]);
-    D.J[d] = (R *)(A + P.off_J[d]);
     D.P[d] = (R *)(A + P.off_P[d]);
     D.Q[d] = (R *)(A + P.off_Q[d]);
   }
+  D.J4 = (R *)(A + P.off_J4);
   D.layer_of_plane = (const int *)(A + P.off_lop);
   D.mplane = (const int *)(A + P.off_mplane);
   D.kplane = (const int *)(A + P.off_kplane);
@@ -780,14 +780,21 @@ template <class R>
 int get_fields_t(pic_ctx *h, double *dst) {
   const Plan &P = h->P;
   Ctx<R> &X = ctx_of<R>(h);
-  std::vector<char> raw(std::max(P.nfield, P.nmat) * sizeof(R));
-  R *const *arrs[3] = {X.d.E, X.d.B, X.d.J};
-  for (int g3 = 0; g3 < 3; ++g3)
+  std::vector<char> raw(std::max(4 * P.nfield, P.nmat) * sizeof(R));
+  R *const *arrs[2] = {X.d.E, X.d.B};
+  for (int g3 = 0; g3 < 2; ++g3)
     for (int d = 0; d < 3; ++d) {
       int rc = copy_out(h, off_of(h, arrs[g3][d]), raw.data(), P.nfield * sizeof(R));
       if (rc) return rc;
       to_double<R>(raw, P.nfield, dst + (size_t)(3 * g3 + d) * P.nfield);
     }
+  {
+    int rc = copy_out(h, off_of(h, X.d.J4), raw.data(), 4 * P.nfield * sizeof(R));
+    if (rc) return rc;
+    const R *j = (const R *)raw.data();
+    for (int d = 0; d < 3; ++d)
+      for (long long o = 0; o < P.nfield; ++o) dst[(size_t)(6 + d) * P.nfield + o] = (double)j[4 * o + d];
+  }
   std::vector<double> tmp(P.nmat);
   R *const *pq[2] = {X.d.P, X.d.Q};
   for (int g2 = 0; g2 < 2; ++g2)
@@ -810,13 +817,21 @@ int set_fields_t(pic_ctx *h, const double *src) {
   const Plan &P = h->P;
   Ctx<R> &X = ctx_of<R>(h);
   std::vector<char> raw;
-  R *const *arrs[3] = {X.d.E, X.d.B, X.d.J};
-  for (int g3 = 0; g3 < 3; ++g3)
+  R *const *arrs[2] = {X.d.E, X.d.B};
+  for (int g3 = 0; g3 < 2; ++g3)
     for (int d = 0; d < 3; ++d) {
       from_double<R>(src + (size_t)(3 * g3 + d) * P.nfield, P.nfield, raw);
       int rc = copy_in(h, off_of(h, arrs[g3][d]), raw.data(), raw.size());
       if (rc) return rc;
     }
+  {
+    std::vector<double> j4(4 * P.nfield, 0.0);
+    for (int d = 0; d < 3; ++d)
+      for (long long o = 0; o < P.nfield; ++o) j4[4 * o + d] = src[(size_t)(6 + d) * P.nfield + o];
+    from_double<R>(j4.data(), j4.size(), raw);
+    int rc = copy_in(h, off_of(h, X.d.J4), raw.data(), raw.size());
+    if (rc) return rc;
+  }
   std::vector<double> tmp(P.nmat);
   R *const *pq[2] = {X.d.P, X.d.Q};
   for (int g2 = 0; g2 < 2; ++g2)

@@ -49,8 +49,9 @@ struct Dev {
   R dtdx, dtdy, dtdz;             // dt / dx ...
   double dt_d, V_d, dx_d, dy_d, dz_d;
   double E0, omega, fwhm, t_peak, cep;
-  // fields: nfield each (E, B, J), nmat each (P, Q)
-  R *E[3], *B[3], *J[3], *P[3], *Q[3];
+  // fields: nfield each (E, B), J interleaved (Jx, Jy, Jz, 0) per point,
+  // nmat each (P, Q)
+  R *E[3], *B[3], *J4, *P[3], *Q[3];
   const int *layer_of_plane;      // nz, -1 vacuum
   const int *mplane;              // nz, -1 vacuum
   const int *kplane;              // n_mplanes: z plane of material plane

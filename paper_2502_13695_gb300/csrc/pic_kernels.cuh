@@ -78,18 +78,19 @@ __device__ __forceinline__ void shape_half(R d, R w[3]) {
   w[2] = R(0.5) * hp * hp;
 }
 
-// sum_c wz[c] sum_b wy[b] sum_a wx[a] f[z_c, y_b, x_a]
+// sum_c wz[c] sum_b wy[b] sum_a wx[a] f[zo_c + yo_b + x_a]; zo, yo are plane
+// and row offsets in elements
 template <class R>
-__device__ __forceinline__ R gather27(const R *__restrict__ f, int nx, int ny, const int xs[3],
-                                      const int ys[3], const int zs[3], const R wx[3],
-                                      const R wy[3], const R wz[3]) {
+__device__ __forceinline__ R gather27(const R *__restrict__ f, const int xs[3], const int yo[3],
+                                      const int zo[3], const R wx[3], const R wy[3],
+                                      const R wz[3]) {
   R acc = R(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     R accy = R(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const R *row = f + ((long long)zs[c] * ny + ys[b]) * nx;
+      const R *row = f + (zo[c] + yo[b]);
       const R accx = wx[0] * __ldg(row + xs[0]) + wx[1] * __ldg(row + xs[1]) +
                      wx[2] * __ldg(row + xs[2]);
       accy += wy[b] * accx;
@@ -104,16 +105,35 @@ __device__ __forceinline__ void atomic_add(R *p, R v) {
   atomicAdd(p, v);
 }
 
-// Esirkepov deposit on a 4-node frame per axis (moves are below one cell).
-// All loops are unrolled with compile-time indices so the frame arrays stay in
-// registers; frame sizes enter only as predicates.
+// Adds (a, b, c) to the interleaved current of one field point: one
+// red.global.add.v4.f32 in FP32, three scalar atomics in FP64.
+template <class R>
+__device__ __forceinline__ void red_add3(R *p, R a, R b, R c);
+template <>
+__device__ __forceinline__ void red_add3<float>(float *p, float a, float b, float c) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(0.0f)
+               : "memory");
+}
+template <>
+__device__ __forceinline__ void red_add3<double>(double *p, double a, double b, double c) {
+  if (a != 0.0) atomicAdd(p, a);
+  if (b != 0.0) atomicAdd(p + 1, b);
+  if (c != 0.0) atomicAdd(p + 2, c);
+}
+
+// Esirkepov deposit on a 4-node frame per axis (moves are below one cell):
+// with S0, S1 the old and new shape, DS = S1 - S0, A = S0 + DS/2 and C_d the
+// running sum of DS_d along d,
+//   J_x(a,b,c) = jpref_x C_x[a] (A_y[b] A_z[c] + DS_y[b] DS_z[c] / 12)
+// and cyclically; the three components of one node go out in one vector
+// reduction.  C_d is exactly 0 on the last node of the support.
 template <class R>
 __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], const int co[3],
                                           const R oo[3], const int cn[3], const R on[3]) {
-  R DS[3][4], A[3][4];
-  int nn[3], nf[3];
-  int node[3][4];
-  const int nx = D.nx, ny = D.ny;
+  R DS[3][4], A[3][4], Cs[3][4];
+  int nn[3], off[3][4];
+  const int nx = D.nx, ny = D.ny, nxy = D.nxy;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R wo[3], wn[3];
@@ -125,49 +145,42 @@ __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], con
     const bool lo = s < 0, hi = s > 0;
     const int base = i0o - 1 - (lo ? 1 : 0);
     nn[d] = 3 + (s != 0);
-    nf[d] = 2 + (s != 0);
-    // S0 at frame offset lo, S1 at offset hi
     const R S0[4] = {lo ? R(0) : wo[0], lo ? wo[0] : wo[1], lo ? wo[1] : wo[2], lo ? wo[2] : R(0)};
     const R S1[4] = {hi ? R(0) : wn[0], hi ? wn[0] : wn[1], hi ? wn[1] : wn[2], hi ? wn[2] : R(0)};
+    R run = R(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       DS[d][q] = S1[q] - S0[q];
       A[d][q] = S0[q] + R(0.5) * DS[d][q];
+      run += DS[d][q];
+      Cs[d][q] = q < nn[d] - 1 ? jpref[d] * run : R(0);
       const int g = base + q;
-      node[d][q] = d == 0 ? wrap(g, nx) : (d == 1 ? wrap(g, ny) : g);
+      off[d][q] = d == 0 ? wrap(g, nx) : (d == 1 ? wrap(g, ny) * nx : g * nxy);
     }
   }
+  R *__restrict__ J = D.J4;
+  const R twelfth = R(1.0 / 12.0);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int e = (d + 1) % 3, f = (d + 2) % 3;
-    R *__restrict__ J = D.J[d];
+  for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (b >= nn[e] || c >= nn[f]) continue;
-        const R M = A[e][b] * A[f][c] + DS[e][b] * DS[f][c] * R(1.0 / 12.0);
-        if (M == R(0)) continue;
-        R run = R(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          run += DS[d][a];
-          if (a >= nf[d]) continue;
-          const R v = jpref[d] * run * M;
-          if (v == R(0)) continue;
-          int id3[3];
-          id3[d] = node[d][a];
-          id3[e] = node[e][b];
-          id3[f] = node[f][c];
-          atomic_add(J + ((long long)id3[2] * ny + id3[1]) * nx + id3[0], v);
-        }
+      for (int a = 0; a < 4; ++a) {
+        if (a >= nn[0] || b >= nn[1] || c >= nn[2]) continue;
+        const R jx = Cs[0][a] * (A[1][b] * A[2][c] + DS[1][b] * DS[2][c] * twelfth);
+        const R jy = Cs[1][b] * (A[2][c] * A[0][a] + DS[2][c] * DS[0][a] * twelfth);
+        const R jz = Cs[2][c] * (A[0][a] * A[1][b] + DS[0][a] * DS[1][b] * twelfth);
+        if (jx == R(0) && jy == R(0) && jz == R(0)) continue;
+        red_add3(J + 4 * (off[2][c] + off[1][b] + off[0][a]), jx, jy, jz);
       }
-    }
-  }
 }
 
+// Blocks per SM for the push: FP32 fits three (80 registers), FP64 two.
+template <class R> struct PushOcc { static constexpr int v = 2; };
+template <> struct PushOcc<float> { static constexpr int v = 3; };
+
 template <class R>
-__global__ void __launch_bounds__(256) k_push(Ctx<R> X) {
+__global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
   const Dev<R> &D = X.d;
   const unsigned long long n = min(*D.nslots, D.cap);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
@@ -185,10 +198,11 @@ __global__ void __launch_bounds__(256) k_push(Ctx<R> X) {
     const uint32_t tag = D.ptag[p];
     const LayerR<R> &L = X.lr[tag >> 1];
     const int sp = tag & 1u;
-    // shapes: integer grid (weights + node indices) and half-integer grid
+    // shapes on the integer and half-integer grids; node offsets in elements
     R wi[3][3], wh[3][3];
     int xi[3], xh[3], yi[3], yh[3], zi[3], zh[3];
     {
+      const int nxy = D.nxy;
       int b;
       shape_int(off[0], wi[0], b);
       shape_half(off[0], wh[0]);
@@ -201,23 +215,23 @@ __global__ void __launch_bounds__(256) k_push(Ctx<R> X) {
       shape_half(off[1], wh[1]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        yi[a] = wrap(cj + b + a, ny);
-        yh[a] = wrap(cj - 1 + a, ny);
+        yi[a] = wrap(cj + b + a, ny) * nx;
+        yh[a] = wrap(cj - 1 + a, ny) * nx;
       }
       shape_int(off[2], wi[2], b);
       shape_half(off[2], wh[2]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        zi[a] = ck + b + a;
-        zh[a] = ck - 1 + a;
+        zi[a] = (ck + b + a) * nxy;
+        zh[a] = (ck - 1 + a) * nxy;
       }
     }
-    const R Ex = gather27(D.E[0], nx, ny, xh, yi, zi, wh[0], wi[1], wi[2]);
-    const R Ey = gather27(D.E[1], nx, ny, xi, yh, zi, wi[0], wh[1], wi[2]);
-    const R Ez = gather27(D.E[2], nx, ny, xi, yi, zh, wi[0], wi[1], wh[2]);
-    const R Bx = gather27(D.B[0], nx, ny, xi, yh, zh, wi[0], wh[1], wh[2]);
-    const R By = gather27(D.B[1], nx, ny, xh, yi, zh, wh[0], wi[1], wh[2]);
-    const R Bz = gather27(D.B[2], nx, ny, xh, yh, zi, wh[0], wh[1], wi[2]);
+    const R Ex = gather27(D.E[0], xh, yi, zi, wh[0], wi[1], wi[2]);
+    const R Ey = gather27(D.E[1], xi, yh, zi, wi[0], wh[1], wi[2]);
+    const R Ez = gather27(D.E[2], xi, yi, zh, wi[0], wi[1], wh[2]);
+    const R Bx = gather27(D.B[0], xi, yh, zh, wi[0], wh[1], wh[2]);
+    const R By = gather27(D.B[1], xh, yi, zh, wh[0], wi[1], wh[2]);
+    const R Bz = gather27(D.B[2], xh, yh, zi, wh[0], wh[1], wi[2]);
     // relativistic Boris rotation between two half electric kicks
     const R h = L.qmdt2[sp];
     R um[3] = {u[0] + h * Ex, u[1] + h * Ey, u[2] + h * Ez};
@@ -291,6 +305,26 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
   D.B[2][o] -= h * ((Ey[oi] - Ey[o]) * D.idx - (Ex[oj] - Ex[o]) * D.idy);
 }
 
+__device__ __forceinline__ void load_j3(const float *j4, float &a, float &b, float &c) {
+  const float4 v = *reinterpret_cast<const float4 *>(j4);
+  a = v.x;
+  b = v.y;
+  c = v.z;
+}
+__device__ __forceinline__ void load_j3(const double *j4, double &a, double &b, double &c) {
+  const double2 v = *reinterpret_cast<const double2 *>(j4);
+  a = v.x;
+  b = v.y;
+  c = j4[2];
+}
+__device__ __forceinline__ void clear_j3(float *j4) {
+  *reinterpret_cast<float4 *>(j4) = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void clear_j3(double *j4) {
+  reinterpret_cast<double2 *>(j4)[0] = make_double2(0.0, 0.0);
+  j4[2] = 0.0;
+}
+
 template <class R>
 __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) {
   R dp;
@@ -323,7 +357,9 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
     const R bz = Bz[o];
     const R dBz_dy = (bz - Bz[omj]) * D.idy;
     const R dBz_dx = (bz - Bz[omi]) * D.idx;
-    const R jx = D.J[0][o], jy = D.J[1][o];
+    R *const j4 = D.J4 + 4 * o;
+    R jx, jy, jz;
+    load_j3(j4, jx, jy, jz);
     const R ex0 = D.E[0][o], ey0 = D.E[1][o];
     R ex1, ey1;
     const int L = k < nz ? D.layer_of_plane[k] : -1;
@@ -367,10 +403,8 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
     joule += jx * R(0.5) * (ex0 + ex1) + jy * R(0.5) * (ey0 + ey1);
     D.E[0][o] = ex1;
     D.E[1][o] = ey1;
-    D.J[0][o] = R(0);
-    D.J[1][o] = R(0);
+    clear_j3(j4);
     if (k < nz) {
-      const R jz = D.J[2][o];
       const R az = c2dt * ((By[o] - By[omi]) * D.idx - (Bx[o] - Bx[omj]) * D.idy) - dtie * jz;
       const R ez0 = D.E[2][o];
       R ez1;
@@ -384,7 +418,6 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
       }
       joule += jz * R(0.5) * (ez0 + ez1);
       D.E[2][o] = ez1;
-      D.J[2][o] = R(0);
     }
   }
   const double tot = block_sum<R>((double)joule);
@@ -570,29 +603,41 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
     const unsigned long long Town = D.T[m];
     if (fast && Town == 0ull) alive = 0;
     const R sig = X.lr[L].sig_v;
-    for (uint32_t bits = alive; bits; bits &= bits - 1) {
-      const uint32_t s = __ffs(bits) - 1;
-      unsigned long long Tuse = Town;
+    // slots 2q and 2q+1 share Philox block (step, cell, q, 3): words 0-1 and
+    // 2-3 are their 64-bit uniforms
+    for (uint32_t bits = alive; bits;) {
+      const uint32_t q = (uint32_t)(__ffs(bits) - 1) >> 1;
+      const uint32_t pair_bits = bits & (3u << (2 * q));
+      bits &= ~(3u << (2 * q));
+      unsigned long long Tuse[2] = {Town, Town};
       if (!fast) {
-        // only a neutral that starts within the largest possible displacement
-        // of a face (|v| < 7 sigma) may sit in another cell at t^{n+1}
-        R off0[3];
-        neutral_pos(D, c, s, off0);
-        const R reach = R(7) * sig * t1;
-        const bool near = fmin(off0[0], R(1) - off0[0]) <= reach * D.idx ||
-                          fmin(off0[1], R(1) - off0[1]) <= reach * D.idy ||
-                          fmin(off0[2], R(1) - off0[2]) <= reach * D.idz;
-        if (near) {
-          Neutral<R> nu;
-          Tuse = neutral_at(D, sig, i, j, k, c, s, t1, nu)
-                     ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-                     : 0ull;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t s = 2 * q + h;
+          if (!((pair_bits >> s) & 1u)) continue;
+          // only a neutral that starts within the largest possible
+          // displacement of a face (|v| < 7 sigma) may sit in another cell
+          R off0[3];
+          neutral_pos(D, c, s, off0);
+          const R reach = R(7) * sig * t1;
+          const bool near = fmin(off0[0], R(1) - off0[0]) <= reach * D.idx ||
+                            fmin(off0[1], R(1) - off0[1]) <= reach * D.idy ||
+                            fmin(off0[2], R(1) - off0[2]) <= reach * D.idz;
+          if (near) {
+            Neutral<R> nu;
+            Tuse[h] = neutral_at(D, sig, i, j, k, c, s, t1, nu)
+                          ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+                          : 0ull;
+          }
         }
       }
-      if (Tuse == 0ull) continue;
-      const uint4 w = draw(D.seed, (uint32_t)step, c, s, kStreamIon);
-      const unsigned long long r64 = ((unsigned long long)w.y << 32) | w.x;
-      if (ionises(r64, Tuse)) ion |= 1u << s;
+      if (Tuse[0] == 0ull && Tuse[1] == 0ull) continue;
+      const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
+      const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
+      const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
+      if (((pair_bits >> (2 * q)) & 1u) && Tuse[0] && ionises(r0, Tuse[0])) ion |= 1u << (2 * q);
+      if (((pair_bits >> (2 * q + 1)) & 1u) && Tuse[1] && ionises(r1, Tuse[1]))
+        ion |= 1u << (2 * q + 1);
     }
   }
   // warp-aggregated reservation of pool slots
