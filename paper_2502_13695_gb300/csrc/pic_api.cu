@@ -53,7 +53,8 @@ struct Plan {
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
   size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
-  size_t off_work, off_work_n;
+  size_t off_work, off_work_n, off_leave16;
+  int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t total;
 };
@@ -154,6 +155,9 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
     P.off_pt[b] = take(P.cap * 4);
     P.off_pid[b] = take(P.cap * 8);
   }
+  P.ppc_max = 1;
+  for (const pic_layer &ly : P.layers) P.ppc_max = std::max(P.ppc_max, ly.ppc);
+  P.off_leave16 = take(std::max<long long>(P.nmat, 1) * P.ppc_max * 2);
   P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
   P.off_work_n = take(16);
   P.off_cnt = take(P.ncell * 4);
@@ -364,6 +368,8 @@ void bind(pic_ctx *h) {
   X.lr = (const LayerR<R> *)(A + P.off_lr);
   X.work = (int *)(A + P.off_work);
   X.work_n = (int *)(A + P.off_work_n);
+  X.leave16 = (uint16_t *)(A + P.off_leave16);
+  X.ppc_max = P.ppc_max;
 }
 
 int grid_blocks(long long n) { return (int)std::max<long long>(1, (n + kThreads - 1) / kThreads); }

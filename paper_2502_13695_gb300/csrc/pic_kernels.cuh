@@ -39,6 +39,9 @@ struct Ctx {
   // material cells whose Keldysh threshold must be recomputed this step
   int *work;
   int *work_n;
+  // per-neutral leave steps in units of 64 steps (nmat x ppc_max)
+  uint16_t *leave16;
+  int ppc_max;
 };
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -305,6 +308,20 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
   D.B[2][o] -= h * ((Ey[oi] - Ey[o]) * D.idx - (Ex[oj] - Ex[o]) * D.idy);
 }
 
+template <class R>
+__device__ __forceinline__ R block_sum_r(R v) {
+  __shared__ R part_r[32];
+#pragma unroll
+  for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) part_r[w] = v;
+  __syncthreads();
+  R tot = R(0);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += part_r[q];
+  return tot;
+}
+
 __device__ __forceinline__ void load_j3(const float *j4, float &a, float &b, float &c) {
   const float4 v = *reinterpret_cast<const float4 *>(j4);
   a = v.x;
@@ -420,8 +437,9 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
       D.E[2][o] = ez1;
     }
   }
-  const double tot = block_sum<R>((double)joule);
-  if (threadIdx.x == 0 && tot != 0.0) atomicAdd(D.acc + 0, tot * D.dt_d * D.V_d);
+  // Joule work: block sum in the working precision, one FP64 atomic per block
+  const R tot = block_sum_r(joule);
+  if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
 }
 
 // ---------------------------------------------------------------------------
@@ -464,13 +482,13 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
     }
   }
   D.eamp[m] = amp;
+  if (D.ckey[m] == amp) return;  // threshold cached for this exact amplitude
   const LayerR<R> &L = X.lr[D.layer_of_plane[k]];
   if (!(amp >= L.e_skip)) {
-    if (D.T[m] != 0ull) D.T[m] = 0ull;
+    D.T[m] = 0ull;
     D.ckey[m] = amp;
     return;
   }
-  if (D.ckey[m] == amp) return;  // threshold cached for this exact amplitude
   // cache miss: queue the cell for k_keldysh (warp-aggregated append)
   const unsigned act = __activemask();
   const int lane = threadIdx.x & 31;
@@ -587,7 +605,6 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   int i = 0, j = 0, k = 0, L = 0;
   uint32_t c = 0;
   R t1 = R(0);
-  bool fast = true;
   if (active) alive = D.alive[m];
   if (alive) {
     const int nx = D.nx, nxy = D.nxy;
@@ -598,46 +615,46 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
     k = D.kplane[mp];
     L = D.layer_of_plane[k];
     c = (uint32_t)((long long)k * nxy + r);
-    t1 = R((double)(step + 1) * D.dt_d);
-    fast = (unsigned long long)(step + 1) < (unsigned long long)D.leave_step[m];
     const unsigned long long Town = D.T[m];
-    if (fast && Town == 0ull) alive = 0;
-    const R sig = X.lr[L].sig_v;
-    // slots 2q and 2q+1 share Philox block (step, cell, q, 3): words 0-1 and
-    // 2-3 are their 64-bit uniforms
-    for (uint32_t bits = alive; bits;) {
-      const uint32_t q = (uint32_t)(__ffs(bits) - 1) >> 1;
-      const uint32_t pair_bits = bits & (3u << (2 * q));
-      bits &= ~(3u << (2 * q));
-      unsigned long long Tuse[2] = {Town, Town};
-      if (!fast) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t s = 2 * q + h;
-          if (!((pair_bits >> s) & 1u)) continue;
-          // only a neutral that starts within the largest possible
-          // displacement of a face (|v| < 7 sigma) may sit in another cell
-          R off0[3];
-          neutral_pos(D, c, s, off0);
-          const R reach = R(7) * sig * t1;
-          const bool near = fmin(off0[0], R(1) - off0[0]) <= reach * D.idx ||
-                            fmin(off0[1], R(1) - off0[1]) <= reach * D.idy ||
-                            fmin(off0[2], R(1) - off0[2]) <= reach * D.idz;
-          if (near) {
-            Neutral<R> nu;
-            Tuse[h] = neutral_at(D, sig, i, j, k, c, s, t1, nu)
-                          ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-                          : 0ull;
-          }
-        }
+    // neutrals that may have left the birth cell by t^{n+1}: their own
+    // leave step (64-step units, rounded down) has been reached
+    uint32_t exc = 0;
+    if ((unsigned long long)(step + 1) >= (unsigned long long)D.leave_step[m]) {
+      const uint16_t *ls = X.leave16 + m * X.ppc_max;
+      for (uint32_t bits = alive; bits; bits &= bits - 1) {
+        const uint32_t s = __ffs(bits) - 1;
+        if ((unsigned long long)(step + 1) >= 64ull * ls[s]) exc |= 1u << s;
       }
-      if (Tuse[0] == 0ull && Tuse[1] == 0ull) continue;
-      const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
-      const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
-      const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
-      if (((pair_bits >> (2 * q)) & 1u) && Tuse[0] && ionises(r0, Tuse[0])) ion |= 1u << (2 * q);
-      if (((pair_bits >> (2 * q + 1)) & 1u) && Tuse[1] && ionises(r1, Tuse[1]))
-        ion |= 1u << (2 * q + 1);
+    }
+    // birth-cell threshold for every other alive neutral; slots 2q and 2q+1
+    // share Philox block (step, cell, q, 3): words 0-1 and 2-3
+    if (Town != 0ull) {
+      for (uint32_t bits = alive & ~exc; bits;) {
+        const uint32_t q = (uint32_t)(__ffs(bits) - 1) >> 1;
+        const uint32_t pb = bits & (3u << (2 * q));
+        bits &= ~(3u << (2 * q));
+        const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
+        const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
+        const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
+        if (((pb >> (2 * q)) & 1u) && ionises(r0, Town)) ion |= 1u << (2 * q);
+        if (((pb >> (2 * q + 1)) & 1u) && ionises(r1, Town)) ion |= 1u << (2 * q + 1);
+      }
+    }
+    // the few neutrals near a face: exact position, threshold of that cell
+    const R sig = X.lr[L].sig_v;
+    t1 = R((double)(step + 1) * D.dt_d);
+    for (uint32_t bits = exc; bits; bits &= bits - 1) {
+      const uint32_t s = __ffs(bits) - 1;
+      Neutral<R> nu;
+      const unsigned long long Tuse =
+          neutral_at(D, sig, i, j, k, c, s, t1, nu)
+              ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+              : 0ull;
+      if (Tuse == 0ull) continue;
+      const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 1, kStreamIon);
+      const unsigned long long r64 = (s & 1u) ? (((unsigned long long)w.w << 32) | w.z)
+                                              : (((unsigned long long)w.y << 32) | w.x);
+      if (ionises(r64, Tuse)) ion |= 1u << s;
     }
   }
   // warp-aggregated reservation of pool slots
@@ -704,16 +721,21 @@ __global__ void k_init_material(Ctx<R> X) {
   const uint32_t c = (uint32_t)((long long)k * nxy + r);
   const int ppc = L.ppc;
   D.alive[m] = ppc >= 32 ? 0xFFFFFFFFu : ((1u << ppc) - 1u);
-  double tmin = 1e300;
+  double smin = 4e9;
   const double dl[3] = {D.dx_d, D.dy_d, D.dz_d};
+  const double vmax = 7.0 * L.sigv;
+  uint16_t *ls = X.leave16 + m * X.ppc_max;
   for (int s = 0; s < ppc; ++s) {
     const uint4 w = draw(D.seed, 0u, c, (uint32_t)s, kStreamPos);
     const double o3[3] = {unit_open<double>(w.x), unit_open<double>(w.y), unit_open<double>(w.z)};
-    for (int d = 0; d < 3; ++d) tmin = fmin(tmin, fmin(o3[d], 1.0 - o3[d]) * dl[d]);
+    double t = 1e300;
+    for (int d = 0; d < 3; ++d) t = fmin(t, fmin(o3[d], 1.0 - o3[d]) * dl[d]);
+    // steps before which this neutral is certainly inside its birth cell
+    const double st = vmax > 0.0 ? fmin(floor(t / vmax / D.dt_d), 4e9) : 4e9;
+    smin = fmin(smin, st);
+    ls[s] = (uint16_t)fmin(floor(st / 64.0), 65535.0);
   }
-  const double vmax = 7.0 * L.sigv;
-  double steps = vmax > 0.0 ? floor(tmin / vmax / D.dt_d) : 4e9;
-  D.leave_step[m] = steps >= 4e9 ? 0xFFFFFFFFu : (uint32_t)steps;
+  D.leave_step[m] = smin >= 4e9 ? 0xFFFFFFFFu : (uint32_t)smin;
   D.pm[m] = R(0);
   D.eamp[m] = R(0);
   D.ckey[m] = R(-1);
