@@ -247,6 +247,31 @@ int pic_set_material(pic_handle h, const uint32_t *alive, const double *win);
 int pic_get_scalars(pic_handle h, long long *step, double out[4]);
 int pic_set_scalars(pic_handle h, long long step, const double in[4]);
 
+/* ---- allocation-free field energy -------------------------------------
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory, such as code that runs while a stream is being
+ * captured into a CUDA graph, or a process whose device memory is planned up
+ * front by another allocator (a serving loop holding a fixed budget).  It
+ * computes sum over n field points of (eps0 |E|^2 + |B|^2 / mu0) / 2 times
+ * cell_volume, the U_field of pic_diagnostics, with no allocation: its
+ * scratch is one FP64 partial per block of 2048 points in a static device
+ * array of 512 KiB that every GPU loading this library keeps until the
+ * process exits.
+ *   precision   : PIC_FP32 or PIC_FP64, the element type of the six arrays
+ *   Ex..Bz      : device arrays of n elements each (caller-owned)
+ *   n           : 0 .. 134217728 (65536 blocks of 2048); larger is PIC_EINVAL
+ *   d_out       : device pointer to one double, written on `stream`
+ *   stream      : cudaStream_t (NULL: the legacy default stream)
+ * The result is deterministic (fixed partition, fixed summation order).  The
+ * first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the scratch: calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller. */
+int pic_field_energy_noalloc(int precision, const void *Ex, const void *Ey, const void *Ez,
+                             const void *Bx, const void *By, const void *Bz, long long n,
+                             double cell_volume, double *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpicgb300.so")
-SOURCES = [os.path.join(CSRC, "pic_api.cu")]
+SOURCES = [os.path.join(CSRC, "pic_api.cu"), os.path.join(CSRC, "pic_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("pic_device.cuh", "pic_kernels.cuh")] + [
     os.path.join(os.path.dirname(HERE), "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -259,6 +259,12 @@ std::vector<LayerR<R>> layer_working(const Plan &P, const std::vector<LayerK> &l
 
 }  // namespace
 
+// Lets the allocation-free entry point (its own translation unit) report
+// errors through pic_last_error().
+namespace pg_internal {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace pg_internal
+
 struct pic_ctx {
   Plan P;
   std::vector<LayerK> lk;
