@@ -137,9 +137,9 @@ typedef struct {
 
 /* Kernel classes reported by pic_profile_read. */
 #define PIC_PROF_PUSH 0    /* gather + Boris + deposit */
-#define PIC_PROF_BHALF 1   /* both B half steps */
-#define PIC_PROF_EFULL 2   /* E + polarisation + boundaries */
-#define PIC_PROF_WINDOW 3  /* amplitude window + Keldysh */
+#define PIC_PROF_FIELDS 1  /* fused B half, E + polarisation + faces, B half, window */
+#define PIC_PROF_KELDYSH 2 /* Keldysh thresholds of the cells whose amplitude changed */
+#define PIC_PROF_WINDOW 3  /* window alone (window phase without the field phase) */
 #define PIC_PROF_IONIZE 4  /* ionisation draws + pair appends */
 #define PIC_PROF_SORT 5    /* pool sort (all its kernels) */
 #define PIC_PROF_OTHER 6   /* step counter */

@@ -11,6 +11,7 @@
 
 #include "../../include/pic.h"
 #include "pic_kernels.cuh"
+#include "pic_fields.cuh"
 
 using namespace pg;
 
@@ -49,6 +50,7 @@ struct Plan {
   int nb_scan, diag_blocks_p, diag_blocks_g;
   // arena offsets
   size_t off_E[3], off_B[3], off_J4, off_P[3], off_Q[3];
+  size_t off_E2[3], off_B2[3], off_J4b, off_P2[3], off_Q2[3];
   size_t off_lop, off_mplane, off_kplane, off_lk, off_lr;
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
@@ -136,6 +138,11 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_J4 = take(P.nfield * 4 * R);
   for (int d = 0; d < 3; ++d) P.off_P[d] = take(P.nmat * R);
   for (int d = 0; d < 3; ++d) P.off_Q[d] = take(P.nmat * R);
+  for (int d = 0; d < 3; ++d) P.off_E2[d] = take(P.nfield * R);
+  for (int d = 0; d < 3; ++d) P.off_B2[d] = take(P.nfield * R);
+  P.off_J4b = take(P.nfield * 4 * R);
+  for (int d = 0; d < 3; ++d) P.off_P2[d] = take(P.nmat * R);
+  for (int d = 0; d < 3; ++d) P.off_Q2[d] = take(P.nmat * R);
   P.off_lop = take(g.nz * sizeof(int));
   P.off_mplane = take(g.nz * sizeof(int));
   P.off_kplane = take(std::max(1, P.n_mplanes) * sizeof(int));
@@ -340,7 +347,12 @@ void bind(pic_ctx *h) {
     D.B[d] = (R *)(A + P.off_B[d]);
     D.P[d] = (R *)(A + P.off_P[d]);
     D.Q[d] = (R *)(A + P.off_Q[d]);
+    X.E2[d] = (R *)(A + P.off_E2[d]);
+    X.B2[d] = (R *)(A + P.off_B2[d]);
+    X.P2[d] = (R *)(A + P.off_P2[d]);
+    X.Q2[d] = (R *)(A + P.off_Q2[d]);
   }
+  X.J4b = (R *)(A + P.off_J4b);
   D.J4 = (R *)(A + P.off_J4);
   D.layer_of_plane = (const int *)(A + P.off_lop);
   D.mplane = (const int *)(A + P.off_mplane);
@@ -443,32 +455,51 @@ int enqueue(pic_ctx *h, int mask) {
     h->launches += 1;
   }
   if (mask & PIC_PHASE_FIELDS) {
-    prof_begin(h, PIC_PROF_BHALF);
-    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
-    prof_end(h);
-    prof_begin(h, PIC_PROF_EFULL);
-    k_efull<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X);
-    prof_end(h);
-    prof_begin(h, PIC_PROF_BHALF);
-    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
-    prof_end(h);
-    h->launches += 3;
-  }
-  if (P.nmat > 0) {
-    if (mask & PIC_PHASE_WINDOW) {
-      prof_begin(h, PIC_PROF_WINDOW);
-      PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
-      k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
-      k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
-      prof_end(h);
-      h->launches += 2;
+    // fused field pass (with the window when that phase is requested too)
+    const bool win = (mask & PIC_PHASE_WINDOW) && P.nmat > 0;
+    prof_begin(h, PIC_PROF_FIELDS);
+    if (win) PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
+    FieldOut<R> W;
+    for (int d = 0; d < 3; ++d) {
+      W.E[d] = X.E2[d];
+      W.B[d] = X.B2[d];
+      W.P[d] = X.P2[d];
+      W.Q[d] = X.Q2[d];
     }
-    if (mask & PIC_PHASE_IONIZE) {
-      prof_begin(h, PIC_PROF_IONIZE);
-      k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    W.Jclear = X.J4b;
+    const int ntx = (P.g.nx + FTX - 1) / FTX, nty = (P.g.ny + FTY - 1) / FTY;
+    const int nch = (P.g.nz + 1 + FZ - 1) / FZ;
+    k_fields<R><<<ntx * nty * nch, FTHREADS, FSMEM_ELEMS * sizeof(R), s>>>(X, W, win ? 1 : 0);
+    prof_end(h);
+    h->launches += 1;
+    for (int d = 0; d < 3; ++d) {
+      std::swap(X.d.E[d], X.E2[d]);
+      std::swap(X.d.B[d], X.B2[d]);
+      std::swap(X.d.P[d], X.P2[d]);
+      std::swap(X.d.Q[d], X.Q2[d]);
+    }
+    std::swap(X.d.J4, X.J4b);
+    if (win) {
+      prof_begin(h, PIC_PROF_KELDYSH);
+      k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
       prof_end(h);
       h->launches += 1;
     }
+  } else if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
+    prof_begin(h, PIC_PROF_WINDOW);
+    PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
+    k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    prof_end(h);
+    prof_begin(h, PIC_PROF_KELDYSH);
+    k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
+    prof_end(h);
+    h->launches += 2;
+  }
+  if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
+    prof_begin(h, PIC_PROF_IONIZE);
+    k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    prof_end(h);
+    h->launches += 1;
   }
   if (mask & PIC_PHASE_ADVANCE) {
     prof_begin(h, PIC_PROF_OTHER);
@@ -492,6 +523,8 @@ template <class R>
 int init_state(pic_ctx *h) {
   const Plan &P = h->P;
   cudaStream_t s = h->stream;
+  PIC_CUDA(cudaFuncSetAttribute(k_fields<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(FSMEM_ELEMS * sizeof(R))));
   PIC_CUDA(cudaMemsetAsync(h->arena, 0, P.total, s));
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));

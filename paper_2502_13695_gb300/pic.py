@@ -25,7 +25,7 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_get_fields", "pic_set_fields", "pic_get_particles",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read"]
-PROF_NAMES = ["push", "bhalf", "efull", "window", "ionize", "sort", "other"]
+PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other"]
 
 
 class PicError(RuntimeError):
