@@ -184,6 +184,32 @@ __host__ __device__ __forceinline__ R dawson(R z) {
   return s * R(0.56418958354775628);  // 1/sqrt(pi)
 }
 
+// FP32 evaluation on the device: piecewise degree-8 polynomials on
+// [0.2, 5) (generated by gen_dawson_f32.py, 1.3e-7 relative), the series
+// above elsewhere.  FP64 keeps the exponential-sum method everywhere.
+#include "dawson_f32_table.inc"
+
+template <class R>
+__host__ __device__ __forceinline__ R dawson_w(R z) {
+  return dawson<R>(z);
+}
+template <>
+__host__ __device__ __forceinline__ float dawson_w<float>(float z) {
+#ifdef __CUDA_ARCH__
+  if (z >= PG_DAWSON_LO && z < 5.0f) {
+    const float u = (z - PG_DAWSON_LO) * PG_DAWSON_INV_W;
+    const int iv = min((int)u, PG_DAWSON_NINT - 1);
+    const float t = 2.0f * (u - (float)iv) - 1.0f;
+    const float *c = kDawsonF32[iv];
+    float acc = c[PG_DAWSON_DEG];
+#pragma unroll
+    for (int q = PG_DAWSON_DEG - 1; q >= 0; --q) acc = fmaf(acc, t, c[q]);
+    return acc;
+  }
+#endif
+  return dawson<float>(z);
+}
+
 // ---------------------------------------------------------------------------
 // Keldysh threshold (Sec. 2.1, corrected form) for one cell:
 //   gamma = kG / E, gamma1 = g^2/(1+g^2), gamma2 = 1/(1+g^2),
@@ -219,7 +245,7 @@ __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterm
   int n = 0;
   for (; n < nterms; ++n) {
     const R z = sqrt(cd * (base + R(n)));
-    const R term = rn * dawson<R>(z);
+    const R term = rn * dawson_w<R>(z);
     sum += term;
     if (z > R(0.9242) && term * tail <= R(0.5) * Eps<R>::v() * sum) {
       ++n;

@@ -114,23 +114,74 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
     }
   };
 
+  // Global inputs of one plane, loaded into registers one iteration ahead so
+  // that their latency overlaps the E^n plane load: B^n on the B^{n+1/2}
+  // region, J and P, Q on the E^{n+1} region (at most kPts points a thread).
+  constexpr int kPts = (FBX * FBY + FTHREADS - 1) / FTHREADS;
+  struct Pre {
+    R b[kPts][3];
+    R j[kPts][3];
+    R pq[kPts][6];
+  };
+  auto prefetch = [&](int k, Pre &pf) {
+    if (k < 0 || k > nz) return;
+    {
+      const int w = txe + 2, n = w * (tye + 2);
+#pragma unroll
+      for (int u = 0; u < kPts; ++u) {
+        const int q = tid + u * FTHREADS;
+        if (q < n) {
+          const int ly = q / w, lx = q - ly * w;
+          const long long o = (long long)k * nxy + wy(y0 - 1 + ly) * nx + wx(x0 - 1 + lx);
+          pf.b[u][0] = k < nz ? D.B[0][o] : R(0);
+          pf.b[u][1] = k < nz ? D.B[1][o] : R(0);
+          pf.b[u][2] = D.B[2][o];
+        }
+      }
+    }
+    {
+      const int w = txe + 1, n = w * (tye + 1);
+      const int L = k < nz ? D.layer_of_plane[k] : -1;
+#pragma unroll
+      for (int u = 0; u < kPts; ++u) {
+        const int q = tid + u * FTHREADS;
+        if (q < n) {
+          const int ly = q / w, lx = q - ly * w;
+          const int r = wy(y0 + ly) * nx + wx(x0 + lx);
+          const long long o = (long long)k * nxy + r;
+          load_j3(D.J4 + 4 * o, pf.j[u][0], pf.j[u][1], pf.j[u][2]);
+          if (L >= 0) {
+            const long long m = (long long)D.mplane[k] * nxy + r;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              pf.pq[u][d] = D.P[d][m];
+              pf.pq[u][3 + d] = D.Q[d][m];
+            }
+          }
+        }
+      }
+    }
+  };
+
   // B^{n+1/2}(k) on the region (txe+2) x (tye+2), same origin as E^n
-  auto half_B = [&](int k) {
+  auto half_B = [&](int k, const Pre &pf) {
     const R *e0 = En + slotE(k) * 3 * FEP;
     const R *e1 = (k < nz) ? En + slotE(k + 1) * 3 * FEP : nullptr;
     R *dst = Bh + (k & 1) * 3 * FBP;
     const int w = txe + 2, n = w * (tye + 2);
-    for (int q = tid; q < n; q += FTHREADS) {
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      const int q = tid + u * FTHREADS;
+      if (q >= n) continue;
       const int ly = q / w, lx = q - ly * w;
       const int l = ly * FEX + lx;
-      const long long o = (long long)k * nxy + wy(y0 - 1 + ly) * nx + wx(x0 - 1 + lx);
       const R ex = e0[l], ey = e0[FEP + l], ez = e0[2 * FEP + l];
       R bx = R(0), by = R(0);
       if (k < nz) {
-        bx = D.B[0][o] - h * ((e0[2 * FEP + l + FEX] - ez) * idy - (e1[FEP + l] - ey) * idz);
-        by = D.B[1][o] - h * ((e1[l] - ex) * idz - (e0[2 * FEP + l + 1] - ez) * idx);
+        bx = pf.b[u][0] - h * ((e0[2 * FEP + l + FEX] - ez) * idy - (e1[FEP + l] - ey) * idz);
+        by = pf.b[u][1] - h * ((e1[l] - ex) * idz - (e0[2 * FEP + l + 1] - ez) * idx);
       }
-      const R bz = D.B[2][o] - h * ((e0[FEP + l + 1] - ey) * idx - (e0[l + FEX] - ex) * idy);
+      const R bz = pf.b[u][2] - h * ((e0[FEP + l + 1] - ey) * idx - (e0[l + FEX] - ex) * idy);
       const int lb = ly * FBX + lx;
       dst[lb] = bx;
       dst[FBP + lb] = by;
@@ -140,7 +191,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
 
   // E^{n+1}(k) on the region (txe+1) x (tye+1), origin (x0, y0); owned points
   // (inside the tile and the chunk) are written to the output buffers
-  auto full_E = [&](int k) {
+  auto full_E = [&](int k, const Pre &pf) {
     const R *e0 = En + slotE(k) * 3 * FEP;
     const R *b0 = Bh + (k & 1) * 3 * FBP;
     const R *bm = (k > 0) ? Bh + ((k - 1) & 1) * 3 * FBP : nullptr;
@@ -156,7 +207,10 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       eyi = D.pol == 0 ? R(0) : R(einc);
     }
     const int w = txe + 1, n = w * (tye + 1);
-    for (int q = tid; q < n; q += FTHREADS) {
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      const int q = tid + u * FTHREADS;
+      if (q >= n) continue;
       const int ly = q / w, lx = q - ly * w;
       const int le = (ly + 1) * FEX + (lx + 1);  // in the E^n frame
       const int lb = (ly + 1) * FBX + (lx + 1);  // in the B^{n+1/2} frame
@@ -164,8 +218,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       const int r = gy * nx + gx;
       const long long o = (long long)k * nxy + r;
       const bool own = own_plane && lx < txe && ly < tye;
-      R jx, jy, jz;
-      load_j3(D.J4 + 4 * o, jx, jy, jz);
+      const R jx = pf.j[u][0], jy = pf.j[u][1], jz = pf.j[u][2];
       const R bz = b0[2 * FBP + lb];
       const R dBz_dy = (bz - b0[2 * FBP + lb - FBX]) * idy;
       const R dBz_dx = (bz - b0[2 * FBP + lb - 1]) * idx;
@@ -174,12 +227,12 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
       R px = R(0), py = R(0), pz = R(0), qx = R(0), qy = R(0), qz = R(0);
       if (m >= 0) {
-        px = D.P[0][m];
-        py = D.P[1][m];
-        pz = D.P[2][m];
-        qx = D.Q[0][m];
-        qy = D.Q[1][m];
-        qz = D.Q[2][m];
+        px = pf.pq[u][0];
+        py = pf.pq[u][1];
+        pz = pf.pq[u][2];
+        qx = pf.pq[u][3];
+        qy = pf.pq[u][4];
+        qz = pf.pq[u][5];
       }
       if (k == 0 || k == nz) {
         const R al = D.alpha, cc = R(kC);
@@ -271,23 +324,33 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
   };
 
   // prologue: E^n(k0-1 .. k0+1), B^{n+1/2}(k0-1, k0), E^{n+1}(k0)
-  if (k0 >= 1) load_En(k0 - 1);
-  load_En(k0);
-  if (k0 + 1 <= nz) load_En(k0 + 1);
-  __syncthreads();
-  if (k0 >= 1) half_B(k0 - 1);
-  half_B(k0);
-  __syncthreads();
-  full_E(k0);
-  __syncthreads();
+  {
+    Pre pa, pb;
+    prefetch(k0 - 1, pa);
+    prefetch(k0, pb);
+    if (k0 >= 1) load_En(k0 - 1);
+    load_En(k0);
+    if (k0 + 1 <= nz) load_En(k0 + 1);
+    __syncthreads();
+    if (k0 >= 1) half_B(k0 - 1, pa);
+    half_B(k0, pb);
+    __syncthreads();
+    full_E(k0, pb);
+    __syncthreads();
+  }
+  Pre cur;
+  prefetch(k0 + 1, cur);
   for (int q = k0; q < k1; ++q) {
+    Pre nxt;
+    if (q + 1 < k1) prefetch(q + 2, nxt);  // in flight during this plane
     if (q + 2 <= nz) load_En(q + 2);
     __syncthreads();
-    if (q + 1 <= nz) half_B(q + 1);
+    if (q + 1 <= nz) half_B(q + 1, cur);
     __syncthreads();
-    if (q + 1 <= nz) full_E(q + 1);
+    if (q + 1 <= nz) full_E(q + 1, cur);
     __syncthreads();
     finish(q);
+    cur = nxt;
   }
   const R tot = block_sum_r(joule);
   if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
