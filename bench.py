@@ -306,6 +306,71 @@ def run_native(args, rank, local, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_scan(args):
+    """Batched fluence scan: 64 instances 64x64x{128..512}, fluence 0.1-3
+    J cm^-2 log-spaced, FP32, advanced together from one CUDA graph, against
+    the same instances run one at a time on the same GPU.  Time-to-result of
+    an instance is measured from the start of its mode's run."""
+    import torch
+    from paper_2502_13695_gb300 import build, pic, workloads as wl
+    build.build()
+    cfgs = wl.config4(args.scan_instances)
+    steps = args.scan_steps
+    # batched: every instance on its own stream, one graph per 32-step period
+    sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
+    batch = pic.Batch(sims)
+    batch.step(32)  # capture + warm-up
+    batch.sync()
+    p0 = sum(s.info()["particle_steps"] for s in sims)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    batch.sync()
+    t_batch = time.perf_counter() - t0
+    p_batch = sum(s.info()["particle_steps"] for s in sims) - p0
+    cells = sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs) * steps
+    batch.close()
+    for s_ in sims:
+        s_.close()
+    del sims
+    torch.cuda.empty_cache()
+    # one at a time (each instance created, warmed 32 steps, then timed)
+    lat, t_seq, p_seq = [], 0.0, 0.0
+    for c in cfgs:
+        sim = pic.Simulation(c)
+        sim.step(32)
+        sim.sync()
+        q0 = sim.info()["particle_steps"]
+        t1 = time.perf_counter()
+        sim.step(steps)
+        sim.sync()
+        t_seq += time.perf_counter() - t1
+        lat.append(t_seq)
+        p_seq += sim.info()["particle_steps"] - q0
+        sim.close()
+        del sim
+    torch.cuda.empty_cache()
+    lat = sorted(lat)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+    line = {"metric": METRIC, "value": p_batch / t_batch, "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": 32, "ms_per_step": 1e3 * t_batch / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"fluence scan, {len(cfgs)} instances 64x64x(128..512)",
+                       "mode": "batched CUDA graph"},
+            "cell_updates_per_s": cells / t_batch,
+            "scan_time_to_result_s": {"batched_p50": t_batch, "batched_p99": t_batch,
+                                      "one_at_a_time_p50": pct(lat, 0.5),
+                                      "one_at_a_time_p99": pct(lat, 0.99)},
+            "one_at_a_time": {"particle_steps_per_s": p_seq / t_seq,
+                              "cell_updates_per_s": cells / t_seq, "total_s": t_seq},
+            "batched_total_s": t_batch}
+    print(json.dumps(line), flush=True)
+
+
 def _op(dist, name):
     if dist is None:
         return None
@@ -324,12 +389,18 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["silica", "scan"], default="silica")
+    ap.add_argument("--scan-instances", type=int, default=64)
+    ap.add_argument("--scan-steps", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", "1"))
         run_reference(args, rank, world, None)
+        return
+    if args.workload == "scan":
+        run_scan(args)
         return
     rank, local, world, dist = dist_setup(args.gpus)
     try:

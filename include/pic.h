@@ -247,6 +247,23 @@ int pic_set_material(pic_handle h, const uint32_t *alive, const double *win);
 int pic_get_scalars(pic_handle h, long long *step, double out[4]);
 int pic_set_scalars(pic_handle h, long long step, const double in[4]);
 
+/* ---- batches: many simulations advanced by one CUDA graph ----------------
+ * Advances uneven simulations together (the batched fluence scan): the
+ * batch captures one period of steps of every member into a CUDA graph, each
+ * member's kernels on that member's own stream, forked from and joined to
+ * the batch stream, and replays it; the period is the least common multiple
+ * of 2 sort_interval over the members, after which every member's buffers
+ * are back in their starting order.  Members keep their own state and may be
+ * read (or stepped alone) between batch calls; a member stepped alone makes
+ * the next batch call capture again.
+ *   members : n handles, each created on its own non-NULL stream
+ *   stream  : batch stream (non-NULL), also the stream batch calls order on
+ * pic_batch_step enqueues asynchronously on `stream`; errors as pic_step. */
+typedef struct pic_batch_ctx *pic_batch;
+int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *out);
+int pic_batch_step(pic_batch b, int n_steps);
+int pic_batch_destroy(pic_batch b);
+
 /* ---- allocation-free field energy -------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory, such as code that runs while a stream is being

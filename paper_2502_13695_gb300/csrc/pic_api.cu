@@ -655,6 +655,150 @@ int pic_create(const pic_grid *grid, const pic_material *mat, const pic_pulse *p
   return PIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pic_batch_ctx {
+  std::vector<pic_ctx *> m;
+  cudaStream_t stream = nullptr;
+  int period = 32;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> step_at_capture_end;  // members' host steps after capture
+  std::vector<long long> launches_per_period;  // kernels one replay runs per member
+  std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+long long gcd_ll(long long a, long long b) { return b ? gcd_ll(b, a % b) : a; }
+
+int batch_capture(pic_batch_ctx *b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaStream_t s = b->stream;
+  std::vector<long long> l0;
+  for (pic_ctx *h : b->m) l0.push_back(h->launches);
+  PIC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = PIC_OK;
+  cudaError_t e = cudaEventRecord(b->ev[0], s);
+  for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q)
+    e = cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0);
+  for (int st = 0; st < b->period && rc == PIC_OK && e == cudaSuccess; ++st)
+    for (size_t q = 0; q < b->m.size() && rc == PIC_OK; ++q) rc = enqueue_any(b->m[q], PIC_PHASE_ALL);
+  for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(b->ev[1 + q], b->m[q]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev[1 + q], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(PIC_ECUDA, std::string("graph capture: ") +
+                               cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return fail(PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  // the capture advanced every member's host state by one period; the first
+  // replay makes the device catch up
+  b->step_at_capture_end.clear();
+  b->launches_per_period.clear();
+  for (size_t q = 0; q < b->m.size(); ++q) {
+    b->step_at_capture_end.push_back(b->m[q]->step);
+    b->launches_per_period.push_back(b->m[q]->launches - l0[q]);
+  }
+  PIC_CUDA(cudaGraphLaunch(b->exec, s));
+  return PIC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *out) {
+  if (!members || n <= 0 || !stream || !out) return fail(PIC_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  pic_batch_ctx *b = new pic_batch_ctx();
+  b->stream = (cudaStream_t)stream;
+  long long per = 2;
+  for (int q = 0; q < n; ++q) {
+    pic_ctx *h = members[q];
+    if (!h || !h->stream || h->stream == b->stream) {
+      delete b;
+      return fail(PIC_EINVAL, "batch members need their own non-NULL streams");
+    }
+    if (h->profiling) {
+      delete b;
+      return fail(PIC_ESTATE, "a batch member is profiling");
+    }
+    const long long p2 = 2ll * h->P.g.sort_interval;
+    per = per / gcd_ll(per, p2) * p2;
+    b->m.push_back(h);
+  }
+  if (per > 4096) {
+    delete b;
+    return fail(PIC_EINVAL, "members' sort intervals give a graph period above 4096 steps");
+  }
+  b->period = (int)per;
+  b->ev.resize(n + 1);
+  for (auto &e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  *out = b;
+  return PIC_OK;
+}
+
+int pic_batch_step(pic_batch b, int n_steps) {
+  if (!b || n_steps < 0) return fail(PIC_EINVAL, "bad batch step arguments");
+  for (pic_ctx *h : b->m)
+    if (h->sticky) return fail(h->sticky, "a batch member holds a device error");
+  while (n_steps > 0) {
+    if (n_steps < b->period) {
+      // tail: members step one by one on their streams, ordered after the batch stream
+      PIC_CUDA(cudaEventRecord(b->ev[0], b->stream));
+      for (size_t q = 0; q < b->m.size(); ++q) {
+        PIC_CUDA(cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0));
+        for (int st = 0; st < n_steps; ++st) {
+          const int rc = enqueue_any(b->m[q], PIC_PHASE_ALL);
+          if (rc) return rc;
+        }
+        PIC_CUDA(cudaEventRecord(b->ev[1 + q], b->m[q]->stream));
+        PIC_CUDA(cudaStreamWaitEvent(b->stream, b->ev[1 + q], 0));
+      }
+      return PIC_OK;
+    }
+    bool valid = b->exec != nullptr && b->step_at_capture_end.size() == b->m.size();
+    for (size_t q = 0; valid && q < b->m.size(); ++q)
+      valid = b->m[q]->step == b->step_at_capture_end[q];
+    if (!valid) {
+      const int rc = batch_capture(b);
+      if (rc) return rc;
+    } else {
+      PIC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+      for (size_t q = 0; q < b->m.size(); ++q) {
+        b->m[q]->step += b->period;
+        b->m[q]->launches += b->launches_per_period[q];
+        b->step_at_capture_end[q] = b->m[q]->step;
+      }
+    }
+    n_steps -= b->period;
+  }
+  return PIC_OK;
+}
+
+int pic_batch_destroy(pic_batch b) {
+  if (!b) return PIC_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &e : b->ev) cudaEventDestroy(e);
+  delete b;
+  return PIC_OK;
+}
+
 int pic_profile(pic_handle h, int enable) {
   if (!h) return fail(PIC_EINVAL, "null handle");
   h->profiling = enable != 0;

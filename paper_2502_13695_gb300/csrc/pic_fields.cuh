@@ -13,6 +13,9 @@
 // recomputed redundantly, so the pass reads E, B, J, P, Q from the current
 // buffers and writes the owned points of the other buffers (double
 // buffering); J of the other buffer is cleared for the next deposit.
+// Global inputs move to shared memory with cp.async one plane iteration
+// ahead (E^n(q+3), B^n(q+2), J, P, Q(q+2) while plane q is computed), into
+// double-buffered staging, so DRAM latency overlaps a whole plane of work.
 #pragma once
 #include "pic_kernels.cuh"
 
@@ -23,7 +26,20 @@ constexpr int FEX = FTX + 3, FEY = FTY + 3;  // E^n region, origin (x0-1, y0-1)
 constexpr int FBX = FTX + 2, FBY = FTY + 2;  // B^{n+1/2} region, same origin
 constexpr int FFX = FTX + 1, FFY = FTY + 1;  // E^{n+1} region, origin (x0, y0)
 constexpr int FEP = FEX * FEY, FBP = FBX * FBY, FFP = FFX * FFY;
-constexpr int FSMEM_ELEMS = 9 * FEP + 6 * FBP + 6 * FFP;
+// shared memory, in reals: E^n ring (3 planes x 3), B^n staging (2 x 3),
+// J staging (2 x 4 interleaved), P, Q staging (2 x 6), B^{n+1/2} (2 x 3),
+// E^{n+1} (2 x 3)
+// (every region starts on a multiple of 4 reals: 16-byte cp.async needs
+// 16-byte aligned shared addresses)
+constexpr int fsm_al(int x) { return (x + 3) & ~3; }
+constexpr int FSM_EN = 0;
+constexpr int FSM_BN = fsm_al(FSM_EN + 9 * FEP);
+constexpr int FSM_J = fsm_al(FSM_BN + 6 * FBP);
+constexpr int FSM_PQ = fsm_al(FSM_J + 8 * FFP);
+constexpr int FSM_BH = fsm_al(FSM_PQ + 12 * FFP);
+constexpr int FSM_E1 = fsm_al(FSM_BH + 6 * FBP);
+constexpr int FSMEM_ELEMS = fsm_al(FSM_E1 + 6 * FFP);
+static_assert(FSM_J % 4 == 0 && (4 * FFP) % 4 == 0, "J staging must be 16-byte aligned");
 
 // Where the field pass writes (the non-current halves of the double buffers).
 template <class R>
@@ -31,6 +47,18 @@ struct FieldOut {
   R *E[3], *B[3], *P[3], *Q[3];
   R *Jclear;
 };
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <class R>
 __device__ __forceinline__ void window_update(const Ctx<R> &X, long long m, int k, R a) {
@@ -77,9 +105,13 @@ template <class R>
 __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, int do_window) {
   const Dev<R> &D = X.d;
   extern __shared__ __align__(16) unsigned char fsm_raw[];
-  R *const En = reinterpret_cast<R *>(fsm_raw);  // [3 slots][3 comps][FEP]
-  R *const Bh = En + 9 * FEP;                     // [2 slots][3][FBP]
-  R *const E1 = Bh + 6 * FBP;                     // [2 slots][3][FFP]
+  R *const sm = reinterpret_cast<R *>(fsm_raw);
+  R *const En = sm + FSM_EN;  // [3 slots][3][FEP]
+  R *const Bn = sm + FSM_BN;  // [2 slots][3][FBP]
+  R *const Js = sm + FSM_J;   // [2 slots][FFP][4]
+  R *const PQ = sm + FSM_PQ;  // [2 slots][6][FFP]
+  R *const Bh = sm + FSM_BH;  // [2 slots][3][FBP]
+  R *const E1 = sm + FSM_E1;  // [2 slots][3][FFP]
   const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
   const int ntx = (nx + FTX - 1) / FTX, nty = (ny + FTY - 1) / FTY;
   int bid = blockIdx.x;
@@ -100,89 +132,81 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
   auto wy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
   auto slotE = [](int k) { return ((k % 3) + 3) % 3; };
 
-  // E^n plane k -> slot, region origin (x0-1, y0-1), size (txe+3) x (tye+3)
-  auto load_En = [&](int k) {
+  // asynchronous staging of plane k's inputs (nothing for planes outside 0..nz)
+  auto stage_En = [&](int k) {
+    if (k < 0 || k > nz) return;
     R *dst = En + slotE(k) * 3 * FEP;
     const int w = txe + 3, n = w * (tye + 3);
     for (int q = tid; q < n; q += FTHREADS) {
       const int ly = q / w, lx = q - ly * w;
       const long long o = (long long)k * nxy + wy(y0 - 1 + ly) * nx + wx(x0 - 1 + lx);
       const int l = ly * FEX + lx;
-      dst[l] = D.E[0][o];
-      dst[FEP + l] = D.E[1][o];
-      dst[2 * FEP + l] = D.E[2][o];
+      cp_async<sizeof(R)>(dst + l, D.E[0] + o);
+      cp_async<sizeof(R)>(dst + FEP + l, D.E[1] + o);
+      cp_async<sizeof(R)>(dst + 2 * FEP + l, D.E[2] + o);
     }
   };
-
-  // Global inputs of one plane, loaded into registers one iteration ahead so
-  // that their latency overlaps the E^n plane load: B^n on the B^{n+1/2}
-  // region, J and P, Q on the E^{n+1} region (at most kPts points a thread).
-  constexpr int kPts = (FBX * FBY + FTHREADS - 1) / FTHREADS;
-  struct Pre {
-    R b[kPts][3];
-    R j[kPts][3];
-    R pq[kPts][6];
-  };
-  auto prefetch = [&](int k, Pre &pf) {
+  auto stage_Bn = [&](int k) {
     if (k < 0 || k > nz) return;
-    {
-      const int w = txe + 2, n = w * (tye + 2);
-#pragma unroll
-      for (int u = 0; u < kPts; ++u) {
-        const int q = tid + u * FTHREADS;
-        if (q < n) {
-          const int ly = q / w, lx = q - ly * w;
-          const long long o = (long long)k * nxy + wy(y0 - 1 + ly) * nx + wx(x0 - 1 + lx);
-          pf.b[u][0] = k < nz ? D.B[0][o] : R(0);
-          pf.b[u][1] = k < nz ? D.B[1][o] : R(0);
-          pf.b[u][2] = D.B[2][o];
-        }
+    R *dst = Bn + (k & 1) * 3 * FBP;
+    const int w = txe + 2, n = w * (tye + 2);
+    for (int q = tid; q < n; q += FTHREADS) {
+      const int ly = q / w, lx = q - ly * w;
+      const long long o = (long long)k * nxy + wy(y0 - 1 + ly) * nx + wx(x0 - 1 + lx);
+      const int l = ly * FBX + lx;
+      if (k < nz) {
+        cp_async<sizeof(R)>(dst + l, D.B[0] + o);
+        cp_async<sizeof(R)>(dst + FBP + l, D.B[1] + o);
       }
+      cp_async<sizeof(R)>(dst + 2 * FBP + l, D.B[2] + o);
     }
-    {
-      const int w = txe + 1, n = w * (tye + 1);
-      const int L = k < nz ? D.layer_of_plane[k] : -1;
+  };
+  auto stage_JPQ = [&](int k) {
+    if (k < 0 || k > nz) return;
+    R *js = Js + (k & 1) * 4 * FFP;
+    R *pq = PQ + (k & 1) * 6 * FFP;
+    const int L = k < nz ? D.layer_of_plane[k] : -1;
+    const int w = txe + 1, n = w * (tye + 1);
+    for (int q = tid; q < n; q += FTHREADS) {
+      const int ly = q / w, lx = q - ly * w;
+      const int r = wy(y0 + ly) * nx + wx(x0 + lx);
+      const long long o = (long long)k * nxy + r;
+      const int l = ly * FFX + lx;
+      if (sizeof(R) == 4) {
+        cp_async<16>(js + 4 * l, D.J4 + 4 * o);
+      } else {
+        cp_async<16>(js + 4 * l, D.J4 + 4 * o);
+        cp_async<16>(js + 4 * l + 2, D.J4 + 4 * o + 2);
+      }
+      if (L >= 0) {
+        const long long m = (long long)D.mplane[k] * nxy + r;
 #pragma unroll
-      for (int u = 0; u < kPts; ++u) {
-        const int q = tid + u * FTHREADS;
-        if (q < n) {
-          const int ly = q / w, lx = q - ly * w;
-          const int r = wy(y0 + ly) * nx + wx(x0 + lx);
-          const long long o = (long long)k * nxy + r;
-          load_j3(D.J4 + 4 * o, pf.j[u][0], pf.j[u][1], pf.j[u][2]);
-          if (L >= 0) {
-            const long long m = (long long)D.mplane[k] * nxy + r;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              pf.pq[u][d] = D.P[d][m];
-              pf.pq[u][3 + d] = D.Q[d][m];
-            }
-          }
+        for (int d = 0; d < 3; ++d) {
+          cp_async<sizeof(R)>(pq + d * FFP + l, D.P[d] + m);
+          cp_async<sizeof(R)>(pq + (3 + d) * FFP + l, D.Q[d] + m);
         }
       }
     }
   };
 
   // B^{n+1/2}(k) on the region (txe+2) x (tye+2), same origin as E^n
-  auto half_B = [&](int k, const Pre &pf) {
+  auto half_B = [&](int k) {
     const R *e0 = En + slotE(k) * 3 * FEP;
     const R *e1 = (k < nz) ? En + slotE(k + 1) * 3 * FEP : nullptr;
+    const R *bn = Bn + (k & 1) * 3 * FBP;
     R *dst = Bh + (k & 1) * 3 * FBP;
     const int w = txe + 2, n = w * (tye + 2);
-#pragma unroll
-    for (int u = 0; u < kPts; ++u) {
-      const int q = tid + u * FTHREADS;
-      if (q >= n) continue;
+    for (int q = tid; q < n; q += FTHREADS) {
       const int ly = q / w, lx = q - ly * w;
       const int l = ly * FEX + lx;
+      const int lb = ly * FBX + lx;
       const R ex = e0[l], ey = e0[FEP + l], ez = e0[2 * FEP + l];
       R bx = R(0), by = R(0);
       if (k < nz) {
-        bx = pf.b[u][0] - h * ((e0[2 * FEP + l + FEX] - ez) * idy - (e1[FEP + l] - ey) * idz);
-        by = pf.b[u][1] - h * ((e1[l] - ex) * idz - (e0[2 * FEP + l + 1] - ez) * idx);
+        bx = bn[lb] - h * ((e0[2 * FEP + l + FEX] - ez) * idy - (e1[FEP + l] - ey) * idz);
+        by = bn[FBP + lb] - h * ((e1[l] - ex) * idz - (e0[2 * FEP + l + 1] - ez) * idx);
       }
-      const R bz = pf.b[u][2] - h * ((e0[FEP + l + 1] - ey) * idx - (e0[l + FEX] - ex) * idy);
-      const int lb = ly * FBX + lx;
+      const R bz = bn[2 * FBP + lb] - h * ((e0[FEP + l + 1] - ey) * idx - (e0[l + FEX] - ex) * idy);
       dst[lb] = bx;
       dst[FBP + lb] = by;
       dst[2 * FBP + lb] = bz;
@@ -191,10 +215,12 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
 
   // E^{n+1}(k) on the region (txe+1) x (tye+1), origin (x0, y0); owned points
   // (inside the tile and the chunk) are written to the output buffers
-  auto full_E = [&](int k, const Pre &pf) {
+  auto full_E = [&](int k) {
     const R *e0 = En + slotE(k) * 3 * FEP;
     const R *b0 = Bh + (k & 1) * 3 * FBP;
     const R *bm = (k > 0) ? Bh + ((k - 1) & 1) * 3 * FBP : nullptr;
+    const R *js = Js + (k & 1) * 4 * FFP;
+    const R *pq = PQ + (k & 1) * 6 * FFP;
     R *dst = E1 + (k & 1) * 3 * FFP;
     const int L = k < nz ? D.layer_of_plane[k] : -1;
     const bool own_plane = k >= k0 && k < k1;
@@ -207,32 +233,26 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       eyi = D.pol == 0 ? R(0) : R(einc);
     }
     const int w = txe + 1, n = w * (tye + 1);
-#pragma unroll
-    for (int u = 0; u < kPts; ++u) {
-      const int q = tid + u * FTHREADS;
-      if (q >= n) continue;
+    for (int q = tid; q < n; q += FTHREADS) {
       const int ly = q / w, lx = q - ly * w;
       const int le = (ly + 1) * FEX + (lx + 1);  // in the E^n frame
       const int lb = (ly + 1) * FBX + (lx + 1);  // in the B^{n+1/2} frame
-      const int gx = wx(x0 + lx), gy = wy(y0 + ly);
-      const int r = gy * nx + gx;
-      const long long o = (long long)k * nxy + r;
+      const int lf = ly * FFX + lx;
       const bool own = own_plane && lx < txe && ly < tye;
-      const R jx = pf.j[u][0], jy = pf.j[u][1], jz = pf.j[u][2];
+      const R jx = js[4 * lf], jy = js[4 * lf + 1], jz = js[4 * lf + 2];
       const R bz = b0[2 * FBP + lb];
       const R dBz_dy = (bz - b0[2 * FBP + lb - FBX]) * idy;
       const R dBz_dx = (bz - b0[2 * FBP + lb - 1]) * idx;
       const R ex0 = e0[le], ey0 = e0[FEP + le], ez0 = e0[2 * FEP + le];
       R ex1, ey1, ez1 = R(0);
-      const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
       R px = R(0), py = R(0), pz = R(0), qx = R(0), qy = R(0), qz = R(0);
-      if (m >= 0) {
-        px = pf.pq[u][0];
-        py = pf.pq[u][1];
-        pz = pf.pq[u][2];
-        qx = pf.pq[u][3];
-        qy = pf.pq[u][4];
-        qz = pf.pq[u][5];
+      if (L >= 0) {
+        px = pq[lf];
+        py = pq[FFP + lf];
+        pz = pq[2 * FFP + lf];
+        qx = pq[3 * FFP + lf];
+        qy = pq[4 * FFP + lf];
+        qz = pq[5 * FFP + lf];
       }
       if (k == 0 || k == nz) {
         const R al = D.alpha, cc = R(kC);
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       } else {
         const R ax = c2dt * (dBz_dy - (b0[FBP + lb] - bm[FBP + lb]) * idz) - dtie * jx;
         const R ay = c2dt * ((b0[lb] - bm[lb]) * idz - dBz_dx) - dtie * jy;
-        if (m >= 0) {
+        if (L >= 0) {
           const LayerR<R> &Ly = X.lr[L];
           ex1 = e_point(Ly, ex0, ax, px, qx);
           ey1 = e_point(Ly, ey0, ay, py, qy);
@@ -261,20 +281,22 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
       if (k < nz) {
         const R az = c2dt * ((b0[FBP + lb] - b0[FBP + lb - 1]) * idx - (b0[lb] - b0[lb - FBX]) * idy) -
                      dtie * jz;
-        if (m >= 0)
+        if (L >= 0)
           ez1 = e_point(X.lr[L], ez0, az, pz, qz);
         else
           ez1 = ez0 + az;
       }
-      const int lf = ly * FFX + lx;
       dst[lf] = ex1;
       dst[FFP + lf] = ey1;
       dst[2 * FFP + lf] = ez1;
       if (own) {
+        const int r = (y0 + ly) * nx + (x0 + lx);
+        const long long o = (long long)k * nxy + r;
         W.E[0][o] = ex1;
         W.E[1][o] = ey1;
         W.E[2][o] = ez1;
-        if (m >= 0) {
+        if (L >= 0) {
+          const long long m = (long long)D.mplane[k] * nxy + r;
           W.P[0][m] = px;
           W.P[1][m] = py;
           W.P[2][m] = pz;
@@ -324,34 +346,41 @@ __global__ void __launch_bounds__(FTHREADS) k_fields(Ctx<R> X, FieldOut<R> W, in
   };
 
   // prologue: E^n(k0-1 .. k0+1), B^{n+1/2}(k0-1, k0), E^{n+1}(k0)
-  {
-    Pre pa, pb;
-    prefetch(k0 - 1, pa);
-    prefetch(k0, pb);
-    if (k0 >= 1) load_En(k0 - 1);
-    load_En(k0);
-    if (k0 + 1 <= nz) load_En(k0 + 1);
-    __syncthreads();
-    if (k0 >= 1) half_B(k0 - 1, pa);
-    half_B(k0, pb);
-    __syncthreads();
-    full_E(k0, pb);
-    __syncthreads();
-  }
-  Pre cur;
-  prefetch(k0 + 1, cur);
+  stage_En(k0 - 1);
+  stage_En(k0);
+  stage_En(k0 + 1);
+  stage_Bn(k0 - 1);
+  stage_Bn(k0);
+  stage_JPQ(k0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  if (k0 >= 1) half_B(k0 - 1);
+  half_B(k0);
+  __syncthreads();
+  full_E(k0);
+  __syncthreads();
+  // inputs of the first loop iteration
+  stage_En(k0 + 2);
+  stage_Bn(k0 + 1);
+  stage_JPQ(k0 + 1);
+  cp_async_commit();
   for (int q = k0; q < k1; ++q) {
-    Pre nxt;
-    if (q + 1 < k1) prefetch(q + 2, nxt);  // in flight during this plane
-    if (q + 2 <= nz) load_En(q + 2);
+    cp_async_wait_all();  // E^n(q+2), B^n(q+1), J/P/Q(q+1) have landed
     __syncthreads();
-    if (q + 1 <= nz) half_B(q + 1, cur);
+    if (q + 1 < k1) {      // next plane's inputs, in flight during this one
+      stage_En(q + 3);
+      stage_Bn(q + 2);
+      stage_JPQ(q + 2);
+    }
+    cp_async_commit();
+    if (q + 1 <= nz) half_B(q + 1);
     __syncthreads();
-    if (q + 1 <= nz) full_E(q + 1, cur);
+    if (q + 1 <= nz) full_E(q + 1);
     __syncthreads();
     finish(q);
-    cur = nxt;
   }
+  cp_async_wait_all();
   const R tot = block_sum_r(joule);
   if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
 }

@@ -24,7 +24,8 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_diagnostics", "pic_info_get", "pic_destroy", "pic_last_error",
            "pic_get_fields", "pic_set_fields", "pic_get_particles",
            "pic_set_particles", "pic_get_material", "pic_set_material",
-           "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read"]
+           "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
+           "pic_batch_create", "pic_batch_step", "pic_batch_destroy"]
 PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other"]
 
 
@@ -119,6 +120,9 @@ def lib():
         L.pic_get_scalars.argtypes = [vp, P(ll), vp]
         L.pic_set_scalars.argtypes = [vp, ll, vp]
         L.pic_profile.argtypes = [vp, i]
+        L.pic_batch_create.argtypes = [P(vp), i, vp, P(vp)]
+        L.pic_batch_step.argtypes = [vp, i]
+        L.pic_batch_destroy.argtypes = [vp]
         L.pic_profile_read.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
@@ -326,3 +330,37 @@ class Simulation:
         self.set_particles(st["particles"])
         mat = st["material"]
         self.set_material(mat["alive"], mat.get("win"))
+
+
+class Batch:
+    """Simulations advanced together from one CUDA graph (see pic_batch_*).
+    Every member must have been created on its own stream."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.sims = list(sims)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (ctypes.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        h = ctypes.c_void_p()
+        _check(lib().pic_batch_create(arr, len(self.sims), ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n: int):
+        _check(lib().pic_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self.stream.synchronize()
+        for s in self.sims:
+            s.sync()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().pic_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
