@@ -129,7 +129,7 @@ typedef struct {
   long long n_neutrals;      /* initial neutral macroparticles */
   long long capacity;        /* charged-particle slots */
   long long n_particles;     /* charged-particle slots in use (pic_info) */
-  long long step;            /* steps taken (pic_info) */
+  long long step;            /* steps the device has completed (pic_info) */
   size_t arena_bytes;        /* device bytes pic_create needs */
   long long launches;        /* kernels launched on the handle so far (pic_info) */
   double particle_steps;     /* charged-particle pushes done so far (pic_info) */
@@ -137,9 +137,9 @@ typedef struct {
 
 /* Kernel classes reported by pic_profile_read. */
 #define PIC_PROF_PUSH 0    /* gather + Boris + deposit */
-#define PIC_PROF_FIELDS 1  /* fused B half, E + polarisation + faces, B half, window */
+#define PIC_PROF_FIELDS 1  /* B half step, E + polarisation + z faces, B half step */
 #define PIC_PROF_KELDYSH 2 /* Keldysh thresholds of the cells whose amplitude changed */
-#define PIC_PROF_WINDOW 3  /* window alone (window phase without the field phase) */
+#define PIC_PROF_WINDOW 3  /* cell-centred |E| window and Keldysh cache check */
 #define PIC_PROF_IONIZE 4  /* ionisation draws + pair appends */
 #define PIC_PROF_SORT 5    /* pool sort (all its kernels) */
 #define PIC_PROF_OTHER 6   /* step counter */

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpicgb300.so")
 SOURCES = [os.path.join(CSRC, "pic_api.cu"), os.path.join(CSRC, "pic_noalloc.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("pic_device.cuh", "pic_kernels.cuh", "pic_fields.cuh",
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("pic_device.cuh", "pic_kernels.cuh",
                                                   "dawson_f32_table.inc")] + [
     os.path.join(os.path.dirname(HERE), "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -11,7 +11,6 @@
 
 #include "../../include/pic.h"
 #include "pic_kernels.cuh"
-#include "pic_fields.cuh"
 
 using namespace pg;
 
@@ -50,7 +49,6 @@ struct Plan {
   int nb_scan, diag_blocks_p, diag_blocks_g;
   // arena offsets
   size_t off_E[3], off_B[3], off_J4, off_P[3], off_Q[3];
-  size_t off_E2[3], off_B2[3], off_J4b, off_P2[3], off_Q2[3];
   size_t off_lop, off_mplane, off_kplane, off_lk, off_lr;
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
@@ -138,11 +136,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_J4 = take(P.nfield * 4 * R);
   for (int d = 0; d < 3; ++d) P.off_P[d] = take(P.nmat * R);
   for (int d = 0; d < 3; ++d) P.off_Q[d] = take(P.nmat * R);
-  for (int d = 0; d < 3; ++d) P.off_E2[d] = take(P.nfield * R);
-  for (int d = 0; d < 3; ++d) P.off_B2[d] = take(P.nfield * R);
-  P.off_J4b = take(P.nfield * 4 * R);
-  for (int d = 0; d < 3; ++d) P.off_P2[d] = take(P.nmat * R);
-  for (int d = 0; d < 3; ++d) P.off_Q2[d] = take(P.nmat * R);
+
   P.off_lop = take(g.nz * sizeof(int));
   P.off_mplane = take(g.nz * sizeof(int));
   P.off_kplane = take(std::max(1, P.n_mplanes) * sizeof(int));
@@ -347,12 +341,7 @@ void bind(pic_ctx *h) {
     D.B[d] = (R *)(A + P.off_B[d]);
     D.P[d] = (R *)(A + P.off_P[d]);
     D.Q[d] = (R *)(A + P.off_Q[d]);
-    X.E2[d] = (R *)(A + P.off_E2[d]);
-    X.B2[d] = (R *)(A + P.off_B2[d]);
-    X.P2[d] = (R *)(A + P.off_P2[d]);
-    X.Q2[d] = (R *)(A + P.off_Q2[d]);
   }
-  X.J4b = (R *)(A + P.off_J4b);
   D.J4 = (R *)(A + P.off_J4);
   D.layer_of_plane = (const int *)(A + P.off_lop);
   D.mplane = (const int *)(A + P.off_mplane);
@@ -455,37 +444,14 @@ int enqueue(pic_ctx *h, int mask) {
     h->launches += 1;
   }
   if (mask & PIC_PHASE_FIELDS) {
-    // fused field pass (with the window when that phase is requested too)
-    const bool win = (mask & PIC_PHASE_WINDOW) && P.nmat > 0;
     prof_begin(h, PIC_PROF_FIELDS);
-    if (win) PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
-    FieldOut<R> W;
-    for (int d = 0; d < 3; ++d) {
-      W.E[d] = X.E2[d];
-      W.B[d] = X.B2[d];
-      W.P[d] = X.P2[d];
-      W.Q[d] = X.Q2[d];
-    }
-    W.Jclear = X.J4b;
-    const int ntx = (P.g.nx + FTX - 1) / FTX, nty = (P.g.ny + FTY - 1) / FTY;
-    const int nch = (P.g.nz + 1 + FZ - 1) / FZ;
-    k_fields<R><<<ntx * nty * nch, FTHREADS, FSMEM_ELEMS * sizeof(R), s>>>(X, W, win ? 1 : 0);
+    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
+    k_efull<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X);
+    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
     prof_end(h);
-    h->launches += 1;
-    for (int d = 0; d < 3; ++d) {
-      std::swap(X.d.E[d], X.E2[d]);
-      std::swap(X.d.B[d], X.B2[d]);
-      std::swap(X.d.P[d], X.P2[d]);
-      std::swap(X.d.Q[d], X.Q2[d]);
-    }
-    std::swap(X.d.J4, X.J4b);
-    if (win) {
-      prof_begin(h, PIC_PROF_KELDYSH);
-      k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
-      prof_end(h);
-      h->launches += 1;
-    }
-  } else if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
+    h->launches += 3;
+  }
+  if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
     prof_begin(h, PIC_PROF_WINDOW);
     PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
     k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
@@ -523,8 +489,6 @@ template <class R>
 int init_state(pic_ctx *h) {
   const Plan &P = h->P;
   cudaStream_t s = h->stream;
-  PIC_CUDA(cudaFuncSetAttribute(k_fields<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(FSMEM_ELEMS * sizeof(R))));
   PIC_CUDA(cudaMemsetAsync(h->arena, 0, P.total, s));
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));
@@ -877,7 +841,10 @@ int pic_info_get(pic_handle h, pic_info *out) {
   const int rc = copy_out(h, P.off_nslots, &ns, 8);
   if (rc) return rc;
   out->n_particles = (long long)std::min<unsigned long long>(ns, P.cap);
-  out->step = h->step;
+  long long dstep = 0;
+  const int rc1 = copy_out(h, P.off_step, &dstep, 8);
+  if (rc1) return rc1;
+  out->step = dstep;
   out->launches = h->launches;
   double acc[5];
   const int rc2 = copy_out(h, P.off_acc, acc, sizeof(acc));

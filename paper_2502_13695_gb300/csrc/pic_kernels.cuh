@@ -42,8 +42,6 @@ struct Ctx {
   // per-neutral leave steps in units of 64 steps (nmat x ppc_max)
   uint16_t *leave16;
   int ppc_max;
-  // the other halves of the double-buffered field state
-  R *E2[3], *B2[3], *J4b, *P2[3], *Q2[3];
 };
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
