@@ -371,6 +371,62 @@ def run_scan(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving trace: Poisson arrivals (4/s) of silica or 10-pair mirror
+    requests on grids 32^3 .. 128x128x512, 500-2000 steps, FP32, admitted
+    against a 150 GB budget with continuous batching; compared with serving
+    the same trace one request at a time (FIFO, each request's service time
+    measured alone on the same GPU)."""
+    import torch
+    from paper_2502_13695_gb300 import build, pic, serve, workloads as wl
+    build.build()
+    trace = wl.config5(args.serve_requests)
+    reqs = [serve.Request(q, t["cfg"], t["cfg"]["steps"], t["arrival_s"]) for q, t in enumerate(trace)]
+    # one at a time: service time of every request alone, then FIFO in time
+    service = []
+    psteps_alone = 0.0
+    for r in reqs:
+        sim = pic.Simulation(r.cfg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(r.steps)
+        sim.sync()
+        service.append(time.perf_counter() - t0)
+        psteps_alone += sim.info()["particle_steps"]
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    free_at, fifo = 0.0, []
+    for r, sv in zip(reqs, service):
+        start = max(r.arrival_s, free_at)
+        free_at = start + sv
+        fifo.append(free_at - r.arrival_s)
+    # continuous batching in real time
+    srv = serve.Server(budget_bytes=150e9)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    lat = sorted(r.time_to_result_s for r in res)
+    fifo = sorted(fifo)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+    line = {"metric": METRIC, "value": psteps_alone / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": sum(r.steps for r in reqs), "warmup": 0,
+            "ms_per_step": 1e3 * wall / max(1, sum(r.steps for r in reqs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving trace, {len(reqs)} requests, Poisson 4/s, "
+                                   "budget 150 GB", "mode": "continuous batching"},
+            "serve_time_to_result_s": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99),
+                                       "one_at_a_time_p50": pct(fifo, 0.5),
+                                       "one_at_a_time_p99": pct(fifo, 0.99)},
+            "serve_wall_s": wall, "one_at_a_time_busy_s": sum(service),
+            "last_arrival_s": reqs[-1].arrival_s}
+    print(json.dumps(line), flush=True)
+
+
 def _op(dist, name):
     if dist is None:
         return None
@@ -389,7 +445,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["silica", "scan"], default="silica")
+    ap.add_argument("--workload", choices=["silica", "scan", "serve"], default="silica")
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--scan-instances", type=int, default=64)
     ap.add_argument("--scan-steps", type=int, default=1000)
     args = ap.parse_args()
@@ -401,6 +458,9 @@ def main():
         return
     if args.workload == "scan":
         run_scan(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     rank, local, world, dist = dist_setup(args.gpus)
     try:
