@@ -256,12 +256,16 @@ int pic_set_scalars(pic_handle h, long long step, const double in[4]);
  * are back in their starting order.  Members keep their own state and may be
  * read (or stepped alone) between batch calls; a member stepped alone makes
  * the next batch call capture again.
- *   members : n handles, each created on its own non-NULL stream
- *   stream  : batch stream (non-NULL), also the stream batch calls order on
- * pic_batch_step enqueues asynchronously on `stream`; errors as pic_step. */
+ *   members : n handles, each created on a non-NULL stream (members may share
+ *             one, which serialises them)
+ *   stream  : batch stream, not a member's; NULL lets the batch create and
+ *             own one
+ * pic_batch_step enqueues asynchronously; pic_batch_sync waits for the batch
+ * and reports member errors as pic_sync does. */
 typedef struct pic_batch_ctx *pic_batch;
 int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *out);
 int pic_batch_step(pic_batch b, int n_steps);
+int pic_batch_sync(pic_batch b);
 int pic_batch_destroy(pic_batch b);
 
 /* ---- allocation-free field energy -------------------------------------

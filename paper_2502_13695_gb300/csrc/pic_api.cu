@@ -463,7 +463,7 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
     prof_begin(h, PIC_PROF_IONIZE);
-    k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    k_ionize<R><<<grid_blocks(P.nmat * ((P.ppc_max + 1) / 2)), kThreads, 0, s>>>(X);
     prof_end(h);
     h->launches += 1;
   }
@@ -627,6 +627,7 @@ int pic_create(const pic_grid *grid, const pic_material *mat, const pic_pulse *p
 struct pic_batch_ctx {
   std::vector<pic_ctx *> m;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;
   int period = 32;
   cudaGraphExec_t exec = nullptr;
   std::vector<long long> step_at_capture_end;  // members' host steps after capture
@@ -686,18 +687,29 @@ int batch_capture(pic_batch_ctx *b) {
 extern "C" {
 
 int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *out) {
-  if (!members || n <= 0 || !stream || !out) return fail(PIC_EINVAL, "bad batch arguments");
+  if (!members || n <= 0 || !out) return fail(PIC_EINVAL, "bad batch arguments");
   *out = nullptr;
   pic_batch_ctx *b = new pic_batch_ctx();
-  b->stream = (cudaStream_t)stream;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    const cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return fail(PIC_ECUDA, std::string("cudaStreamCreateWithFlags: ") + cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
   long long per = 2;
   for (int q = 0; q < n; ++q) {
     pic_ctx *h = members[q];
     if (!h || !h->stream || h->stream == b->stream) {
+      if (b->own_stream) cudaStreamDestroy(b->stream);
       delete b;
-      return fail(PIC_EINVAL, "batch members need their own non-NULL streams");
+      return fail(PIC_EINVAL, "batch members need non-NULL streams other than the batch stream");
     }
     if (h->profiling) {
+      if (b->own_stream) cudaStreamDestroy(b->stream);
       delete b;
       return fail(PIC_ESTATE, "a batch member is profiling");
     }
@@ -706,6 +718,7 @@ int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *
     b->m.push_back(h);
   }
   if (per > 4096) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return fail(PIC_EINVAL, "members' sort intervals give a graph period above 4096 steps");
   }
@@ -754,11 +767,22 @@ int pic_batch_step(pic_batch b, int n_steps) {
   return PIC_OK;
 }
 
+int pic_batch_sync(pic_batch b) {
+  if (!b) return fail(PIC_EINVAL, "null batch");
+  PIC_CUDA(cudaStreamSynchronize(b->stream));
+  for (pic_ctx *h : b->m) {
+    const int rc = pic_sync(h);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
 int pic_batch_destroy(pic_batch b) {
   if (!b) return PIC_OK;
   cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (auto &e : b->ev) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return PIC_OK;
 }

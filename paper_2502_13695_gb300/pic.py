@@ -25,7 +25,7 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_get_fields", "pic_set_fields", "pic_get_particles",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
-           "pic_batch_create", "pic_batch_step", "pic_batch_destroy"]
+           "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy"]
 PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other"]
 
 
@@ -122,6 +122,7 @@ def lib():
         L.pic_profile.argtypes = [vp, i]
         L.pic_batch_create.argtypes = [P(vp), i, vp, P(vp)]
         L.pic_batch_step.argtypes = [vp, i]
+        L.pic_batch_sync.argtypes = [vp]
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_profile_read.argtypes = [vp, vp, vp]
         _lib = L
@@ -337,22 +338,19 @@ class Batch:
     Every member must have been created on its own stream."""
 
     def __init__(self, sims, stream=None):
-        import torch
         self.sims = list(sims)
-        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream = stream  # None: the batch owns a private stream
         arr = (ctypes.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
         h = ctypes.c_void_p()
-        _check(lib().pic_batch_create(arr, len(self.sims), ctypes.c_void_p(self.stream.cuda_stream),
-                                      ctypes.byref(h)))
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(lib().pic_batch_create(arr, len(self.sims), sp, ctypes.byref(h)))
         self._h = h
 
     def step(self, n: int):
         _check(lib().pic_batch_step(self._h, int(n)))
 
     def sync(self):
-        self.stream.synchronize()
-        for s in self.sims:
-            s.sync()
+        _check(lib().pic_batch_sync(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
