@@ -463,7 +463,7 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
     prof_begin(h, PIC_PROF_IONIZE);
-    k_ionize<R><<<grid_blocks(P.nmat * ((P.ppc_max + 1) / 2)), kThreads, 0, s>>>(X);
+    k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
     prof_end(h);
     h->launches += 1;
   }
@@ -638,6 +638,24 @@ struct pic_batch_ctx {
 namespace {
 long long gcd_ll(long long a, long long b) { return b ? gcd_ll(b, a % b) : a; }
 
+// Work already queued on a member's own stream (a pic_step outside the batch)
+// comes before the batch's next graph: the batch stream waits on every member.
+int join_members_into_batch(pic_batch_ctx *b) {
+  for (size_t q = 0; q < b->m.size(); ++q) {
+    PIC_CUDA(cudaEventRecord(b->ev[1 + q], b->m[q]->stream));
+    PIC_CUDA(cudaStreamWaitEvent(b->stream, b->ev[1 + q], 0));
+  }
+  return PIC_OK;
+}
+
+// And a member's later work (its own pic_step, state reads after pic_sync)
+// comes after the graph: every member stream waits on the batch stream.
+int join_batch_into_members(pic_batch_ctx *b) {
+  PIC_CUDA(cudaEventRecord(b->ev[0], b->stream));
+  for (size_t q = 0; q < b->m.size(); ++q) PIC_CUDA(cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0));
+  return PIC_OK;
+}
+
 int batch_capture(pic_batch_ctx *b) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -646,6 +664,7 @@ int batch_capture(pic_batch_ctx *b) {
   cudaStream_t s = b->stream;
   std::vector<long long> l0;
   for (pic_ctx *h : b->m) l0.push_back(h->launches);
+  if (const int rj = join_members_into_batch(b)) return rj;
   PIC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = PIC_OK;
   cudaError_t e = cudaEventRecord(b->ev[0], s);
@@ -680,7 +699,7 @@ int batch_capture(pic_batch_ctx *b) {
     b->launches_per_period.push_back(b->m[q]->launches - l0[q]);
   }
   PIC_CUDA(cudaGraphLaunch(b->exec, s));
-  return PIC_OK;
+  return join_batch_into_members(b);
 }
 }  // namespace
 
@@ -755,7 +774,9 @@ int pic_batch_step(pic_batch b, int n_steps) {
       const int rc = batch_capture(b);
       if (rc) return rc;
     } else {
+      if (const int rj = join_members_into_batch(b)) return rj;
       PIC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+      if (const int rj = join_batch_into_members(b)) return rj;
       for (size_t q = 0; q < b->m.size(); ++q) {
         b->m[q]->step += b->period;
         b->m[q]->launches += b->launches_per_period[q];

@@ -595,22 +595,20 @@ __device__ __forceinline__ bool ionises(unsigned long long r64, unsigned long lo
   return T == ~0ull || r64 < T;
 }
 
-// One thread per slot pair (2q, 2q+1) of a material cell: the pair shares
-// Philox block (step, cell, q, 3), words 0-1 for slot 2q and 2-3 for 2q+1.
+// One thread per material cell (a thread per slot pair measured twice as
+// slow: four threads repeat the cell's index and threshold loads).
 template <class R>
 __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   const Dev<R> &D = X.d;
-  const int npair_max = (X.ppc_max + 1) >> 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long m = t / npair_max;
-  const uint32_t q = (uint32_t)(t - m * npair_max);
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool active = m < D.nmat;
   const long long step = *D.step;
-  uint32_t pair = 0, ion = 0;
+  uint32_t alive = 0, ion = 0;
   int i = 0, j = 0, k = 0, L = 0;
   uint32_t c = 0;
   R t1 = R(0);
-  if (m < D.nmat) pair = (D.alive[m] >> (2 * q)) & 3u;
-  if (pair) {
+  if (active) alive = D.alive[m];
+  if (alive) {
     const int nx = D.nx, nxy = D.nxy;
     const int mp = (int)(m / nxy);
     const int r = (int)(m - (long long)mp * nxy);
@@ -619,30 +617,46 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
     k = D.kplane[mp];
     L = D.layer_of_plane[k];
     c = (uint32_t)((long long)k * nxy + r);
-    t1 = R((double)(step + 1) * D.dt_d);
     const unsigned long long Town = D.T[m];
-    // neutrals that may have left the birth cell by t^{n+1}: their own leave
-    // step (64-step units, rounded down) has been reached
-    unsigned long long Tuse[2] = {Town, Town};
+    // neutrals that may have left the birth cell by t^{n+1}: their own
+    // leave step (64-step units, rounded down) has been reached
+    uint32_t exc = 0;
     if ((unsigned long long)(step + 1) >= (unsigned long long)D.leave_step[m]) {
       const uint16_t *ls = X.leave16 + m * X.ppc_max;
-      const R sig = X.lr[L].sig_v;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t s = 2 * q + h;
-        if (!((pair >> h) & 1u) || (unsigned long long)(step + 1) < 64ull * ls[s]) continue;
-        Neutral<R> nu;
-        Tuse[h] = neutral_at(D, sig, i, j, k, c, s, t1, nu)
-                      ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-                      : 0ull;
+      for (uint32_t bits = alive; bits; bits &= bits - 1) {
+        const uint32_t s = __ffs(bits) - 1;
+        if ((unsigned long long)(step + 1) >= 64ull * ls[s]) exc |= 1u << s;
       }
     }
-    if (((pair & 1u) && Tuse[0]) || ((pair & 2u) && Tuse[1])) {
-      const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
-      const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
-      const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
-      if ((pair & 1u) && Tuse[0] && ionises(r0, Tuse[0])) ion |= 1u;
-      if ((pair & 2u) && Tuse[1] && ionises(r1, Tuse[1])) ion |= 2u;
+    // birth-cell threshold for every other alive neutral; slots 2q and 2q+1
+    // share Philox block (step, cell, q, 3): words 0-1 and 2-3
+    if (Town != 0ull) {
+      for (uint32_t bits = alive & ~exc; bits;) {
+        const uint32_t q = (uint32_t)(__ffs(bits) - 1) >> 1;
+        const uint32_t pb = bits & (3u << (2 * q));
+        bits &= ~(3u << (2 * q));
+        const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
+        const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
+        const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
+        if (((pb >> (2 * q)) & 1u) && ionises(r0, Town)) ion |= 1u << (2 * q);
+        if (((pb >> (2 * q + 1)) & 1u) && ionises(r1, Town)) ion |= 1u << (2 * q + 1);
+      }
+    }
+    // the few neutrals near a face: exact position, threshold of that cell
+    const R sig = X.lr[L].sig_v;
+    t1 = R((double)(step + 1) * D.dt_d);
+    for (uint32_t bits = exc; bits; bits &= bits - 1) {
+      const uint32_t s = __ffs(bits) - 1;
+      Neutral<R> nu;
+      const unsigned long long Tuse =
+          neutral_at(D, sig, i, j, k, c, s, t1, nu)
+              ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+              : 0ull;
+      if (Tuse == 0ull) continue;
+      const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 1, kStreamIon);
+      const unsigned long long r64 = (s & 1u) ? (((unsigned long long)w.w << 32) | w.z)
+                                              : (((unsigned long long)w.y << 32) | w.x);
+      if (ionises(r64, Tuse)) ion |= 1u << s;
     }
   }
   // warp-aggregated reservation of pool slots
@@ -663,9 +677,8 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   const LayerR<R> &Ly = X.lr[L];
   const int ppc = Ly.ppc;
   uint32_t done = 0;
-  for (int h = 0; h < 2; ++h) {
-    if (!((ion >> h) & 1u)) continue;
-    const uint32_t s = 2 * q + h;
+  for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
+    const uint32_t s = __ffs(bits) - 1;
     if (slot + 1 >= D.cap) {
       atomicOr(D.err, kErrPool);
       break;
@@ -676,20 +689,19 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
     const unsigned long long gid = (unsigned long long)c * ppc + s;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      const unsigned long long qq = slot + sp;
-      D.pid[qq] = 2ull * gid + sp;
-      D.pcell[qq] = ncell;
+      const unsigned long long q = slot + sp;
+      D.pid[q] = 2ull * gid + sp;
+      D.pcell[q] = ncell;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        D.po[d][qq] = nu.off[d];
-        D.pu[d][qq] = nu.u[d];
+        D.po[d][q] = nu.off[d];
+        D.pu[d][q] = nu.u[d];
       }
-      D.ptag[qq] = ((uint32_t)L << 1) | (uint32_t)sp;
+      D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
     }
     done |= 1u << s;
-    slot += 2;
   }
-  if (done) atomicAnd(D.alive + m, ~done);
+  D.alive[m] = alive & ~done;
   const double nd = (double)__popc(done);
   const LayerK &LK = D.layers[L];
   atomicAdd(D.acc + 1, nd * LK.wmac);

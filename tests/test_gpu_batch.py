@@ -40,4 +40,12 @@ def test_batch_of_uneven_instances_matches_oracle(oracle_mod):
     o = oracle_mod.Sim(cfgs[0])
     o.step(105)
     assert rel_l2(sims[0].fields()[0:3], o.fields()[0:3]) <= 1e-12
+    # and a member stepped alone right after a replay starts from the replay's end
+    batch.step(32)
+    sims[1].step(2)
+    sims[1].sync()
+    o = oracle_mod.Sim(cfgs[1])
+    o.step(136)
+    assert sims[1].scalars()["step"] == 136
+    assert rel_l2(sims[1].fields()[0:3], o.fields()[0:3]) <= 1e-12
     batch.close()
