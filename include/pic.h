@@ -12,7 +12,7 @@
  *   - the per-cell maximum of |E| over the last optical cycle (Sec. 2.1,
  *     rolling window) and the Keldysh photoionisation rate (Sec. 2.1, Eqs.
  *     for x, W and Q);
- *   - counter-based Philox4x32-10 draws keyed by (seed, step, cell, slot pair) that
+ *   - counter-based Philox4x32-10 draws keyed by (seed, step, cell, slot group) that
  *     ionise each molecule at most once (Sec. 2.1) into an electron and a
  *     hole with the Table 1 effective masses (Sec. 3.2).
  *
@@ -71,7 +71,7 @@ typedef struct pic_ctx *pic_handle;
 
 /* Grid and numerical parameters. */
 typedef struct {
-  int nx, ny, nz;      /* cells; nx, ny >= 4, nz >= 8 */
+  int nx, ny, nz;      /* cells; nx, ny >= 4, 8 <= nz < 65535 */
   int precision;       /* PIC_FP64 or PIC_FP32 (fields, push, deposit) */
   double dx, dy, dz;   /* cell sizes [m] */
   double cfl;          /* dt = cfl / (c sqrt(1/dx^2+1/dy^2+1/dz^2)), 0 < cfl <= 1

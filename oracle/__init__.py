@@ -122,11 +122,16 @@ def lib():
             L.or_incident.restype = d
             L.or_incident.argtypes = [vp, d]
             L.or_philox.argtypes = [vp, vp, vp]
+            L.or_ion_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_uint32]
+            L.or_ion_uniform.restype = ctypes.c_uint64
             L.or_dawson.restype = d
             L.or_dawson.argtypes = [d]
             L.or_ellip_KE.argtypes = [d, d, _P(d), _P(d)]
             L.or_keldysh_W.restype = d
             L.or_keldysh_W.argtypes = [d, d, d, d, i, _P(i)]
+            L.or_keldysh_parts.argtypes = [d, d, d, d, i, _P(i), vp]
+            L.or_keldysh_parts.restype = d
             L.or_boris.argtypes = [d, d, vp, vp, vp]
             _lib = L
         return _lib
@@ -148,6 +153,11 @@ def philox(ctr, key) -> np.ndarray:
     return out
 
 
+def ion_uniform(seed: int, step: int, cell: int, slot: int) -> int:
+    """The 64-bit uniform a neutral compares with its ionisation threshold."""
+    return int(lib().or_ion_uniform(int(seed), int(step), int(cell), int(slot)))
+
+
 def dawson(z: float) -> float:
     return lib().or_dawson(float(z))
 
@@ -167,6 +177,15 @@ def keldysh_W(E: float, omega: float, gap_J: float, mstar_kg: float,
     w = lib().or_keldysh_W(float(E), float(omega), float(gap_J),
                            float(mstar_kg), int(nterms), ctypes.byref(used))
     return (w, used.value) if return_terms else w
+
+
+def keldysh_parts(E: float, omega: float, gap_J: float, mstar_kg: float, nterms: int = 500):
+    """The rate W and its pieces: dict(W, gamma, x, N = floor(x + 1), Q)."""
+    parts = np.zeros(4)
+    used = ctypes.c_int()
+    w = lib().or_keldysh_parts(float(E), float(omega), float(gap_J), float(mstar_kg),
+                               int(nterms), ctypes.byref(used), _ptr(parts))
+    return dict(W=w, gamma=parts[0], x=parts[1], N=parts[2], Q=parts[3])
 
 
 def boris(qm: float, dt: float, E, B, u) -> np.ndarray:

@@ -19,8 +19,10 @@
  *   ionisation     : one event per molecule (Sec. 2.1), electron + hole with
  *                    the Table 1 effective masses (Sec. 3.2)
  * Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) supplies
- * every random number, keyed by (seed) with counter (step, cell, slot, stream);
- * the ionisation stream gives two slots one block (slot >> 1).
+ * every random number, keyed by (seed) with counter (step, cell, slot, stream).
+ * A neutral's 64-bit ionisation uniform takes its top 16 bits from the block
+ * (step, cell, slot >> 3, 3) shared by eight slots and its low 48 bits from
+ * the block (step, cell, slot, 4) (or_ion_uniform).
  *
  * Parity pins for every function here live in tests/test_oracle_*.py.
  */
@@ -42,6 +44,7 @@
 #define OR_STREAM_POS 1u
 #define OR_STREAM_VEL 2u
 #define OR_STREAM_ION 3u
+#define OR_STREAM_ION_LOW 4u
 
 /* ------------------------------------------------------------------------ */
 /* Configuration (mirrors the library's inputs, declared independently)     */
@@ -115,6 +118,21 @@ static void philox_draw(uint64_t seed, uint32_t step, uint32_t cell,
 }
 
 static double u01(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+/* The uniform 64-bit number a neutral draws at a step: bits 63..48 are the
+ * 16-bit half (slot & 1: high half) of word (slot & 7) >> 1 of the block
+ * (step, cell, slot >> 3, ION); bits 47..0 are the low 16 bits of word 1
+ * above word 0 of the block (step, cell, slot, ION_LOW).  It ionises when it
+ * is below the threshold T = floor(p 2^64). */
+uint64_t or_ion_uniform(uint64_t seed, uint32_t step, uint32_t cell, uint32_t slot) {
+  uint32_t a[4], b[4];
+  philox_draw(seed, step, cell, slot >> 3, OR_STREAM_ION, a);
+  philox_draw(seed, step, cell, slot, OR_STREAM_ION_LOW, b);
+  uint32_t w = a[(slot & 7u) >> 1];
+  uint64_t hi16 = (slot & 1u) ? (w >> 16) : (w & 0xFFFFu);
+  uint64_t lo48 = ((uint64_t)(b[1] & 0xFFFFu) << 32) | (uint64_t)b[0];
+  return (hi16 << 48) | lo48;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Complete elliptic integrals, parameter convention (reading K1):           */
@@ -192,12 +210,16 @@ double or_dawson(double z) {
 /* where adding it, or any later term, leaves the double sum unchanged: the    */
 /* result is bit-identical to summing all nterms terms.                       */
 /* ------------------------------------------------------------------------ */
-double or_keldysh_W(double E, double omega, double gap_J, double mstar_kg,
-                    int nterms, int *terms_used) {
+/* Keldysh rate W (returned) and, when parts is not NULL, its pieces:
+ * parts[0] = gamma, [1] = x, [2] = floor(x + 1), [3] = Q(gamma, x). */
+double or_keldysh_parts(double E, double omega, double gap_J, double mstar_kg,
+                        int nterms, int *terms_used, double parts[4]) {
   if (terms_used) *terms_used = 0;
+  if (parts) parts[0] = parts[1] = parts[2] = parts[3] = 0.0;
   if (!(E > 0.0)) return 0.0;
   double g = omega * sqrt(mstar_kg * gap_J) / (OR_QE * E);
   double g2 = g * g;
+  if (parts) parts[0] = g;
   if (!(g2 < 1e300)) return 0.0;
   double gam1 = g2 / (1.0 + g2), gam2 = 1.0 / (1.0 + g2);
   double K1, KmE1, K2, KmE2;
@@ -221,9 +243,19 @@ double or_keldysh_W(double E, double omega, double gap_J, double mstar_kg,
   }
   if (terms_used) *terms_used = n;
   double Q = sqrt(OR_PI / (2.0 * K2)) * sum;
+  if (parts) {
+    parts[1] = x;
+    parts[2] = N;
+    parts[3] = Q;
+  }
   double pref = 2.0 * (2.0 * omega / (9.0 * OR_PI)) *
                 pow(mstar_kg * omega / (OR_HBAR * sqrt(gam1)), 1.5);
   return pref * Q * exp(-N * a);
+}
+
+double or_keldysh_W(double E, double omega, double gap_J, double mstar_kg,
+                    int nterms, int *terms_used) {
+  return or_keldysh_parts(E, omega, gap_J, mstar_kg, nterms, terms_used, NULL);
 }
 
 /* Probability that one molecule ionises in one step (reading K5):
@@ -776,13 +808,7 @@ void or_ionize_pass(or_sim *s) {
             T = s->T[m2];
             always = s->Talways[m2];
           }
-          /* slots 2q and 2q+1 share the Philox block (step, cell, q, ION):
-           * words 0,1 form slot 2q's 64-bit uniform, words 2,3 slot 2q+1's */
-          uint32_t r[4];
-          philox_draw(s->cfg.seed, (uint32_t)s->step, cell, (uint32_t)(sl >> 1),
-                      OR_STREAM_ION, r);
-          int hw = (sl & 1) ? 2 : 0;
-          uint64_t r64 = ((uint64_t)r[hw + 1] << 32) | r[hw];
+          uint64_t r64 = or_ion_uniform(s->cfg.seed, (uint32_t)s->step, cell, (uint32_t)sl);
           if (!(always || r64 < T)) continue;
           s->alive[m] &= ~(1u << sl);
           double v2 = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];

@@ -64,6 +64,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   if (!grid || !mat || !pulse) return fail(PIC_EINVAL, "null configuration pointer");
   const pic_grid &g = *grid;
   if (g.nx < 4 || g.ny < 4 || g.nz < 8) return fail(PIC_EINVAL, "grid needs nx, ny >= 4, nz >= 8");
+  if (g.nz >= 65535) return fail(PIC_EINVAL, "grid needs nz < 65535 (one launch row per z plane)");
   if (!(g.dx > 0 && g.dy > 0 && g.dz > 0)) return fail(PIC_EINVAL, "cell sizes must be > 0");
   if (!(g.cfl > 0 && g.cfl <= 1.0)) return fail(PIC_EINVAL, "cfl must be in (0, 1]");
   if (g.precision != PIC_FP64 && g.precision != PIC_FP32)
@@ -280,6 +281,7 @@ struct pic_ctx {
   bool fp64 = true;
   int sticky = PIC_OK;
   long long launches = 0;
+  int field_v = 1;  // x points per thread of the field and window kernels
   // profiling: (class, start, stop) event triples, reused across reads
   bool profiling = false;
   struct Rec {
@@ -445,16 +447,32 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
-    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
-    k_efull<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X);
-    k_bhalf<R><<<grid_blocks(P.nfield), kThreads, 0, s>>>(X.d);
+    if constexpr (sizeof(R) == 4) {
+      if (h->field_v == 4) {
+        const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
+        k_bhalf<4, R><<<grid, kThreads, 0, s>>>(X.d);
+        k_efull<4, R><<<grid, kThreads, 0, s>>>(X);
+        k_bhalf<4, R><<<grid, kThreads, 0, s>>>(X.d);
+      }
+    }
+    if (h->field_v == 1) {
+      const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
+      k_bhalf<1, R><<<grid, kThreads, 0, s>>>(X.d);
+      k_efull<1, R><<<grid, kThreads, 0, s>>>(X);
+      k_bhalf<1, R><<<grid, kThreads, 0, s>>>(X.d);
+    }
     prof_end(h);
     h->launches += 3;
   }
   if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
     prof_begin(h, PIC_PROF_WINDOW);
     PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
-    k_window<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    if constexpr (sizeof(R) == 4) {
+      if (h->field_v == 4)
+        k_window<4, R><<<dim3(grid_blocks(P.nxy / 4), P.n_mplanes), kThreads, 0, s>>>(X);
+    }
+    if (h->field_v == 1)
+      k_window<1, R><<<dim3(grid_blocks(P.nxy), P.n_mplanes), kThreads, 0, s>>>(X);
     prof_end(h);
     prof_begin(h, PIC_PROF_KELDYSH);
     k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
@@ -463,7 +481,7 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
     prof_begin(h, PIC_PROF_IONIZE);
-    k_ionize<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(X);
+    k_ionize<R><<<dim3(grid_blocks(P.nxy), P.n_mplanes), kThreads, 0, s>>>(X);
     prof_end(h);
     h->launches += 1;
   }
@@ -591,6 +609,7 @@ int pic_create(const pic_grid *grid, const pic_material *mat, const pic_pulse *p
   h->seed = seed;
   h->stream = (cudaStream_t)stream;
   h->fp64 = h->P.g.precision == PIC_FP64;
+  h->field_v = (!h->fp64 && h->P.g.nx % 4 == 0) ? 4 : 1;
   h->lk = layer_constants(h->P);
   if (d_arena) {
     if (arena_bytes < h->P.total || ((uintptr_t)d_arena % kAlign)) {

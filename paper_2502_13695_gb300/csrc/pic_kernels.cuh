@@ -288,24 +288,69 @@ __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
 // ---------------------------------------------------------------------------
 // Fields
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= D.nfield) return;
-  const int nx = D.nx, nxy = D.nxy;
-  const int k = (int)(o / nxy);
-  const int r = (int)(o - (long long)k * nxy);
-  const int j = r / nx, i = r - j * nx;
-  const long long oi = (i == nx - 1) ? o - (nx - 1) : o + 1;
-  const long long oj = (j == D.ny - 1) ? o - (long long)(D.ny - 1) * nx : o + nx;
-  const R h = R(0.5) * D.dt;
-  const R *Ex = D.E[0], *Ey = D.E[1], *Ez = D.E[2];
-  if (k < D.nz) {
-    const R ez = Ez[o], ey = Ey[o], ex = Ex[o];
-    D.B[0][o] -= h * ((Ez[oj] - ez) * D.idy - (Ey[o + nxy] - ey) * D.idz);
-    D.B[1][o] -= h * ((Ex[o + nxy] - ex) * D.idz - (Ez[oi] - ez) * D.idx);
+// Points per thread of the field and window kernels: V consecutive x points
+// of one row.  V = 4 (FP32, nx a multiple of 4) moves them with 16-byte
+// vector loads and stores; the launch is (row chunks, z planes).
+template <int V, class R>
+__device__ __forceinline__ void ldv(R *d, const R *p) {
+  if constexpr (V == 4 && sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l) d[l] = p[l];
   }
-  D.B[2][o] -= h * ((Ey[oi] - Ey[o]) * D.idx - (Ex[oj] - Ex[o]) * D.idy);
+}
+template <int V, class R>
+__device__ __forceinline__ void stv(R *p, const R *d) {
+  if constexpr (V == 4 && sizeof(R) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(d[0], d[1], d[2], d[3]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l) p[l] = d[l];
+  }
+}
+
+// B half step (Faraday) on V points of plane blockIdx.y.
+template <int V, class R>
+__global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
+  const int nx = D.nx, ny = D.ny, nxy = D.nxy;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (r >= nxy) return;
+  const int k = blockIdx.y;
+  const int j = r / nx, i = r - j * nx;
+  const long long o = (long long)k * nxy + r;
+  const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
+  const long long ov = (i + V == nx) ? o + V - nx : o + V;  // x + 1 of the last point
+  const R h = R(0.5) * D.dt;
+  R ex[V], ey[V + 1], exj[V], b[V];
+  ldv<V>(ex, D.E[0] + o);
+  ldv<V>(ey, D.E[1] + o);
+  ey[V] = D.E[1][ov];
+  ldv<V>(exj, D.E[0] + oj);
+  ldv<V>(b, D.B[2] + o);
+#pragma unroll
+  for (int l = 0; l < V; ++l) b[l] -= h * ((ey[l + 1] - ey[l]) * D.idx - (exj[l] - ex[l]) * D.idy);
+  stv<V>(D.B[2] + o, b);
+  if (k < D.nz) {
+    R ez[V + 1], ezj[V], eyk[V], exk[V];
+    ldv<V>(ez, D.E[2] + o);
+    ez[V] = D.E[2][ov];
+    ldv<V>(ezj, D.E[2] + oj);
+    ldv<V>(eyk, D.E[1] + o + nxy);
+    ldv<V>(exk, D.E[0] + o + nxy);
+    ldv<V>(b, D.B[0] + o);
+#pragma unroll
+    for (int l = 0; l < V; ++l) b[l] -= h * ((ezj[l] - ez[l]) * D.idy - (eyk[l] - ey[l]) * D.idz);
+    stv<V>(D.B[0] + o, b);
+    ldv<V>(b, D.B[1] + o);
+#pragma unroll
+    for (int l = 0; l < V; ++l) b[l] -= h * ((exk[l] - ex[l]) * D.idz - (ez[l + 1] - ez[l]) * D.idx);
+    stv<V>(D.B[1] + o, b);
+  }
 }
 
 template <class R>
@@ -357,28 +402,41 @@ __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) 
   return e0 + a - dp;
 }
 
-template <class R>
-__global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
+// E step on V points of plane blockIdx.y: Ampere with J and the polarisation
+// current, Silver-Mueller faces at k = 0 (with the incident field) and k = nz,
+// Joule work J.(E^n + E^{n+1})/2, J cleared for the next deposit.  Three
+// blocks per SM (80 registers) measured faster than two at 100 registers.
+template <int V, class R>
+__global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
   const Dev<R> &D = X.d;
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const int k = blockIdx.y;
   R joule = R(0);
-  if (o < D.nfield) {
-    const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
-    const int k = (int)(o / nxy);
-    const int r = (int)(o - (long long)k * nxy);
+  if (r < nxy) {
     const int j = r / nx, i = r - j * nx;
-    const long long omi = (i == 0) ? o + (nx - 1) : o - 1;
+    const long long o = (long long)k * nxy + r;
+    const long long omv = (i == 0) ? o + (nx - 1) : o - 1;  // x - 1 of the first point
     const long long omj = (j == 0) ? o + (long long)(ny - 1) * nx : o - nx;
-    const R *Bx = D.B[0], *By = D.B[1], *Bz = D.B[2];
     const R c2dt = D.c2dt, dtie = R(D.dt_d / kEps0);
-    const R bz = Bz[o];
-    const R dBz_dy = (bz - Bz[omj]) * D.idy;
-    const R dBz_dx = (bz - Bz[omi]) * D.idx;
-    R *const j4 = D.J4 + 4 * o;
-    R jx, jy, jz;
-    load_j3(j4, jx, jy, jz);
-    const R ex0 = D.E[0][o], ey0 = D.E[1][o];
-    R ex1, ey1;
+    // bz[0] is the x - 1 neighbour of the first point, bz[1..V] the points
+    R bz[V + 1], bzj[V], bx[V], by[V];
+    bz[0] = D.B[2][omv];
+    ldv<V>(bz + 1, D.B[2] + o);
+    ldv<V>(bzj, D.B[2] + omj);
+    ldv<V>(bx, D.B[0] + o);
+    ldv<V>(by, D.B[1] + o);
+    R jx[V], jy[V], jz[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) load_j3(D.J4 + 4 * (o + l), jx[l], jy[l], jz[l]);
+    R ex0[V], ey0[V], ex1[V], ey1[V], dBz_dy[V], dBz_dx[V];
+    ldv<V>(ex0, D.E[0] + o);
+    ldv<V>(ey0, D.E[1] + o);
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      dBz_dy[l] = (bz[l + 1] - bzj[l]) * D.idy;
+      dBz_dx[l] = (bz[l + 1] - bz[l]) * D.idx;
+    }
     const int L = k < nz ? D.layer_of_plane[k] : -1;
     const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
     if (k == 0 || k == nz) {
@@ -390,51 +448,89 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
         const double env = exp(-2.0 * 0.69314718055994531 * t * t / (D.fwhm * D.fwhm));
         const double einc = D.E0 * env * cos(D.omega * t + D.cep);
         const R exi = D.pol == 0 ? R(einc) : R(0), eyi = D.pol == 0 ? R(0) : R(einc);
-        ex1 = ((R(1) - al) * ex0 - R(2) * al * cc * By[o] + R(4) * al * exi +
-               (c2dt * dBz_dy - dtie * jx)) * inv;
-        ey1 = ((R(1) - al) * ey0 + R(2) * al * cc * Bx[o] + R(4) * al * eyi -
-               (c2dt * dBz_dx + dtie * jy)) * inv;
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          ex1[l] = ((R(1) - al) * ex0[l] - R(2) * al * cc * by[l] + R(4) * al * exi +
+                    (c2dt * dBz_dy[l] - dtie * jx[l])) * inv;
+          ey1[l] = ((R(1) - al) * ey0[l] + R(2) * al * cc * bx[l] + R(4) * al * eyi -
+                    (c2dt * dBz_dx[l] + dtie * jy[l])) * inv;
+        }
       } else {
-        const long long om = o - nxy;
-        ex1 = ((R(1) - al) * ex0 + R(2) * al * cc * By[om] + (c2dt * dBz_dy - dtie * jx)) * inv;
-        ey1 = ((R(1) - al) * ey0 - R(2) * al * cc * Bx[om] - (c2dt * dBz_dx + dtie * jy)) * inv;
+        R bxm[V], bym[V];
+        ldv<V>(bxm, D.B[0] + o - nxy);
+        ldv<V>(bym, D.B[1] + o - nxy);
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          ex1[l] = ((R(1) - al) * ex0[l] + R(2) * al * cc * bym[l] +
+                    (c2dt * dBz_dy[l] - dtie * jx[l])) * inv;
+          ey1[l] = ((R(1) - al) * ey0[l] - R(2) * al * cc * bxm[l] -
+                    (c2dt * dBz_dx[l] + dtie * jy[l])) * inv;
+        }
       }
     } else {
-      const long long om = o - nxy;
-      const R ax = c2dt * (dBz_dy - (By[o] - By[om]) * D.idz) - dtie * jx;
-      const R ay = c2dt * ((Bx[o] - Bx[om]) * D.idz - dBz_dx) - dtie * jy;
+      R bxm[V], bym[V], ax[V], ay[V];
+      ldv<V>(bxm, D.B[0] + o - nxy);
+      ldv<V>(bym, D.B[1] + o - nxy);
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        ax[l] = c2dt * (dBz_dy[l] - (by[l] - bym[l]) * D.idz) - dtie * jx[l];
+        ay[l] = c2dt * ((bx[l] - bxm[l]) * D.idz - dBz_dx[l]) - dtie * jy[l];
+      }
       if (m >= 0) {
         const LayerR<R> &Ly = X.lr[L];
-        R px = D.P[0][m], qx = D.Q[0][m], py = D.P[1][m], qy = D.Q[1][m];
-        ex1 = e_point(Ly, ex0, ax, px, qx);
-        ey1 = e_point(Ly, ey0, ay, py, qy);
-        D.P[0][m] = px;
-        D.Q[0][m] = qx;
-        D.P[1][m] = py;
-        D.Q[1][m] = qy;
+        R px[V], qx[V], py[V], qy[V];
+        ldv<V>(px, D.P[0] + m);
+        ldv<V>(qx, D.Q[0] + m);
+        ldv<V>(py, D.P[1] + m);
+        ldv<V>(qy, D.Q[1] + m);
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          ex1[l] = e_point(Ly, ex0[l], ax[l], px[l], qx[l]);
+          ey1[l] = e_point(Ly, ey0[l], ay[l], py[l], qy[l]);
+        }
+        stv<V>(D.P[0] + m, px);
+        stv<V>(D.Q[0] + m, qx);
+        stv<V>(D.P[1] + m, py);
+        stv<V>(D.Q[1] + m, qy);
       } else {
-        ex1 = ex0 + ax;
-        ey1 = ey0 + ay;
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          ex1[l] = ex0[l] + ax[l];
+          ey1[l] = ey0[l] + ay[l];
+        }
       }
     }
-    joule += jx * R(0.5) * (ex0 + ex1) + jy * R(0.5) * (ey0 + ey1);
-    D.E[0][o] = ex1;
-    D.E[1][o] = ey1;
-    clear_j3(j4);
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      joule += jx[l] * R(0.5) * (ex0[l] + ex1[l]) + jy[l] * R(0.5) * (ey0[l] + ey1[l]);
+      clear_j3(D.J4 + 4 * (o + l));
+    }
+    stv<V>(D.E[0] + o, ex1);
+    stv<V>(D.E[1] + o, ey1);
     if (k < nz) {
-      const R az = c2dt * ((By[o] - By[omi]) * D.idx - (Bx[o] - Bx[omj]) * D.idy) - dtie * jz;
-      const R ez0 = D.E[2][o];
-      R ez1;
+      R bxj[V], ez0[V], ez1[V], az[V];
+      const R byp = D.B[1][omv];
+      ldv<V>(bxj, D.B[0] + omj);
+      ldv<V>(ez0, D.E[2] + o);
+#pragma unroll
+      for (int l = 0; l < V; ++l)
+        az[l] = c2dt * ((by[l] - (l ? by[l - 1] : byp)) * D.idx - (bx[l] - bxj[l]) * D.idy) -
+                dtie * jz[l];
       if (m >= 0) {
-        R pz = D.P[2][m], qz = D.Q[2][m];
-        ez1 = e_point(X.lr[L], ez0, az, pz, qz);
-        D.P[2][m] = pz;
-        D.Q[2][m] = qz;
+        R pz[V], qz[V];
+        ldv<V>(pz, D.P[2] + m);
+        ldv<V>(qz, D.Q[2] + m);
+#pragma unroll
+        for (int l = 0; l < V; ++l) ez1[l] = e_point(X.lr[L], ez0[l], az[l], pz[l], qz[l]);
+        stv<V>(D.P[2] + m, pz);
+        stv<V>(D.Q[2] + m, qz);
       } else {
-        ez1 = ez0 + az;
+#pragma unroll
+        for (int l = 0; l < V; ++l) ez1[l] = ez0[l] + az[l];
       }
-      joule += jz * R(0.5) * (ez0 + ez1);
-      D.E[2][o] = ez1;
+#pragma unroll
+      for (int l = 0; l < V; ++l) joule += jz[l] * R(0.5) * (ez0[l] + ez1[l]);
+      stv<V>(D.E[2] + o, ez1);
     }
   }
   // Joule work: block sum in the working precision, one FP64 atomic per block
@@ -445,58 +541,108 @@ __global__ void __launch_bounds__(256) k_efull(Ctx<R> X) {
 // ---------------------------------------------------------------------------
 // Amplitude window + Keldysh threshold, one thread per material cell
 // ---------------------------------------------------------------------------
-template <class R>
+template <int V, class R>
 __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
   const Dev<R> &D = X.d;
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (m >= D.nmat) return;
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
-  const int mp = (int)(m / nxy);
-  const int r = (int)(m - (long long)mp * nxy);
-  const int j = r / nx, i = r - j * nx;
-  const int k = D.kplane[mp];
-  const long long o = (long long)k * nxy + r;
-  const long long oi = (i == nx - 1) ? o - (nx - 1) : o + 1;
-  const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
-  const long long oij = (j == ny - 1) ? oi - (long long)(ny - 1) * nx : oi + nx;
-  const R *Ex = D.E[0], *Ey = D.E[1], *Ez = D.E[2];
-  const R ax = R(0.25) * (((Ex[o] + Ex[oj]) + Ex[o + nxy]) + Ex[oj + nxy]);
-  const R ay = R(0.25) * (((Ey[o] + Ey[oi]) + Ey[o + nxy]) + Ey[oi + nxy]);
-  const R az = R(0.25) * (((Ez[o] + Ez[oi]) + Ez[oj]) + Ez[oij]);
-  const R a = sqrt(ax * ax + ay * ay + az * az);
-  // sliding maximum: slots <= s hold this block's samples, slots > s the
-  // suffix maxima of the previous block; pm is the running block prefix max
-  const int NW = D.NW;
-  const int s = (int)(*D.step % NW);
-  R *__restrict__ W = D.win + m;
-  const long long st = D.nmat;
-  W[s * st] = a;
-  const R pm = s == 0 ? a : fmax(D.pm[m], a);
-  D.pm[m] = pm;
-  const R amp = s + 1 < NW ? fmax(pm, W[(s + 1) * st]) : pm;
-  if (s == NW - 1) {
-    R run = W[(NW - 1) * st];
-    for (int q = NW - 2; q >= 0; --q) {
-      run = fmax(run, W[q * st]);
-      W[q * st] = run;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const int mp = blockIdx.y;
+  const long long m = (long long)mp * nxy + r;
+  uint32_t miss = 0;  // cells whose threshold k_keldysh must recompute
+  if (r < nxy) {
+    const int j = r / nx, i = r - j * nx;
+    const int k = D.kplane[mp];
+    const long long o = (long long)k * nxy + r;
+    const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
+    const long long ov = (i + V == nx) ? o + V - nx : o + V;     // x + 1 of the last point
+    const long long ojv = (i + V == nx) ? oj + V - nx : oj + V;  // and one row up
+    // cell-centred amplitude: mean of the four edge values of each component
+    R ex[V], exj[V], exk[V], exjk[V], ey[V + 1], eyk[V + 1], ez[V + 1], ezj[V + 1];
+    ldv<V>(ex, D.E[0] + o);
+    ldv<V>(exj, D.E[0] + oj);
+    ldv<V>(exk, D.E[0] + o + nxy);
+    ldv<V>(exjk, D.E[0] + oj + nxy);
+    ldv<V>(ey, D.E[1] + o);
+    ey[V] = D.E[1][ov];
+    ldv<V>(eyk, D.E[1] + o + nxy);
+    eyk[V] = D.E[1][ov + nxy];
+    ldv<V>(ez, D.E[2] + o);
+    ez[V] = D.E[2][ov];
+    ldv<V>(ezj, D.E[2] + oj);
+    ezj[V] = D.E[2][ojv];
+    R a[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      const R ax = R(0.25) * (((ex[l] + exj[l]) + exk[l]) + exjk[l]);
+      const R ay = R(0.25) * (((ey[l] + ey[l + 1]) + eyk[l]) + eyk[l + 1]);
+      const R az = R(0.25) * (((ez[l] + ez[l + 1]) + ezj[l]) + ezj[l + 1]);
+      a[l] = sqrt(ax * ax + ay * ay + az * az);
+    }
+    // sliding maximum: slots <= s hold this block's samples, slots > s the
+    // suffix maxima of the previous block; pm is the running block prefix max
+    const int NW = D.NW;
+    const int s = (int)(*D.step % NW);
+    R *__restrict__ W = D.win + m;
+    const long long st = D.nmat;
+    stv<V>(W + s * st, a);
+    R pm[V], amp[V];
+    if (s == 0) {
+#pragma unroll
+      for (int l = 0; l < V; ++l) pm[l] = a[l];
+    } else {
+      ldv<V>(pm, D.pm + m);
+#pragma unroll
+      for (int l = 0; l < V; ++l) pm[l] = fmax(pm[l], a[l]);
+    }
+    stv<V>(D.pm + m, pm);
+    if (s + 1 < NW) {
+      ldv<V>(amp, W + (s + 1) * st);
+#pragma unroll
+      for (int l = 0; l < V; ++l) amp[l] = fmax(pm[l], amp[l]);
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l) amp[l] = pm[l];
+    }
+    if (s == NW - 1) {
+      R run[V], w[V];
+#pragma unroll
+      for (int l = 0; l < V; ++l) run[l] = a[l];
+      for (int q = NW - 2; q >= 0; --q) {
+        ldv<V>(w, W + q * st);
+#pragma unroll
+        for (int l = 0; l < V; ++l) run[l] = fmax(run[l], w[l]);
+        stv<V>(W + q * st, run);
+      }
+    }
+    stv<V>(D.eamp + m, amp);
+    R key[V];
+    ldv<V>(key, D.ckey + m);
+    const R e_skip = X.lr[D.layer_of_plane[k]].e_skip;
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      if (key[l] == amp[l]) continue;  // threshold cached for this exact amplitude
+      if (!(amp[l] >= e_skip)) {
+        D.T[m + l] = 0ull;
+        D.ckey[m + l] = amp[l];
+      } else {
+        miss |= 1u << l;
+      }
     }
   }
-  D.eamp[m] = amp;
-  if (D.ckey[m] == amp) return;  // threshold cached for this exact amplitude
-  const LayerR<R> &L = X.lr[D.layer_of_plane[k]];
-  if (!(amp >= L.e_skip)) {
-    D.T[m] = 0ull;
-    D.ckey[m] = amp;
-    return;
-  }
-  // cache miss: queue the cell for k_keldysh (warp-aggregated append)
-  const unsigned act = __activemask();
+  // warp-aggregated append of the misses to k_keldysh's work list
+  const int cnt = __popc(miss);
+  int incl = cnt;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(act) - 1;
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, sft);
+    if (lane >= sft) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
   int base = 0;
-  if (lane == leader) base = atomicAdd(X.work_n, __popc(act));
-  base = __shfl_sync(act, base, leader);
-  X.work[base + __popc(act & ((1u << lane) - 1u))] = (int)m;
+  if (lane == 31 && total) base = atomicAdd(X.work_n, total);
+  base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+  for (; miss; miss &= miss - 1) X.work[base++] = (int)(m + __ffs(miss) - 1);
 }
 
 // Keldysh thresholds of the queued cells, one thread per cell.
@@ -516,9 +662,10 @@ __global__ void __launch_bounds__(256) k_keldysh(Ctx<R> X) {
 // ---------------------------------------------------------------------------
 // Ionisation: one thread per material (birth) cell.  A neutral is force-free,
 // at x0 + v0 t with x0, v0 regenerated from Philox; it is drawn against the
-// threshold of the cell it occupies at t^{n+1}.  Until leave_step no neutral
-// of the cell can have crossed a face (|v0| < 7 sigma bounds Box-Muller), so
-// the birth cell's threshold decides without regenerating any state.
+// threshold of the cell it occupies at t^{n+1}.  k_init_material computes
+// from each neutral's own x0, v0 the step before which it cannot have crossed
+// a face (with a margin for the rounding of the run-time position), so until
+// then the birth cell's threshold decides without regenerating any state.
 // ---------------------------------------------------------------------------
 template <class R>
 struct Neutral {
@@ -591,8 +738,41 @@ __device__ __forceinline__ unsigned long long threshold_at(const Dev<R> &D, int 
   return D.T[(long long)mp * D.nxy + (long long)j * D.nx + i];
 }
 
-__device__ __forceinline__ bool ionises(unsigned long long r64, unsigned long long T) {
-  return T == ~0ull || r64 < T;
+// A neutral in slot s ionises when its 64-bit uniform (h16 << 48 | lo48) is
+// below T = floor(p 2^64) (T = ~0: always).  h16 is the 16-bit half
+// (s & 1: high) of word (s & 7) >> 1 of the block (step, cell, s >> 3, 3),
+// shared by eight slots; lo48 comes from the block (step, cell, s, 4), drawn
+// only when h16 equals the top 16 bits of T (otherwise those decide), which
+// happens once in 2^16 draws.
+__device__ __forceinline__ uint32_t ion_h16(const uint4 &w, uint32_t s) {
+  const uint32_t q = (s & 7u) >> 1;
+  const uint32_t v = q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+  return (s & 1u) ? (v >> 16) : (v & 0xFFFFu);
+}
+__device__ __forceinline__ bool ionises(uint32_t h16, unsigned long long T, unsigned long long seed,
+                                        uint32_t step, uint32_t cell, uint32_t s) {
+  if (T == ~0ull) return true;
+  const uint32_t th = (uint32_t)(T >> 48);
+  if (h16 != th) return h16 < th;
+  const uint4 b = draw(seed, step, cell, s, kStreamIonLow);
+  const unsigned long long lo48 = ((unsigned long long)(b.y & 0xFFFFu) << 32) | b.x;
+  return lo48 < (T & 0xFFFFFFFFFFFFull);
+}
+
+// The eight 16-bit halves of one block against the top 16 bits th of a
+// threshold: bit t of *lt is set when slot 8g + t is decided (below), of *eq
+// when its low 48 bits must decide.
+__device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32_t &lt,
+                                             uint32_t &eq) {
+  const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+  lt = 0;
+  eq = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const uint32_t h = (t & 1) ? (v[t >> 1] >> 16) : (v[t >> 1] & 0xFFFFu);
+    lt |= (uint32_t)(h < th) << t;
+    eq |= (uint32_t)(h == th) << t;
+  }
 }
 
 // One thread per material cell (a thread per slot pair measured twice as
@@ -600,8 +780,10 @@ __device__ __forceinline__ bool ionises(unsigned long long r64, unsigned long lo
 template <class R>
 __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   const Dev<R> &D = X.d;
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool active = m < D.nmat;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;  // cell in material plane blockIdx.y
+  const int mp = blockIdx.y;
+  const long long m = (long long)mp * D.nxy + r;
+  const bool active = r < D.nxy;
   const long long step = *D.step;
   uint32_t alive = 0, ion = 0;
   int i = 0, j = 0, k = 0, L = 0;
@@ -610,8 +792,6 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   if (active) alive = D.alive[m];
   if (alive) {
     const int nx = D.nx, nxy = D.nxy;
-    const int mp = (int)(m / nxy);
-    const int r = (int)(m - (long long)mp * nxy);
     j = r / nx;
     i = r - j * nx;
     k = D.kplane[mp];
@@ -628,23 +808,37 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
         if ((unsigned long long)(step + 1) >= 64ull * ls[s]) exc |= 1u << s;
       }
     }
-    // birth-cell threshold for every other alive neutral; slots 2q and 2q+1
-    // share Philox block (step, cell, q, 3): words 0-1 and 2-3
-    if (Town != 0ull) {
+    // birth-cell threshold for every other alive neutral: one block per
+    // group of eight slots decides on the top 16 bits; the rare ties draw
+    // their low 48 bits afterwards
+    if (Town == ~0ull) {
+      ion = alive & ~exc;
+    } else if (Town != 0ull) {
+      const uint32_t th = (uint32_t)(Town >> 48);
+      uint32_t tie = 0;
       for (uint32_t bits = alive & ~exc; bits;) {
-        const uint32_t q = (uint32_t)(__ffs(bits) - 1) >> 1;
-        const uint32_t pb = bits & (3u << (2 * q));
-        bits &= ~(3u << (2 * q));
-        const uint4 w = draw(D.seed, (uint32_t)step, c, q, kStreamIon);
-        const unsigned long long r0 = ((unsigned long long)w.y << 32) | w.x;
-        const unsigned long long r1 = ((unsigned long long)w.w << 32) | w.z;
-        if (((pb >> (2 * q)) & 1u) && ionises(r0, Town)) ion |= 1u << (2 * q);
-        if (((pb >> (2 * q + 1)) & 1u) && ionises(r1, Town)) ion |= 1u << (2 * q + 1);
+        const uint32_t g = (uint32_t)(__ffs(bits) - 1) >> 3;
+        const uint32_t gm = 0xFFu << (8 * g);
+        uint32_t lt, eq;
+        ion_compare8(draw(D.seed, (uint32_t)step, c, g, kStreamIon), th, lt, eq);
+        ion |= bits & gm & (lt << (8 * g));
+        tie |= bits & gm & (eq << (8 * g));
+        bits &= ~gm;
+      }
+      for (; tie; tie &= tie - 1) {
+        const uint32_t s = __ffs(tie) - 1;
+        const uint4 b = draw(D.seed, (uint32_t)step, c, s, kStreamIonLow);
+        const unsigned long long lo48 = ((unsigned long long)(b.y & 0xFFFFu) << 32) | b.x;
+        if (lo48 < (Town & 0xFFFFFFFFFFFFull)) ion |= 1u << s;
       }
     }
-    // the few neutrals near a face: exact position, threshold of that cell
+    // the few neutrals that may have crossed a face: exact position,
+    // threshold of that cell
     const R sig = X.lr[L].sig_v;
-    t1 = R((double)(step + 1) * D.dt_d);
+    if constexpr (sizeof(R) == 4)
+      t1 = R((int)(step + 1)) * D.dt;
+    else
+      t1 = R((double)(step + 1) * D.dt_d);
     for (uint32_t bits = exc; bits; bits &= bits - 1) {
       const uint32_t s = __ffs(bits) - 1;
       Neutral<R> nu;
@@ -653,10 +847,8 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
               ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
               : 0ull;
       if (Tuse == 0ull) continue;
-      const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 1, kStreamIon);
-      const unsigned long long r64 = (s & 1u) ? (((unsigned long long)w.w << 32) | w.z)
-                                              : (((unsigned long long)w.y << 32) | w.x);
-      if (ionises(r64, Tuse)) ion |= 1u << s;
+      const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 3, kStreamIon);
+      if (ionises(ion_h16(w, s), Tuse, D.seed, (uint32_t)step, c, s)) ion |= 1u << s;
     }
   }
   // warp-aggregated reservation of pool slots
@@ -725,15 +917,33 @@ __global__ void k_init_material(Ctx<R> X) {
   D.alive[m] = ppc >= 32 ? 0xFFFFFFFFu : ((1u << ppc) - 1u);
   double smin = 4e9;
   const double dl[3] = {D.dx_d, D.dy_d, D.dz_d};
-  const double vmax = 7.0 * L.sigv;
+  // offset error of the position the working precision computes at run time
+  // (birth offset, Box-Muller velocity and the product v t / dl rounded)
+  const double eps = 16.0 * (sizeof(R) == 4 ? 0x1p-24 : 0x1p-53);
   uint16_t *ls = X.leave16 + m * X.ppc_max;
   for (int s = 0; s < ppc; ++s) {
+    // the neutral's own birth offset and velocity (the same Philox draws the
+    // step uses), in double
     const uint4 w = draw(D.seed, 0u, c, (uint32_t)s, kStreamPos);
     const double o3[3] = {unit_open<double>(w.x), unit_open<double>(w.y), unit_open<double>(w.z)};
+    const uint4 wv = draw(D.seed, 0u, c, (uint32_t)s, kStreamVel);
+    const double r1 = sqrt(-2.0 * log(unit_open<double>(wv.x)));
+    const double r2 = sqrt(-2.0 * log(unit_open<double>(wv.z)));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * unit_open<double>(wv.y), &s1, &c1);
+    sincospi(2.0 * unit_open<double>(wv.w), &s2, &c2);
+    const double v[3] = {L.sigv * r1 * c1, L.sigv * r1 * s1, L.sigv * r2 * c2};
+    // time at which it may reach a face along any axis, less the time the
+    // rounding of its run-time offset can be early by
     double t = 1e300;
-    for (int d = 0; d < 3; ++d) t = fmin(t, fmin(o3[d], 1.0 - o3[d]) * dl[d]);
+    for (int d = 0; d < 3; ++d) {
+      const double av = fabs(v[d]);
+      if (!(av > 0.0)) continue;
+      const double dist = (v[d] > 0.0 ? 1.0 - o3[d] : o3[d]) - eps;
+      t = fmin(t, fmax(dist, 0.0) * dl[d] / av);
+    }
     // steps before which this neutral is certainly inside its birth cell
-    const double st = vmax > 0.0 ? fmin(floor(t / vmax / D.dt_d), 4e9) : 4e9;
+    const double st = fmin(fmax(floor(t / D.dt_d) - 1.0, 0.0), 4e9);
     smin = fmin(smin, st);
     ls[s] = (uint16_t)fmin(floor(st / 64.0), 65535.0);
   }

@@ -67,6 +67,17 @@ def config2():
                 pool_factor=3.0, name="silica-128x128x512-fp32") | {"steps": 2000}
 
 
+def layer_thickness(n_index, fraction, lam=LAMBDA):
+    """Thickness fraction * lam / n of an interference layer (lambda/(4n) for a
+    quarter-wave layer, lambda/(2n) for the mirror's cap)."""
+    return fraction * lam / n_index
+
+
+def layer_cells(n_index, fraction, d, lam=LAMBDA):
+    """That thickness staircased to whole cells of size d."""
+    return max(1, int(round(layer_thickness(n_index, fraction, lam) / d)))
+
+
 def mirror_layers(z_start, pairs, hi_cells, lo_cells, ppc, temp_eV):
     out, z = [], z_start
     for _ in range(pairs):
@@ -81,8 +92,10 @@ def config3():
     """Quarter-wave mirror in FP32: 256x256x1024 at 20 nm, 20 pairs of
     high (5 cells) / low (7 cells) starting at z = 128, 8 ppc, 4 fs /
     0.5 J cm^-2 pulse, 3000 steps."""
-    return grid(256, 256, 1024, 20e-9,
-                mirror_layers(128, 20, 5, 7, 8, 0.01),
+    d = 20e-9
+    return grid(256, 256, 1024, d,
+                mirror_layers(128, 20, layer_cells(HIGH_INDEX["n_index"], 0.25, d),
+                              layer_cells(SILICA["n_index"], 0.25, d), 8, 0.01),
                 pulse(4e-15, 0.5, 8e-15), seed=3, precision="fp32",
                 pool_factor=3.0, name="mirror-256x256x1024-fp32") | {"steps": 3000}
 

@@ -52,6 +52,7 @@ def test_query_sizes(pic):
 
 @pytest.mark.parametrize("mutate, what", [
     (lambda c: c.update(nx=3), "nx"),
+    (lambda c: c.update(nz=65535), "nz above the launch limit"),
     (lambda c: c.update(cfl=1.5), "cfl"),
     (lambda c: c.update(precision="fp16"), "precision"),
     (lambda c: c["layers"][0].update(z0=1), "layer too low"),

@@ -153,8 +153,9 @@ def test_fp64_single_steps_from_oracle_states(pic, oracle_mod):
         g.close()
 
 
-def test_fp32_single_steps_from_oracle_states(pic, oracle_mod):
-    cfg64 = wl.small_slab(precision="fp64")
+@pytest.mark.parametrize("nx", [8, 6])  # 4 x points per thread in the field kernels, and 1
+def test_fp32_single_steps_from_oracle_states(pic, oracle_mod, nx):
+    cfg64 = wl.small_slab(nx=nx, precision="fp64")
     cfg32 = dict(cfg64, precision="fp32")
     o = oracle_mod.Sim(cfg64)
     flips_total, draws_total, slack = 0, 0, 0.0
@@ -177,6 +178,32 @@ def test_fp32_single_steps_from_oracle_states(pic, oracle_mod):
         g.close()
     # FP32 moves each probability by ~1e-6 relative; flips are rare
     assert flips_total <= 3 + 1e-4 * draws_total
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hot_neutrals_crossing_faces(pic, oracle_mod, precision):
+    """Neutrals at ~0.01 c thermal speed move about a third of a cell in 60
+    steps, so most are drawn against a neighbour cell's threshold (or leave
+    the grid): the per-neutral crossing steps must switch every one of them
+    to its exact position in time."""
+    cfg = wl.small_slab(temp_eV=5e6, fluence=3.0, precision="fp64", seed=21)
+    o = oracle_mod.Sim(cfg)
+    g = pic.Simulation(dict(cfg, precision=precision))
+    o.step(60)
+    g.step(60)
+    ag, ao = g.material()["alive"], o.material()["alive"]
+    if precision == "fp64":
+        assert np.array_equal(ag, ao)
+        Fg, Fo = g.fields(), o.fields()
+        for sl in (slice(0, 3), slice(3, 6), slice(9, 12), slice(12, 15)):
+            assert rel_l2(Fg[sl], Fo[sl]) <= TOL64
+        assert_particles_close(g.particles(), o.particles(), cfg, 1e-11, 1e-11, "hot")
+    else:
+        flips = int(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(ag, ao)))
+        alive0 = int(sum(bin(int(a)).count("1") for a in ao))
+        assert flips <= 3 + 1e-3 * alive0, (flips, alive0)
+    # the run did ionise
+    assert o.scalars()["n_events"] > 50
 
 
 def test_vacuum_box_matches(pic, oracle_mod):

@@ -153,3 +153,30 @@ def test_no_ionisation_below_threshold_field(oracle_mod):
         s.phases(4 | 8 | 16)
     assert s.np == 0
     assert np.all(s.material()["T"] == 0)
+
+
+def test_ion_uniform_is_uniform_and_independent(oracle_mod):
+    """The 64-bit ionisation uniform (16 bits from a block shared by eight
+    slots, 48 from the slot's own block): its value, its low 48 bits and its
+    top 16 bits are each uniform, and the eight slots that share a block are
+    uncorrelated."""
+    stats = pytest.importorskip("scipy.stats")
+    n = 3000
+    u = np.zeros((n, 16))
+    for q in range(n):
+        step, cell = 17 + q // 50, 1000 + 7 * (q % 50)
+        for s in range(16):
+            u[q, s] = oracle_mod.ion_uniform(12345, step, cell, s)
+    top = np.floor(u / 2.0**48)
+    low = u - top * 2.0**48
+    assert stats.kstest((u / 2.0**64).ravel(), "uniform").pvalue > 1e-4
+    assert stats.kstest((low / 2.0**48).ravel(), "uniform").pvalue > 1e-4
+    counts = np.bincount((top.ravel() // 4096).astype(int), minlength=16)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    c = np.corrcoef(u.T)
+    off = c[~np.eye(16, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / math.sqrt(n)
+    # a different slot, step or cell gives a different number
+    assert len({oracle_mod.ion_uniform(1, 2, 3, s) for s in range(32)}) == 32
+    assert oracle_mod.ion_uniform(1, 2, 3, 4) != oracle_mod.ion_uniform(1, 3, 3, 4)
+    assert oracle_mod.ion_uniform(1, 2, 3, 4) != oracle_mod.ion_uniform(1, 2, 4, 4)
