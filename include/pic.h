@@ -133,6 +133,10 @@ typedef struct {
   size_t arena_bytes;        /* device bytes pic_create needs */
   long long launches;        /* kernels launched on the handle so far (pic_info) */
   double particle_steps;     /* charged-particle pushes done so far (pic_info) */
+  long long h2d_bytes;       /* host-to-device bytes the library has copied for
+                                this handle: create tables, state writes (pic_info) */
+  long long d2h_bytes;       /* device-to-host bytes it has copied: state reads,
+                                diagnostics, error checks (pic_info) */
 } pic_info;
 
 /* Kernel classes reported by pic_profile_read. */

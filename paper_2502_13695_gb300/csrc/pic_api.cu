@@ -281,6 +281,8 @@ struct pic_ctx {
   bool fp64 = true;
   int sticky = PIC_OK;
   long long launches = 0;
+  long long h2d_bytes = 0, d2h_bytes = 0;  // host <-> device bytes copied so far
+  int push_blocks = 0;                      // resident blocks of k_push on this device
   int field_v = 1;  // x points per thread of the field and window kernels
   // profiling: (class, start, stop) event triples, reused across reads
   bool profiling = false;
@@ -441,7 +443,7 @@ int enqueue(pic_ctx *h, int mask) {
   cudaStream_t s = h->stream;
   if (mask & PIC_PHASE_PARTICLES) {
     prof_begin(h, PIC_PROF_PUSH);
-    k_push<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
+    k_push<R><<<h->push_blocks, kThreads, 0, s>>>(X);
     prof_end(h);
     h->launches += 1;
   }
@@ -508,10 +510,17 @@ int init_state(pic_ctx *h) {
   const Plan &P = h->P;
   cudaStream_t s = h->stream;
   PIC_CUDA(cudaMemsetAsync(h->arena, 0, P.total, s));
+  // the push is persistent: exactly as many blocks as are resident at once
+  int dev = 0, nsm = 0, per_sm = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  PIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<R>, kThreads, 0));
+  h->push_blocks = std::max(1, nsm) * std::max(1, per_sm);
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_mplane, P.mplane.data(), P.mplane.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));
+  h->h2d_bytes += (long long)((P.lop.size() + P.mplane.size() + P.kplane.size()) * sizeof(int));
   if (!P.kplane.empty())
     PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_kplane, P.kplane.data(),
                              P.kplane.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -521,6 +530,7 @@ int init_state(pic_ctx *h) {
     std::vector<LayerR<R>> lr = layer_working<R>(P, h->lk);
     PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lr, lr.data(), lr.size() * sizeof(LayerR<R>),
                              cudaMemcpyHostToDevice, s));
+    h->h2d_bytes += (long long)(h->lk.size() * sizeof(LayerK) + lr.size() * sizeof(LayerR<R>));
     PIC_CUDA(cudaStreamSynchronize(s));  // lr is a host temporary
   }
   if (P.nmat > 0) k_init_material<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(ctx_of<R>(h));
@@ -533,6 +543,7 @@ int check_sticky(pic_ctx *h) {
   int e = 0;
   const Plan &P = h->P;
   PIC_CUDA(cudaMemcpyAsync(&e, h->arena + P.off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  h->d2h_bytes += (long long)sizeof(int);
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   if (e & kErrPool) h->sticky = PIC_EPOOL;
   if (h->sticky == PIC_EPOOL)
@@ -555,12 +566,14 @@ void from_double(const double *src, size_t n, std::vector<char> &raw) {
 
 int copy_in(pic_ctx *h, size_t off, const void *src, size_t bytes) {
   PIC_CUDA(cudaMemcpyAsync(h->arena + off, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  h->h2d_bytes += (long long)bytes;
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   return PIC_OK;
 }
 
 int copy_out(pic_ctx *h, size_t off, void *dst, size_t bytes) {
   PIC_CUDA(cudaMemcpyAsync(dst, h->arena + off, bytes, cudaMemcpyDeviceToHost, h->stream));
+  h->d2h_bytes += (long long)bytes;
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   return PIC_OK;
 }
@@ -914,6 +927,8 @@ int pic_info_get(pic_handle h, pic_info *out) {
   const int rc2 = copy_out(h, P.off_acc, acc, sizeof(acc));
   if (rc2) return rc2;
   out->particle_steps = acc[4];
+  out->h2d_bytes = h->h2d_bytes;  // including this call's own reads
+  out->d2h_bytes = h->d2h_bytes;
   return PIC_OK;
 }
 
@@ -958,6 +973,7 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
   if (dg->n_bins > 0)
     PIC_CUDA(cudaMemcpyAsync(dg->spectrum, spec, dg->n_bins * 8, cudaMemcpyDeviceToHost, s));
   PIC_CUDA(cudaStreamSynchronize(s));
+  h->d2h_bytes += (long long)((pp.size() + pg5.size() + 4 + std::max(dg->n_bins, 0)) * 8);
   double kin = 0, nel = 0, nho = 0;
   for (int b = 0; b < P.diag_blocks_p; ++b) {
     kin += pp[3 * b];

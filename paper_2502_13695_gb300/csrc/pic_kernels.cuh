@@ -178,9 +178,10 @@ __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], con
       }
 }
 
-// Blocks per SM for the push: FP32 fits three (80 registers), FP64 two.
+// Blocks per SM for the push: two (128 registers).  In FP32, 64 and 80
+// registers (four and three blocks) measured slower: the gather's loads in
+// flight per thread matter more than resident warps.
 template <class R> struct PushOcc { static constexpr int v = 2; };
-template <> struct PushOcc<float> { static constexpr int v = 3; };
 
 template <class R>
 __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
@@ -190,15 +191,40 @@ __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
   const R dl_inv[3] = {D.idx, D.idy, D.idz};
   const R c2inv = R(1.0 / (kC * kC));
   double pushed = 0.0;
-  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
-    const int cell = D.pcell[p];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  // each thread loads its next particle's state one iteration ahead, so that
+  // round trip overlaps the current particle's gather and deposit
+  int cell_n = -1;
+  R off_n[3] = {R(0), R(0), R(0)}, u_n[3] = {R(0), R(0), R(0)};
+  uint32_t tag_n = 0;
+  if (p < n) {
+    cell_n = D.pcell[p];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      off_n[d] = D.po[d][p];
+      u_n[d] = D.pu[d][p];
+    }
+    tag_n = D.ptag[p];
+  }
+  for (; p < n; p += stride) {
+    const int cell = cell_n;
+    R off[3] = {off_n[0], off_n[1], off_n[2]};
+    R u[3] = {u_n[0], u_n[1], u_n[2]};
+    const uint32_t tag = tag_n;
+    if (p + stride < n) {
+      const unsigned long long q = p + stride;
+      cell_n = D.pcell[q];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        off_n[d] = D.po[d][q];
+        u_n[d] = D.pu[d][q];
+      }
+      tag_n = D.ptag[q];
+    }
     if (cell < 0) continue;
     pushed += 1.0;
     const int ci = cell % nx, t = cell / nx, cj = t % ny, ck = t / ny;
-    R off[3] = {D.po[0][p], D.po[1][p], D.po[2][p]};
-    R u[3] = {D.pu[0][p], D.pu[1][p], D.pu[2][p]};
-    const uint32_t tag = D.ptag[p];
     const LayerR<R> &L = X.lr[tag >> 1];
     const int sp = tag & 1u;
     // shapes on the integer and half-integer grids; node offsets in elements

@@ -69,7 +69,8 @@ class Info(ctypes.Structure):
                 ("nmat", ctypes.c_longlong), ("n_neutrals", ctypes.c_longlong),
                 ("capacity", ctypes.c_longlong), ("n_particles", ctypes.c_longlong),
                 ("step", ctypes.c_longlong), ("arena_bytes", ctypes.c_size_t),
-                ("launches", ctypes.c_longlong), ("particle_steps", ctypes.c_double)]
+                ("launches", ctypes.c_longlong), ("particle_steps", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_longlong), ("d2h_bytes", ctypes.c_longlong)]
 
 
 class Diag(ctypes.Structure):
