@@ -79,6 +79,9 @@ typedef struct {
   double pool_factor;  /* charged-slot capacity = pool_factor * neutrals + 1024 */
   int keldysh_terms;   /* terms of the Q series cap (Sec. 2.1: 500) */
   int sort_interval;   /* steps between cell sorts of the pool (0: 16) */
+  int imax_every;      /* steps between records of the intensity map (Sec. 5
+                          records every 0.5 fs): 0 = round(0.5 fs / dt), < 0 off */
+  int reserved;
 } pic_grid;
 
 /* One dielectric layer: z cells [z0, z1) over the whole transverse plane.
@@ -98,6 +101,9 @@ typedef struct {
   double damping;     /* Lorentz damping rate [rad/s] */
   double temp_eV;     /* neutral temperature */
   double mol_mass_amu;/* molecular mass */
+  double e_melt;      /* damage energy densities [J/m^3] (Sec. 4.2, Sec. 5: */
+  double e_boil;      /*   melting, boiling, dissociation); 0 = not given */
+  double e_dissoc;
 } pic_layer;
 
 typedef struct {
@@ -212,6 +218,36 @@ int pic_profile_read(pic_handle h, double ms[PIC_PROF_N], long long launches[PIC
 
 /* Synchronous FP64 diagnostics of the current state. */
 int pic_diagnostics(pic_handle h, pic_diag *inout);
+
+/* Damage metrics of the current state (Sec. 4.1 electron density and its
+ * critical and instability densities, Sec. 4.2 energy density and its
+ * melting / boiling / dissociation thresholds, Sec. 5 accumulated intensity).
+ * Synchronous; FP64.
+ *   region      in: transverse node box [region[0], region[1]) x
+ *               [region[2], region[3]) (x then y), 0 <= r0 < r1 <= nx,
+ *               0 <= r2 < r3 <= ny.
+ *   ne_z, ed_z  out (host, nz + 1 doubles each, or NULL): the mean over the
+ *               box's nodes of the TSC-deposited electron density [m^-3] and
+ *               electron kinetic-energy density [J/m^3] on every node plane.
+ *   layer_out   out (host, 4 doubles per layer, or NULL): per layer the
+ *               largest ne_z and ed_z on its node planes z0 <= k < z1, the
+ *               largest recorded |E|^2 / E0^2 over its cells, and its
+ *               instability density 0.09 * 4 * n_mol (four valence electrons
+ *               per molecule).
+ *   layer_flags out (host, n_layers ints, or NULL): bit 0 n_e >= the critical
+ *               density, bit 1 n_e >= the instability density, bits 2-4 the
+ *               energy density >= e_melt, e_boil, e_dissoc (given ones only).
+ *   n_crit      out (or NULL): critical density eps0 m_e omega^2 / e^2 of free
+ *               electrons at the laser frequency [m^-3].
+ * Errors: PIC_EINVAL for a bad region or null handle; PIC_ECUDA. */
+int pic_damage(pic_handle h, const int region[4], double *ne_z, double *ed_z,
+               double *layer_out, int *layer_flags, double *n_crit);
+
+/* The intensity map: per cell (x fastest, nz * ny * nx doubles into the host
+ * array dst) the largest |E^{n+1}|^2 / E0^2 at the cell centre over the
+ * recorded steps (every imax_every steps; E0 the incident peak amplitude,
+ * raw |E|^2 when the fluence is 0).  Synchronous. */
+int pic_get_intensity_max(pic_handle h, double *dst);
 
 int pic_info_get(pic_handle h, pic_info *out);
 int pic_destroy(pic_handle h);

@@ -69,7 +69,8 @@ class Layer(ctypes.Structure):
                 ("me_star", ctypes.c_double), ("mh_star", ctypes.c_double),
                 ("n_mol", ctypes.c_double), ("omega0_eV", ctypes.c_double),
                 ("damping", ctypes.c_double), ("temp_eV", ctypes.c_double),
-                ("mol_mass_amu", ctypes.c_double)]
+                ("mol_mass_amu", ctypes.c_double), ("e_melt", ctypes.c_double),
+                ("e_boil", ctypes.c_double), ("e_dissoc", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -81,6 +82,7 @@ class Config(ctypes.Structure):
                 ("fluence", ctypes.c_double), ("cep", ctypes.c_double),
                 ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("keldysh_terms", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("imax_every", ctypes.c_int), ("pad_imax", ctypes.c_int),
                 ("layers", Layer * MAX_LAYERS)]
 
 
@@ -122,6 +124,9 @@ def lib():
             L.or_incident.restype = d
             L.or_incident.argtypes = [vp, d]
             L.or_philox.argtypes = [vp, vp, vp]
+            L.or_damage.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.or_damage.restype = d
+            L.or_get_imax.argtypes = [vp, vp]
             L.or_ion_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint32]
             L.or_ion_uniform.restype = ctypes.c_uint64
@@ -209,6 +214,7 @@ def make_config(cfg: dict) -> Config:
     c.cep, c.t_peak, c.pol = p.get("cep", 0.0), p["t_peak"], p.get("pol", 0)
     c.seed = cfg["seed"]
     c.keldysh_terms = cfg.get("keldysh_terms", 500)
+    c.imax_every = cfg.get("imax_every", 0)
     layers = cfg["layers"]
     c.n_layers = len(layers)
     for n, ly in enumerate(layers):
@@ -217,6 +223,8 @@ def make_config(cfg: dict) -> Config:
         for f in ("n_index", "gap_eV", "me_star", "mh_star", "n_mol",
                   "omega0_eV", "damping", "temp_eV", "mol_mass_amu"):
             setattr(L, f, float(ly[f]))
+        for f in ("e_melt", "e_boil", "e_dissoc"):
+            setattr(L, f, float(ly.get(f, 0.0)))
     return c
 
 
@@ -349,6 +357,29 @@ class Sim:
 
     def incident(self, t: float) -> float:
         return lib().or_incident(self._h, float(t))
+
+    def intensity_max(self) -> np.ndarray:
+        """Recorded maximum of |E|^2 / E0^2 per cell, shape (nz, ny, nx)."""
+        c = self.cfg
+        out = np.zeros((c["nz"], c["ny"], c["nx"]))
+        lib().or_get_imax(self._h, _ptr(out))
+        return out
+
+    def damage(self, region=None) -> dict:
+        """Damage metrics: region-mean n_e and energy-density profiles per node
+        plane, per-layer peaks, intensity peaks and verdict bits."""
+        c = self.cfg
+        reg = np.ascontiguousarray(region if region is not None else
+                                   [0, c["nx"], 0, c["ny"]], dtype=np.int32)
+        nl = len(c["layers"])
+        ne_z, ed_z = np.zeros(c["nz"] + 1), np.zeros(c["nz"] + 1)
+        lay = np.zeros(max(1, 4 * nl))
+        flags = np.zeros(max(1, nl), dtype=np.int32)
+        ncrit = lib().or_damage(self._h, _ptr(reg), _ptr(ne_z), _ptr(ed_z), _ptr(lay),
+                                _ptr(flags))
+        layers = [dict(ne_peak=lay[4 * L], ed_peak=lay[4 * L + 1], imax_peak=lay[4 * L + 2],
+                       n_inst=lay[4 * L + 3], flags=int(flags[L])) for L in range(nl)]
+        return dict(n_crit=ncrit, ne_z=ne_z, ed_z=ed_z, layers=layers)
 
 
 def omega_laser(lam: float) -> float:

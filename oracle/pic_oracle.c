@@ -62,6 +62,7 @@ typedef struct {
   double damping;      /* Lorentz damping [rad/s] */
   double temp_eV;      /* neutral temperature */
   double mol_mass_amu; /* molecular mass */
+  double e_melt, e_boil, e_dissoc; /* damage energy densities [J/m^3], 0 = none */
 } or_layer;
 
 typedef struct {
@@ -71,6 +72,8 @@ typedef struct {
   uint64_t seed;
   int keldysh_terms;
   int n_layers;
+  int imax_every; /* intensity record interval in steps: 0 = 0.5 fs, < 0 off */
+  int pad_imax;
   or_layer layers[OR_MAX_LAYERS];
 } or_config;
 
@@ -350,6 +353,9 @@ typedef struct {
   uint32_t *ptag;
   long step;
   double U_joule, N_pairs, U_ion, n_events;
+  /* maximum over the recorded steps of |E|^2 / E0^2 at each cell centre */
+  double *imax;
+  int imax_every;
 } or_sim;
 
 static long fidx(const or_sim *s, int i, int j, int k) {
@@ -443,6 +449,11 @@ or_sim *or_create(const or_config *cfg) {
   s->T = calloc(s->nmat ? s->nmat : 1, sizeof(uint64_t));
   s->Talways = calloc(s->nmat ? s->nmat : 1, 1);
   s->alive = calloc(s->nmat ? s->nmat : 1, sizeof(uint32_t));
+  s->imax = calloc((size_t)s->nxy * nz, sizeof(double));
+  /* the paper records the intensity every 0.5 fs (Sec. 5, Plasma Screening) */
+  s->imax_every = cfg->imax_every > 0
+                      ? cfg->imax_every
+                      : (cfg->imax_every == 0 ? (int)fmax(1.0, round(0.5e-15 / s->dt)) : 0);
   for (int k = 0; k < nz; k++) {
     int L = s->layer_of_plane[k];
     if (L < 0) continue;
@@ -457,6 +468,7 @@ or_sim *or_create(const or_config *cfg) {
 
 void or_destroy(or_sim *s) {
   if (!s) return;
+  free(s->imax);
   for (int c = 0; c < NCOMP; c++) free(s->F[c]);
   free(s->layer_of_plane);
   free(s->mplane);
@@ -703,11 +715,38 @@ static void e_full(or_sim *s) {
   s->U_joule += joule * dt * s->V;
 }
 
+/* Accumulated intensity map (Sec. 5, Plasma Screening, Fig. 7c): every
+ * imax_every steps, |E^{n+1}|^2 at each cell centre (4-edge means, as the
+ * amplitude window) over E0^2 (the incident peak amplitude; raw |E|^2 when
+ * E0 = 0), kept as the running maximum. */
+static void record_intensity(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
+  const double norm = s->E0 > 0.0 ? 1.0 / (s->E0 * s->E0) : 1.0;
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        double ax = 0.25 * (((Ex[fidx(s, i, j, k)] + Ex[fidx(s, i, j + 1, k)]) +
+                             Ex[fidx(s, i, j, k + 1)]) +
+                            Ex[fidx(s, i, j + 1, k + 1)]);
+        double ay = 0.25 * (((Ey[fidx(s, i, j, k)] + Ey[fidx(s, i + 1, j, k)]) +
+                             Ey[fidx(s, i, j, k + 1)]) +
+                            Ey[fidx(s, i + 1, j, k + 1)]);
+        double az = 0.25 * (((Ez[fidx(s, i, j, k)] + Ez[fidx(s, i + 1, j, k)]) +
+                             Ez[fidx(s, i, j + 1, k)]) +
+                            Ez[fidx(s, i + 1, j + 1, k)]);
+        double v = (ax * ax + ay * ay + az * az) * norm;
+        long c = ((long)k * ny + j) * nx + i;
+        if (v > s->imax[c]) s->imax[c] = v;
+      }
+}
+
 void or_field_pass(or_sim *s) {
   b_half(s);
   e_full(s);
   b_half(s);
   for (int d = 0; d < 3; d++) memset(s->F[FJX + d], 0, s->nfield * sizeof(double));
+  if (s->imax_every > 0 && (s->step + 1) % s->imax_every == 0) record_intensity(s);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -874,6 +913,85 @@ void or_rho(const or_sim *s, double *rho) {
     deposit_node(s, rho, cell % nx, (cell / nx) % ny, cell / (nx * ny),
                  &s->poff[3 * p], q);
   }
+}
+
+/* Damage metrics (Sec. 4.1-4.2 criteria, Sec. 5): n_e and the electron
+ * energy density (number density x mean kinetic energy, i.e. the deposited
+ * w E_k / V) on the nodes with the TSC shape; their mean over the nodes
+ * (i, j) of the transverse box [r0, r1) x [r2, r3) on every node plane k
+ * (ne_z, ed_z: nz + 1 values); per layer the largest profile value on its
+ * node planes z0 <= k < z1, the largest recorded intensity over its cells,
+ * and the verdicts (bit 0: n_e >= critical density eps0 m_e w^2 / e^2 of
+ * free electrons; bit 1: n_e >= 9% of the valence density, four valence
+ * electrons per molecule; bits 2-4: energy density >= melting, boiling,
+ * dissociation energy density, where given).  out_layers holds 4 doubles
+ * per layer: ne_peak, ed_peak, imax_peak, instability density.  Returns the
+ * critical density. */
+double or_damage(const or_sim *s, const int region[4], double *ne_z, double *ed_z,
+                 double *out_layers, int *flags) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  double *ne = calloc(s->nfield, sizeof(double));
+  double *ed = calloc(s->nfield, sizeof(double));
+  for (long p = 0; p < s->np; p++) {
+    int32_t cell = s->pcell[p];
+    int L = (int)(s->ptag[p] >> 1), sp = (int)(s->ptag[p] & 1u);
+    if (sp != 0) continue;
+    int ci = cell % nx, cj = (cell / nx) % ny, ck = cell / (nx * ny);
+    const double *u = &s->pu[3 * p];
+    double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (OR_C * OR_C));
+    double ek = (g - 1.0) * s->mass[L][0] * OR_C * OR_C;
+    deposit_node(s, ne, ci, cj, ck, &s->poff[3 * p], s->wmac[L] / s->V);
+    deposit_node(s, ed, ci, cj, ck, &s->poff[3 * p], s->wmac[L] * ek / s->V);
+  }
+  double cnt = (double)(region[1] - region[0]) * (double)(region[3] - region[2]);
+  double *pz = malloc((size_t)(nz + 1) * 2 * sizeof(double));
+  for (int k = 0; k <= nz; k++) {
+    double a = 0.0, b = 0.0;
+    for (int j = region[2]; j < region[3]; j++)
+      for (int i = region[0]; i < region[1]; i++) {
+        a += ne[fidx(s, i, j, k)];
+        b += ed[fidx(s, i, j, k)];
+      }
+    pz[2 * k] = cnt > 0.0 ? a / cnt : 0.0;
+    pz[2 * k + 1] = cnt > 0.0 ? b / cnt : 0.0;
+    if (ne_z) ne_z[k] = pz[2 * k];
+    if (ed_z) ed_z[k] = pz[2 * k + 1];
+  }
+  double ncrit = OR_EPS0 * OR_ME * s->omega * s->omega / (OR_QE * OR_QE);
+  for (int L = 0; L < s->cfg.n_layers; L++) {
+    const or_layer *ly = &s->cfg.layers[L];
+    double mne = 0.0, med = 0.0, mi = 0.0;
+    for (int k = ly->z0; k < ly->z1; k++) {
+      if (pz[2 * k] > mne) mne = pz[2 * k];
+      if (pz[2 * k + 1] > med) med = pz[2 * k + 1];
+      for (long q = 0; q < s->nxy; q++)
+        if (s->imax[(long)k * s->nxy + q] > mi) mi = s->imax[(long)k * s->nxy + q];
+    }
+    double ninst = 0.09 * 4.0 * ly->n_mol;
+    if (out_layers) {
+      out_layers[4 * L] = mne;
+      out_layers[4 * L + 1] = med;
+      out_layers[4 * L + 2] = mi;
+      out_layers[4 * L + 3] = ninst;
+    }
+    if (flags) {
+      int f = 0;
+      if (mne >= ncrit) f |= 1;
+      if (mne >= ninst) f |= 2;
+      if (ly->e_melt > 0.0 && med >= ly->e_melt) f |= 4;
+      if (ly->e_boil > 0.0 && med >= ly->e_boil) f |= 8;
+      if (ly->e_dissoc > 0.0 && med >= ly->e_dissoc) f |= 16;
+      flags[L] = f;
+    }
+  }
+  free(pz);
+  free(ne);
+  free(ed);
+  return ncrit;
+}
+
+void or_get_imax(const or_sim *s, double *out) {
+  memcpy(out, s->imax, (size_t)s->nxy * s->cfg.nz * sizeof(double));
 }
 
 void or_diagnostics(const or_sim *s, or_diag *dg, int n_bins, double e_min_eV,

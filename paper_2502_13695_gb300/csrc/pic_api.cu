@@ -54,6 +54,8 @@ struct Plan {
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
   size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
   size_t off_work, off_work_n, off_leave16;
+  size_t off_imax, off_prof;
+  int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t total;
@@ -90,6 +92,10 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.omega = 2.0 * kPi * kC / pulse->lambda;
   P.V = g.dx * g.dy * g.dz;
   P.NW = (int)std::ceil(pulse->lambda / (kC * P.dt));
+  // the paper records the intensity map every 0.5 fs (Sec. 5)
+  P.imax_every = g.imax_every > 0
+                     ? g.imax_every
+                     : (g.imax_every == 0 ? (int)std::max(1.0, std::round(0.5e-15 / P.dt)) : 0);
   P.E0 = std::sqrt(2.0 * pulse->fluence /
                    (kC * kEps0 * pulse->fwhm * std::sqrt(kPi / (4.0 * std::log(2.0)))));
   P.lop.assign(g.nz, -1);
@@ -100,7 +106,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
       return fail(PIC_EINVAL, "layer " + std::to_string(L) + " must satisfy 2 <= z0 < z1 <= nz-2");
     if (ly.ppc < 1 || ly.ppc > 32) return fail(PIC_EINVAL, "ppc must be in 1..32");
     if (!(ly.n_index >= 1 && ly.gap_eV > 0 && ly.me_star > 0 && ly.mh_star > 0 && ly.n_mol > 0 &&
-          ly.omega0_eV > 0 && ly.damping >= 0 && ly.temp_eV >= 0 && ly.mol_mass_amu > 0))
+          ly.omega0_eV > 0 && ly.damping >= 0 && ly.temp_eV >= 0 && ly.mol_mass_amu > 0 &&
+          ly.e_melt >= 0 && ly.e_boil >= 0 && ly.e_dissoc >= 0))
       return fail(PIC_EINVAL, "layer " + std::to_string(L) + " has a non-physical parameter");
     if (std::isfinite(ly.omega0_eV) && ly.omega0_eV * kQe / kHbar <= P.omega)
       return fail(PIC_EINVAL, "Lorentz pole must lie above the laser frequency");
@@ -161,6 +168,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   for (const pic_layer &ly : P.layers) P.ppc_max = std::max(P.ppc_max, ly.ppc);
   P.off_leave16 = take(std::max<long long>(P.nmat, 1) * P.ppc_max * 2);
   P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
+  P.off_imax = take(P.ncell * R);
+  P.off_prof = take((size_t)(2 * (g.nz + 1) + g.nz) * 8);
   P.off_work_n = take(16);
   P.off_cnt = take(P.ncell * 4);
   P.off_bsum = take((size_t)P.nb_scan * 4);
@@ -373,6 +382,9 @@ void bind(pic_ctx *h) {
   D.cap = (unsigned long long)P.cap;
   D.nslots = (unsigned long long *)(A + P.off_nslots);
   D.step = (long long *)(A + P.off_step);
+  D.imax = (R *)(A + P.off_imax);
+  D.imax_every = P.imax_every;
+  D.inv_e0sq = R(P.E0 > 0.0 ? 1.0 / (P.E0 * P.E0) : 1.0);
   D.acc = (double *)(A + P.off_acc);
   D.err = (int *)(A + P.off_err);
   D.seed = h->seed;
@@ -452,16 +464,16 @@ int enqueue(pic_ctx *h, int mask) {
     if constexpr (sizeof(R) == 4) {
       if (h->field_v == 4) {
         const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
-        k_bhalf<4, R><<<grid, kThreads, 0, s>>>(X.d);
+        k_bhalf<4, false, R><<<grid, kThreads, 0, s>>>(X.d);
         k_efull<4, R><<<grid, kThreads, 0, s>>>(X);
-        k_bhalf<4, R><<<grid, kThreads, 0, s>>>(X.d);
+        k_bhalf<4, true, R><<<grid, kThreads, 0, s>>>(X.d);
       }
     }
     if (h->field_v == 1) {
       const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
-      k_bhalf<1, R><<<grid, kThreads, 0, s>>>(X.d);
+      k_bhalf<1, false, R><<<grid, kThreads, 0, s>>>(X.d);
       k_efull<1, R><<<grid, kThreads, 0, s>>>(X);
-      k_bhalf<1, R><<<grid, kThreads, 0, s>>>(X.d);
+      k_bhalf<1, true, R><<<grid, kThreads, 0, s>>>(X.d);
     }
     prof_end(h);
     h->launches += 3;
@@ -929,6 +941,93 @@ int pic_info_get(pic_handle h, pic_info *out) {
   out->particle_steps = acc[4];
   out->h2d_bytes = h->h2d_bytes;  // including this call's own reads
   out->d2h_bytes = h->d2h_bytes;
+  return PIC_OK;
+}
+
+int pic_damage(pic_handle h, const int region[4], double *ne_z, double *ed_z, double *layer_out,
+               int *layer_flags, double *n_crit) {
+  if (!h || !region) return fail(PIC_EINVAL, "null pointer");
+  const Plan &P = h->P;
+  const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
+  if (region[0] < 0 || region[1] > nx || region[0] >= region[1] || region[2] < 0 ||
+      region[3] > ny || region[2] >= region[3])
+    return fail(PIC_EINVAL, "region must be a non-empty box inside [0, nx) x [0, ny)");
+  int rc = check_sticky(h);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  char *A = h->arena;
+  double *ne = (double *)(A + P.off_ne), *ed = (double *)(A + P.off_ed),
+         *rho = (double *)(A + P.off_rho), *spec = (double *)(A + P.off_spec),
+         *part = (double *)(A + P.off_part), *prof = (double *)(A + P.off_prof);
+  PIC_CUDA(cudaMemsetAsync(ne, 0, P.nfield * 8, s));
+  PIC_CUDA(cudaMemsetAsync(ed, 0, P.nfield * 8, s));
+  PIC_CUDA(cudaMemsetAsync(rho, 0, P.nfield * 8, s));
+  const int4 r0 = make_int4(0, nx, 0, ny);
+  const int2 r1 = make_int2(0, nz);
+  if (h->fp64) {
+    k_diag_particles<double><<<P.diag_blocks_p, kThreads, 0, s>>>(h->c64, ne, ed, rho, spec, 0, 0.0,
+                                                                  1.0, r0, r1, part);
+    k_imax_plane<double><<<nz, kThreads, 0, s>>>(h->c64.d.imax, (int)P.nxy, prof + 2 * (nz + 1));
+  } else {
+    k_diag_particles<float><<<P.diag_blocks_p, kThreads, 0, s>>>(h->c32, ne, ed, rho, spec, 0, 0.0,
+                                                                 1.0, r0, r1, part);
+    k_imax_plane<float><<<nz, kThreads, 0, s>>>(h->c32.d.imax, (int)P.nxy, prof + 2 * (nz + 1));
+  }
+  k_profile<<<nz + 1, kThreads, 0, s>>>(ne, ed, nx, ny,
+                                        make_int4(region[0], region[1], region[2], region[3]), prof);
+  PIC_CUDA(cudaGetLastError());
+  std::vector<double> hp(3 * nz + 2);
+  PIC_CUDA(cudaMemcpyAsync(hp.data(), prof, hp.size() * 8, cudaMemcpyDeviceToHost, s));
+  PIC_CUDA(cudaStreamSynchronize(s));
+  h->d2h_bytes += (long long)(hp.size() * 8);
+  // region means per node plane; per layer the peaks over its planes and
+  // the verdicts (critical density of free electrons at the laser frequency,
+  // 9% of four valence electrons per molecule, the layer's energy densities)
+  const double cnt = (double)(region[1] - region[0]) * (double)(region[3] - region[2]);
+  const double ncrit = kEps0 * kMe * P.omega * P.omega / (kQe * kQe);
+  for (int k = 0; k <= nz; ++k) {
+    if (ne_z) ne_z[k] = hp[2 * k] / cnt;
+    if (ed_z) ed_z[k] = hp[2 * k + 1] / cnt;
+  }
+  for (size_t L = 0; L < P.layers.size(); ++L) {
+    const pic_layer &ly = P.layers[L];
+    double mne = 0.0, med = 0.0, mi = 0.0;
+    for (int k = ly.z0; k < ly.z1; ++k) {
+      mne = std::max(mne, hp[2 * k] / cnt);
+      med = std::max(med, hp[2 * k + 1] / cnt);
+      mi = std::max(mi, hp[2 * (nz + 1) + k]);
+    }
+    const double ninst = 0.09 * 4.0 * ly.n_mol;
+    if (layer_out) {
+      layer_out[4 * L] = mne;
+      layer_out[4 * L + 1] = med;
+      layer_out[4 * L + 2] = mi;
+      layer_out[4 * L + 3] = ninst;
+    }
+    if (layer_flags) {
+      int f = 0;
+      if (mne >= ncrit) f |= 1;
+      if (mne >= ninst) f |= 2;
+      if (ly.e_melt > 0.0 && med >= ly.e_melt) f |= 4;
+      if (ly.e_boil > 0.0 && med >= ly.e_boil) f |= 8;
+      if (ly.e_dissoc > 0.0 && med >= ly.e_dissoc) f |= 16;
+      layer_flags[L] = f;
+    }
+  }
+  if (n_crit) *n_crit = ncrit;
+  return PIC_OK;
+}
+
+int pic_get_intensity_max(pic_handle h, double *dst) {
+  if (!h || !dst) return fail(PIC_EINVAL, "null pointer");
+  const Plan &P = h->P;
+  std::vector<char> raw((size_t)P.ncell * P.rsz);
+  const int rc = copy_out(h, P.off_imax, raw.data(), raw.size());
+  if (rc) return rc;
+  if (h->fp64)
+    to_double<double>(raw, (size_t)P.ncell, dst);
+  else
+    to_double<float>(raw, (size_t)P.ncell, dst);
   return PIC_OK;
 }
 

@@ -70,6 +70,11 @@ struct Dev {
   unsigned long long cap;
   unsigned long long *nslots;     // slots in use
   long long *step;                // device step counter
+  // intensity map: per cell the largest recorded |E|^2 / E0^2, recorded when
+  // (step + 1) % imax_every == 0 (0: never)
+  R *imax;
+  int imax_every;
+  R inv_e0sq;
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
   int *err;
   unsigned long long seed;

@@ -340,8 +340,10 @@ __device__ __forceinline__ void stv(R *p, const R *d) {
   }
 }
 
-// B half step (Faraday) on V points of plane blockIdx.y.
-template <int V, class R>
+// B half step (Faraday) on V points of plane blockIdx.y.  kRecord (the half
+// step after the E update): on the steps where the intensity map is
+// recorded, also fold |E^{n+1}|^2 / E0^2 at the V cell centres into it.
+template <int V, bool kRecord, class R>
 __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
@@ -376,6 +378,28 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
 #pragma unroll
     for (int l = 0; l < V; ++l) b[l] -= h * ((exk[l] - ex[l]) * D.idz - (ez[l + 1] - ez[l]) * D.idx);
     stv<V>(D.B[1] + o, b);
+    if constexpr (kRecord) {
+      const int every = D.imax_every;
+      if (every > 0 && (*D.step + 1) % every == 0) {
+        // cell-centred |E|: mean of the four edge values of each component
+        const long long ojv = (i + V == nx) ? oj + V - nx : oj + V;
+        R exjk[V], a2[V], im[V];
+        ldv<V>(exjk, D.E[0] + oj + nxy);
+        const R eyk_v = D.E[1][ov + nxy], ezj_v = D.E[2][ojv];
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          const R ax = R(0.25) * (((ex[l] + exj[l]) + exk[l]) + exjk[l]);
+          const R ay = R(0.25) * (((ey[l] + ey[l + 1]) + eyk[l]) + (l + 1 < V ? eyk[l + 1] : eyk_v));
+          const R az = R(0.25) * (((ez[l] + ez[l + 1]) + ezj[l]) + (l + 1 < V ? ezj[l + 1] : ezj_v));
+          a2[l] = (ax * ax + ay * ay + az * az) * D.inv_e0sq;
+        }
+        R *const cell = D.imax + (long long)k * nxy + r;
+        ldv<V>(im, cell);
+#pragma unroll
+        for (int l = 0; l < V; ++l) im[l] = fmax(im[l], a2[l]);
+        stv<V>(cell, im);
+      }
+    }
   }
 }
 
@@ -1240,6 +1264,38 @@ __global__ void __launch_bounds__(256) k_diag_grid(Ctx<R> X, const double *ne, c
     p[3] = v3;
     p[4] = v4;
   }
+}
+
+// Damage profiles: one block per node plane k sums the deposited n_e and
+// energy density over the transverse node box [reg.x, reg.y) x [reg.z, reg.w)
+// in a fixed order; out[2k], out[2k + 1].
+__global__ void __launch_bounds__(256) k_profile(const double *ne, const double *ed, int nx, int ny,
+                                                  int4 reg, double *out) {
+  const long long base = (long long)blockIdx.x * nx * ny;
+  const int w = reg.y - reg.x, n = w * (reg.w - reg.z);
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const long long o = base + (long long)(reg.z + q / w) * nx + (reg.x + q % w);
+    a += ne[o];
+    b += ed[o];
+  }
+  const double sa = block_sum<double>(a);
+  __syncthreads();
+  const double sb = block_sum<double>(b);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = sa;
+    out[2 * blockIdx.x + 1] = sb;
+  }
+}
+
+// Largest recorded intensity on cell plane blockIdx.x.
+template <class R>
+__global__ void __launch_bounds__(256) k_imax_plane(const R *imax, int nxy, double *out) {
+  const long long base = (long long)blockIdx.x * nxy;
+  double m = 0.0;
+  for (int q = threadIdx.x; q < nxy; q += blockDim.x) m = fmax(m, (double)imax[base + q]);
+  const double v = block_max(m);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
 }  // namespace pg

@@ -25,7 +25,8 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_get_fields", "pic_set_fields", "pic_get_particles",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
-           "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy"]
+           "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
+           "pic_damage", "pic_get_intensity_max"]
 PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other"]
 
 
@@ -40,7 +41,8 @@ class Grid(ctypes.Structure):
                 ("precision", ctypes.c_int), ("dx", ctypes.c_double),
                 ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("pool_factor", ctypes.c_double),
-                ("keldysh_terms", ctypes.c_int), ("sort_interval", ctypes.c_int)]
+                ("keldysh_terms", ctypes.c_int), ("sort_interval", ctypes.c_int),
+                ("imax_every", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Layer(ctypes.Structure):
@@ -48,7 +50,7 @@ class Layer(ctypes.Structure):
                 ("reserved", ctypes.c_int)] + [
         (n, ctypes.c_double) for n in ("n_index", "gap_eV", "me_star", "mh_star",
                                         "n_mol", "omega0_eV", "damping", "temp_eV",
-                                        "mol_mass_amu")]
+                                        "mol_mass_amu", "e_melt", "e_boil", "e_dissoc")]
 
 
 class Material(ctypes.Structure):
@@ -109,6 +111,8 @@ def lib():
         L.pic_step_phases.argtypes = [vp, i]
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, P(Diag)]
+        L.pic_damage.argtypes = [vp, vp, vp, vp, vp, vp, P(ctypes.c_double)]
+        L.pic_get_intensity_max.argtypes = [vp, vp]
         L.pic_info_get.argtypes = [vp, P(Info)]
         L.pic_destroy.argtypes = [vp]
         L.pic_last_error.restype = ctypes.c_char_p
@@ -152,6 +156,7 @@ def c_structs(cfg: dict):
     g.pool_factor = cfg.get("pool_factor", 3.0)
     g.keldysh_terms = cfg.get("keldysh_terms", 500)
     g.sort_interval = cfg.get("sort_interval", 0)
+    g.imax_every = cfg.get("imax_every", 0)
     layers = (Layer * max(1, len(cfg["layers"])))()
     for n, ly in enumerate(cfg["layers"]):
         L = layers[n]
@@ -159,6 +164,8 @@ def c_structs(cfg: dict):
         for f in ("n_index", "gap_eV", "me_star", "mh_star", "n_mol", "omega0_eV",
                   "damping", "temp_eV", "mol_mass_amu"):
             setattr(L, f, float(ly[f]))
+        for f in ("e_melt", "e_boil", "e_dissoc"):
+            setattr(L, f, float(ly.get(f, 0.0)))
     m = Material()
     m.n_layers = len(cfg["layers"])
     m.layers = ctypes.cast(layers, ctypes.POINTER(Layer))
@@ -258,6 +265,30 @@ class Simulation:
         out = {f: getattr(dg, f) for f, _ in Diag._fields_
                if f not in ("reserved", "reserved2", "region", "spectrum")}
         out["spectrum"] = spec[:n_bins]
+        return out
+
+    def damage(self, region=None) -> dict:
+        """Damage metrics (pic_damage): region-mean n_e and energy-density
+        profiles per node plane, per-layer peaks and verdict bits."""
+        c = self.cfg
+        reg = np.ascontiguousarray(region if region is not None else [0, c["nx"], 0, c["ny"]],
+                                   dtype=np.int32)
+        nl = len(c["layers"])
+        ne_z, ed_z = np.zeros(c["nz"] + 1), np.zeros(c["nz"] + 1)
+        lay = np.zeros(max(1, 4 * nl))
+        flags = np.zeros(max(1, nl), dtype=np.int32)
+        ncrit = ctypes.c_double()
+        _check(lib().pic_damage(self._h, _ptr(reg), _ptr(ne_z), _ptr(ed_z), _ptr(lay),
+                                _ptr(flags), ctypes.byref(ncrit)))
+        layers = [dict(ne_peak=lay[4 * L], ed_peak=lay[4 * L + 1], imax_peak=lay[4 * L + 2],
+                       n_inst=lay[4 * L + 3], flags=int(flags[L])) for L in range(nl)]
+        return dict(n_crit=ncrit.value, ne_z=ne_z, ed_z=ed_z, layers=layers)
+
+    def intensity_max(self) -> np.ndarray:
+        """Recorded maximum of |E|^2 / E0^2 per cell, shape (nz, ny, nx)."""
+        c = self.cfg
+        out = np.zeros((c["nz"], c["ny"], c["nx"]))
+        _check(lib().pic_get_intensity_max(self._h, _ptr(out)))
         return out
 
     # state ------------------------------------------------------------------

@@ -7,7 +7,11 @@ Keldysh constants and so on are computed independently by each side.
 
 Materials follow Table 1 of the paper (Sec. 3.2) with the indices and gaps the
 workloads prescribe: fused silica n = 1.45, 9 eV; the high-index mirror layer
-n = 2.1, 3.8 eV with the HfO2 effective masses and molecular density.
+n = 2.1, 3.8 eV with the HfO2 effective masses and molecular density.  Their
+damage energy densities (J m^-3) are the paper's: SiO2 melting 5.7, boiling
+34.7 and dissociation 54 kJ cm^-3 (the low end of 54-68, Sec. 4.2); HfO2
+melting 10.7 and boiling 49.9 kJ cm^-3 and the SiO2 dissociation value, which
+the paper assumes for HfO2 (Sec. 5).
 """
 from __future__ import annotations
 
@@ -20,10 +24,10 @@ KB_EV_PER_K = 8.617333262e-5  # Boltzmann constant in eV/K
 
 SILICA = dict(n_index=1.45, gap_eV=9.0, me_star=0.6, mh_star=8.0,
               n_mol=2.2e28, omega0_eV=9.0, damping=0.0,
-              mol_mass_amu=60.08)
+              mol_mass_amu=60.08, e_melt=5.7e9, e_boil=34.7e9, e_dissoc=54e9)
 HIGH_INDEX = dict(n_index=2.1, gap_eV=3.8, me_star=1.09, mh_star=1.12,
                   n_mol=2.77e28, omega0_eV=3.8, damping=0.0,
-                  mol_mass_amu=210.49)
+                  mol_mass_amu=210.49, e_melt=10.7e9, e_boil=49.9e9, e_dissoc=54e9)
 
 
 def layer(z0, z1, material, ppc, temp_eV, **over):
@@ -39,11 +43,11 @@ def pulse(fwhm, fluence_Jcm2, t_peak, cep=0.0, pol=0, lam=LAMBDA):
 
 
 def grid(nx, ny, nz, d, layers, pls, seed, precision="fp32", cfl=0.95,
-         pool_factor=3.0, keldysh_terms=500, name=""):
+         pool_factor=3.0, keldysh_terms=500, name="", imax_every=0):
     return dict(name=name, nx=nx, ny=ny, nz=nz, dx=d, dy=d, dz=d, cfl=cfl,
                 layers=layers, pulse=pls, seed=int(seed),
                 precision=precision, pool_factor=pool_factor,
-                keldysh_terms=keldysh_terms)
+                keldysh_terms=keldysh_terms, imax_every=imax_every)
 
 
 # --------------------------------------------------------------------------
