@@ -82,7 +82,7 @@ class Config(ctypes.Structure):
                 ("fluence", ctypes.c_double), ("cep", ctypes.c_double),
                 ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("keldysh_terms", ctypes.c_int), ("n_layers", ctypes.c_int),
-                ("imax_every", ctypes.c_int), ("pad_imax", ctypes.c_int),
+                ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int),
                 ("layers", Layer * MAX_LAYERS)]
 
 
@@ -127,6 +127,12 @@ def lib():
             L.or_damage.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_damage.restype = d
             L.or_get_imax.argtypes = [vp, vp]
+            L.or_nanbu_A.argtypes = [d]
+            L.or_nanbu_A.restype = d
+            L.or_nanbu_cos.argtypes = [d, d]
+            L.or_nanbu_cos.restype = d
+            L.or_collide_pair.argtypes = [vp, vp, d, d, d, d, d, d, d, d, d, vp]
+            L.or_collide_pair.restype = d
             L.or_ion_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint32]
             L.or_ion_uniform.restype = ctypes.c_uint64
@@ -161,6 +167,25 @@ def philox(ctr, key) -> np.ndarray:
 def ion_uniform(seed: int, step: int, cell: int, slot: int) -> int:
     """The 64-bit uniform a neutral compares with its ionisation threshold."""
     return int(lib().or_ion_uniform(int(seed), int(step), int(cell), int(slot)))
+
+
+def nanbu_A(s: float) -> float:
+    return lib().or_nanbu_A(float(s))
+
+
+def nanbu_cos(s: float, U: float) -> float:
+    return lib().or_nanbu_cos(float(s), float(U))
+
+
+def collide_pair(ua, ub, ma, mb, wa, wb, neff, na, nb, lambda_D, dtc, U):
+    """One binary collision; returns (ua', ub', s)."""
+    a = np.array(ua, dtype=np.float64)
+    b = np.array(ub, dtype=np.float64)
+    uu = np.ascontiguousarray(U, dtype=np.float64)
+    sv = lib().or_collide_pair(_ptr(a), _ptr(b), float(ma), float(mb), float(wa), float(wb),
+                               float(neff), float(na), float(nb), float(lambda_D), float(dtc),
+                               _ptr(uu))
+    return a, b, sv
 
 
 def dawson(z: float) -> float:
@@ -215,6 +240,7 @@ def make_config(cfg: dict) -> Config:
     c.seed = cfg["seed"]
     c.keldysh_terms = cfg.get("keldysh_terms", 500)
     c.imax_every = cfg.get("imax_every", 0)
+    c.coll_every = cfg.get("coll_every", 0)
     layers = cfg["layers"]
     c.n_layers = len(layers)
     for n, ly in enumerate(layers):

@@ -45,6 +45,8 @@
 #define OR_STREAM_VEL 2u
 #define OR_STREAM_ION 3u
 #define OR_STREAM_ION_LOW 4u
+#define OR_STREAM_COLL_ORDER 5u
+#define OR_STREAM_COLL_PAIR 6u
 
 /* ------------------------------------------------------------------------ */
 /* Configuration (mirrors the library's inputs, declared independently)     */
@@ -73,7 +75,7 @@ typedef struct {
   int keldysh_terms;
   int n_layers;
   int imax_every; /* intensity record interval in steps: 0 = 0.5 fs, < 0 off */
-  int pad_imax;
+  int coll_every; /* steps between binary-collision passes, 0 = none */
   or_layer layers[OR_MAX_LAYERS];
 } or_config;
 
@@ -873,10 +875,269 @@ void or_ionize_pass(or_sim *s) {
   }
 }
 
-/* Phases of one step: 1 particle, 2 field, 4 window + Keldysh, 8 ionisation,
- * 16 advance the step counter.  A full step is 31. */
+/* ------------------------------------------------------------------------ */
+/* Binary collisions among electrons and holes (Sec. 2.2: the Perez/Nanbu    */
+/* module, here written from the published methods: Nanbu, Phys. Rev. E 55,  */
+/* 4642 (1997) for the cumulative scattering angle; Perez et al., Phys.      */
+/* Plasmas 19, 083104 (2012) for the relativistic centre-of-mass frame, the  */
+/* Coulomb logarithm and the low-temperature cap).                           */
+/* ------------------------------------------------------------------------ */
+#define OR_H (2.0 * OR_PI * OR_HBAR)
+
+/* Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s). */
+double or_nanbu_A(double s) {
+  double target = exp(-s);
+  double lo = 1e-12, hi = 1e12;
+  for (int it = 0; it < 200; it++) { /* bisection on log A */
+    double mid = sqrt(lo * hi);
+    double g = mid < 1e-4 ? mid / 3.0 - mid * mid * mid / 45.0 : 1.0 / tanh(mid) - 1.0 / mid;
+    if (g < target)
+      lo = mid;
+    else
+      hi = mid;
+    if (hi / lo < 1.0 + 4e-16) break;
+  }
+  return sqrt(lo * hi);
+}
+
+/* cos chi of the cumulative scattering angle for parameter s and uniform U
+ * (Nanbu): small s 1 + s ln U; large s isotropic; between, the inverse of
+ * the distribution A exp(A cos chi) / (2 sinh A). */
+double or_nanbu_cos(double s, double U) {
+  double c;
+  if (s < 0.1) {
+    c = 1.0 + s * log(U);
+  } else if (s < 6.0) {
+    double A = or_nanbu_A(s);
+    c = log(exp(-A) + 2.0 * U * sinh(A)) / A;
+  } else {
+    c = 2.0 * U - 1.0;
+  }
+  return c < -1.0 ? -1.0 : (c > 1.0 ? 1.0 : c);
+}
+
+/* One binary collision of macroparticles a and b (u = gamma v per unit mass,
+ * masses m, weights w, charges of magnitude e), Perez et al.: transform to
+ * the centre-of-mass frame, rotate the relative momentum by the sampled
+ * (chi, phi), transform back.  neff = n_a n_b / n_ab (inter) or n (intra),
+ * times `frac` (1/2 for the odd-count triplet); na, nb the group densities;
+ * lambda_D the screening length; dtc the collision interval; U[4] uniforms:
+ * angle, azimuth, acceptance of a, acceptance of b.  Returns s. */
+double or_collide_pair(double ua[3], double ub[3], double ma, double mb, double wa, double wb,
+                       double neff, double na, double nb, double lambda_D, double dtc,
+                       const double U[4]) {
+  const double c = OR_C, c2 = OR_C * OR_C;
+  double ga = sqrt(1.0 + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]) / c2);
+  double gb = sqrt(1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]) / c2);
+  double pa[3], pb[3], va[3], vb[3], vc[3];
+  double Etot = ma * ga + mb * gb; /* total energy / c^2 */
+  for (int d = 0; d < 3; d++) {
+    pa[d] = ma * ua[d];
+    pb[d] = mb * ub[d];
+    va[d] = ua[d] / ga;
+    vb[d] = ub[d] / gb;
+    vc[d] = (pa[d] + pb[d]) / Etot;
+  }
+  double vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
+  double gc = 1.0 / sqrt(1.0 - vc2 / c2);
+  double kc = gc * gc / (c2 * (gc + 1.0)); /* (gamma_c - 1) / v_c^2 */
+  double vcva = vc[0] * va[0] + vc[1] * va[1] + vc[2] * va[2];
+  double vcvb = vc[0] * vb[0] + vc[1] * vb[1] + vc[2] * vb[2];
+  double pst[3];
+  for (int d = 0; d < 3; d++) pst[d] = pa[d] + (kc * vcva - gc) * ma * ga * vc[d];
+  double gsa = (1.0 - vcva / c2) * gc * ga, gsb = (1.0 - vcvb / c2) * gc * gb;
+  double p2 = pst[0] * pst[0] + pst[1] * pst[1] + pst[2] * pst[2];
+  double pm = sqrt(p2);
+  if (!(pm > 0.0)) return 0.0;
+  double e2 = OR_QE * OR_QE;
+  double mm = ma * gsa * mb * gsb * c2 / p2 + 1.0;
+  double b0 = e2 / (4.0 * OR_PI * OR_EPS0 * c2) * gc / Etot * mm;
+  double bmin = fmax(OR_H / (2.0 * pm), b0);
+  double lnL = fmax(1.0, 0.5 * log(1.0 + lambda_D * lambda_D / (bmin * bmin)));
+  double sv = neff * dtc * lnL * e2 * e2 /
+              (4.0 * OR_PI * OR_EPS0 * OR_EPS0 * c2 * c2 * ma * ga * mb * gb) * gc * pm / Etot *
+              mm * mm;
+  /* low-temperature cap: collisions no faster than the mean interparticle
+   * spacing allows (Perez et al.) */
+  double vrel = Etot * pm / (ma * gsa * mb * gsb * gc);
+  double dens = fmax(ma * pow(na, 2.0 / 3.0), mb * pow(nb, 2.0 / 3.0));
+  double scap = neff * dtc * pow(4.0 * OR_PI / 3.0, 1.0 / 3.0) * (ma + mb) / dens * vrel;
+  double s = fmin(sv, scap);
+  double cx = or_nanbu_cos(s, U[0]);
+  double sx = sqrt(fmax(0.0, 1.0 - cx * cx));
+  double phi = 2.0 * OR_PI * U[1];
+  double u[3] = {pst[0] / pm, pst[1] / pm, pst[2] / pm}, e1[3], e2v[3];
+  if (fabs(u[2]) < 0.9) {
+    double n = sqrt(u[0] * u[0] + u[1] * u[1]);
+    e1[0] = u[1] / n;
+    e1[1] = -u[0] / n;
+    e1[2] = 0.0;
+  } else {
+    double n = sqrt(u[1] * u[1] + u[2] * u[2]);
+    e1[0] = 0.0;
+    e1[1] = u[2] / n;
+    e1[2] = -u[1] / n;
+  }
+  e2v[0] = u[1] * e1[2] - u[2] * e1[1];
+  e2v[1] = u[2] * e1[0] - u[0] * e1[2];
+  e2v[2] = u[0] * e1[1] - u[1] * e1[0];
+  double cp = cos(phi), sp = sin(phi), pn[3];
+  for (int d = 0; d < 3; d++) pn[d] = pm * (cx * u[d] + sx * (cp * e1[d] + sp * e2v[d]));
+  /* back to the lab frame; b takes -pn in the centre-of-mass frame */
+  double vpa = vc[0] * pn[0] + vc[1] * pn[1] + vc[2] * pn[2];
+  double wmax = fmax(wa, wb);
+  if (U[2] * wmax < wb)
+    for (int d = 0; d < 3; d++) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) / ma;
+  if (U[3] * wmax < wa)
+    for (int d = 0; d < 3; d++) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) / mb;
+  return s;
+}
+
+typedef struct {
+  uint32_t key;
+  uint64_t id;
+  long p;
+} coll_item;
+
+static int cmp_coll(const void *x, const void *y) {
+  const coll_item *a = x, *b = y;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->id < b->id ? -1 : (a->id > b->id ? 1 : 0);
+}
+
+/* One collision pass: in every cell, electrons and holes each in the random
+ * order of their keys (Philox (step, id) stream 5); like-species pairs
+ * (0,1),(2,3),... with an odd count's first three colliding pairwise at half
+ * strength (Takizuka & Abe); then unlike pairs (A_i, B_{i mod |B|}) with A
+ * the larger group.  Pair q of the cell (in that order) draws Philox
+ * (step, cell, q) stream 6. */
+void or_collide_pass(or_sim *s) {
+  if (s->cfg.coll_every <= 0 || (s->step + 1) % s->cfg.coll_every != 0) return;
+  const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
+  const long ncell = (long)nx * ny * nz;
+  const double dtc = s->dt * s->cfg.coll_every;
+  long *cnt = calloc(ncell + 1, sizeof(long));
+  for (long p = 0; p < s->np; p++) cnt[s->pcell[p] + 1]++;
+  for (long c = 0; c < ncell; c++) cnt[c + 1] += cnt[c];
+  long *pos = malloc(ncell * sizeof(long)), *idx = malloc((s->np ? s->np : 1) * sizeof(long));
+  for (long c = 0; c < ncell; c++) pos[c] = cnt[c];
+  for (long p = 0; p < s->np; p++) idx[pos[s->pcell[p]]++] = p;
+  for (long c = 0; c < ncell; c++) {
+    long n = cnt[c + 1] - cnt[c];
+    if (n < 2) continue;
+    coll_item *grp[2];
+    long gn[2] = {0, 0};
+    grp[0] = malloc(n * sizeof(coll_item));
+    grp[1] = malloc(n * sizeof(coll_item));
+    double dens[2] = {0, 0}, wsum[2] = {0, 0}, vm[2][3] = {{0, 0, 0}, {0, 0, 0}}, T[2] = {0, 0};
+    for (long q = cnt[c]; q < cnt[c + 1]; q++) {
+      long p = idx[q];
+      int sp = (int)(s->ptag[p] & 1u), L = (int)(s->ptag[p] >> 1);
+      uint32_t r[4];
+      philox_draw(s->cfg.seed, (uint32_t)s->step, (uint32_t)s->pid[p],
+                  (uint32_t)(s->pid[p] >> 32), OR_STREAM_COLL_ORDER, r);
+      grp[sp][gn[sp]].key = r[0];
+      grp[sp][gn[sp]].id = s->pid[p];
+      grp[sp][gn[sp]].p = p;
+      gn[sp]++;
+      double w = s->wmac[L];
+      const double *u = &s->pu[3 * p];
+      double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (OR_C * OR_C));
+      wsum[sp] += w;
+      for (int d = 0; d < 3; d++) vm[sp][d] += w * u[d] / g;
+    }
+    for (int sp = 0; sp < 2; sp++) {
+      qsort(grp[sp], gn[sp], sizeof(coll_item), cmp_coll);
+      dens[sp] = wsum[sp] / s->V;
+      if (wsum[sp] > 0.0)
+        for (int d = 0; d < 3; d++) vm[sp][d] /= wsum[sp];
+    }
+    /* kinetic temperatures from the velocity variance about the mean */
+    for (long q = cnt[c]; q < cnt[c + 1]; q++) {
+      long p = idx[q];
+      int sp = (int)(s->ptag[p] & 1u), L = (int)(s->ptag[p] >> 1);
+      const double *u = &s->pu[3 * p];
+      double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (OR_C * OR_C));
+      double dv2 = 0.0;
+      for (int d = 0; d < 3; d++) {
+        double dv = u[d] / g - vm[sp][d];
+        dv2 += dv * dv;
+      }
+      T[sp] += s->wmac[L] * s->mass[L][sp] * dv2;
+    }
+    double inv_l2 = 0.0;
+    for (int sp = 0; sp < 2; sp++) {
+      if (wsum[sp] > 0.0) T[sp] /= 3.0 * wsum[sp];
+      if (T[sp] > 0.0) inv_l2 += dens[sp] * OR_QE * OR_QE / (OR_EPS0 * T[sp]);
+    }
+    /* screening no shorter than the interparticle spacing of the holes (the
+     * ions), or of the electrons in a cell without holes */
+    double ni = dens[1] > 0.0 ? dens[1] : dens[0];
+    double ra = pow(4.0 * OR_PI * ni / 3.0, -1.0 / 3.0);
+    double lD = inv_l2 > 0.0 ? fmax(1.0 / sqrt(inv_l2), ra) : ra;
+    uint32_t q = 0;
+    /* like-species pairs */
+    for (int sp = 0; sp < 2; sp++) {
+      long m = gn[sp];
+      if (m < 2) continue;
+      long start = 0;
+      if (m % 2 == 1) {
+        const long tri[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int t = 0; t < 3; t++) {
+          long pa = grp[sp][tri[t][0]].p, pb = grp[sp][tri[t][1]].p;
+          int La = (int)(s->ptag[pa] >> 1), Lb = (int)(s->ptag[pb] >> 1);
+          uint32_t r[4];
+          philox_draw(s->cfg.seed, (uint32_t)s->step, (uint32_t)c, q++, OR_STREAM_COLL_PAIR, r);
+          double U[4] = {u01(r[0]), u01(r[1]), u01(r[2]), u01(r[3])};
+          or_collide_pair(&s->pu[3 * pa], &s->pu[3 * pb], s->mass[La][sp], s->mass[Lb][sp],
+                          s->wmac[La], s->wmac[Lb], 0.5 * dens[sp], dens[sp], dens[sp], lD, dtc, U);
+        }
+        start = 3;
+      }
+      for (long i = start; i + 1 < m; i += 2) {
+        long pa = grp[sp][i].p, pb = grp[sp][i + 1].p;
+        int La = (int)(s->ptag[pa] >> 1), Lb = (int)(s->ptag[pb] >> 1);
+        uint32_t r[4];
+        philox_draw(s->cfg.seed, (uint32_t)s->step, (uint32_t)c, q++, OR_STREAM_COLL_PAIR, r);
+        double U[4] = {u01(r[0]), u01(r[1]), u01(r[2]), u01(r[3])};
+        or_collide_pair(&s->pu[3 * pa], &s->pu[3 * pb], s->mass[La][sp], s->mass[Lb][sp],
+                        s->wmac[La], s->wmac[Lb], dens[sp], dens[sp], dens[sp], lD, dtc, U);
+      }
+    }
+    /* unlike pairs: every particle of the larger group once */
+    if (gn[0] > 0 && gn[1] > 0) {
+      int A = gn[0] >= gn[1] ? 0 : 1, B = 1 - A;
+      double nab = 0.0;
+      for (long i = 0; i < gn[A]; i++) {
+        long pa = grp[A][i].p, pb = grp[B][i % gn[B]].p;
+        nab += fmin(s->wmac[s->ptag[pa] >> 1], s->wmac[s->ptag[pb] >> 1]) / s->V;
+      }
+      double neff = dens[0] * dens[1] / nab;
+      for (long i = 0; i < gn[A]; i++) {
+        /* (electron, hole) order inside the pair */
+        long pA = grp[A][i].p, pB = grp[B][i % gn[B]].p;
+        long pe = A == 0 ? pA : pB, ph = A == 0 ? pB : pA;
+        int Le = (int)(s->ptag[pe] >> 1), Lh = (int)(s->ptag[ph] >> 1);
+        uint32_t r[4];
+        philox_draw(s->cfg.seed, (uint32_t)s->step, (uint32_t)c, q++, OR_STREAM_COLL_PAIR, r);
+        double U[4] = {u01(r[0]), u01(r[1]), u01(r[2]), u01(r[3])};
+        or_collide_pair(&s->pu[3 * pe], &s->pu[3 * ph], s->mass[Le][0], s->mass[Lh][1],
+                        s->wmac[Le], s->wmac[Lh], neff, dens[0], dens[1], lD, dtc, U);
+      }
+    }
+    free(grp[0]);
+    free(grp[1]);
+  }
+  free(cnt);
+  free(pos);
+  free(idx);
+}
+
+/* Phases of one step: 1 particle, 32 collisions, 2 field, 4 window + Keldysh,
+ * 8 ionisation, 16 advance the step counter.  A full step is 63. */
 void or_step_phases(or_sim *s, int mask) {
   if (mask & 1) or_particle_pass(s);
+  if (mask & 32) or_collide_pass(s);
   if (mask & 2) or_field_pass(s);
   if (mask & 4) or_window_keldysh_pass(s);
   if (mask & 8) or_ionize_pass(s);
@@ -884,7 +1145,7 @@ void or_step_phases(or_sim *s, int mask) {
 }
 
 void or_step(or_sim *s, int n) {
-  for (int q = 0; q < n; q++) or_step_phases(s, 31);
+  for (int q = 0; q < n; q++) or_step_phases(s, 63);
 }
 
 /* ------------------------------------------------------------------------ */
