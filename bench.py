@@ -199,6 +199,7 @@ ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
     "window": ("material cell", 48.0),
     "ionize": ("material cell", 16.0),
     "sort": ("particle", 80.0),
+    "collide": ("particle", 36.0),  # momentum read + write 24, tag 4, id 8
 }
 
 
@@ -211,6 +212,8 @@ def run_native(args, rank, local, world, dist):
     cfg["seed"] = cfg["seed"] + 7919 * rank  # independent replica per rank
     if args.pool_factor is not None:
         cfg["pool_factor"] = args.pool_factor
+    if args.coll_every:
+        cfg["coll_every"] = args.coll_every
     sim = pic.Simulation(cfg)
     st = sim.static
     sim.step(args.prerun + args.warmup)
@@ -251,7 +254,7 @@ def run_native(args, rank, local, world, dist):
     unit_name, per_unit = ALG_BYTES.get(dom, ("step", 0.0))
     if dom == "push":
         units = psteps / max(dom_n, 1)
-    elif dom == "sort":
+    elif dom in ("sort", "collide"):
         units = (i1["n_particles"] + i0["n_particles"]) / 2
     elif unit_name == "field point":
         units = st["nfield"]
@@ -284,6 +287,7 @@ def run_native(args, rank, local, world, dist):
         "data": "synthetic",
         "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
                    "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
+                   "collisions_every": args.coll_every,
                    "l2": "state larger than L2 (%.1f GB), no flush" % (st["arena_bytes"] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "cell_updates_per_s": cells_all / t,
@@ -465,6 +469,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coll-every", type=int, default=0,
+                    help="binary-collision pass every N steps (0: none, as the workload defines)")
     ap.add_argument("--workload", choices=["silica", "scan", "serve"], default="silica")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--scan-instances", type=int, default=64)

@@ -54,6 +54,8 @@ extern "C" {
 #define PIC_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define PIC_ECUDA (-5)    /* any CUDA runtime error */
 #define PIC_ESTATE (-6)   /* call not valid in the handle's current state */
+#define PIC_ECOLL (-7)    /* a cell held more charged particles than a collision
+                             pass handles (128) */
 
 #define PIC_FP64 0
 #define PIC_FP32 1
@@ -65,7 +67,9 @@ extern "C" {
 #define PIC_PHASE_WINDOW 4    /* |E| window and Keldysh threshold per cell */
 #define PIC_PHASE_IONIZE 8    /* ionisation draws and pair creation */
 #define PIC_PHASE_ADVANCE 16  /* step counter += 1 */
-#define PIC_PHASE_ALL 31
+#define PIC_PHASE_COLLIDE 32  /* binary collisions (when coll_every divides step + 1);
+                                 runs after the particles, before the fields */
+#define PIC_PHASE_ALL 63
 
 typedef struct pic_ctx *pic_handle;
 
@@ -81,7 +85,8 @@ typedef struct {
   int sort_interval;   /* steps between cell sorts of the pool (0: 16) */
   int imax_every;      /* steps between records of the intensity map (Sec. 5
                           records every 0.5 fs): 0 = round(0.5 fs / dt), < 0 off */
-  int reserved;
+  int coll_every;      /* steps between binary-collision passes among electrons
+                          and holes (Sec. 2.2), each over coll_every * dt; 0 = none */
 } pic_grid;
 
 /* One dielectric layer: z cells [z0, z1) over the whole transverse plane.
@@ -153,7 +158,8 @@ typedef struct {
 #define PIC_PROF_IONIZE 4  /* ionisation draws + pair appends */
 #define PIC_PROF_SORT 5    /* pool sort (all its kernels) */
 #define PIC_PROF_OTHER 6   /* step counter */
-#define PIC_PROF_N 7
+#define PIC_PROF_COLLIDE 7 /* binary collisions (their sort included) */
+#define PIC_PROF_N 8
 
 /* FP64 diagnostics (Sec. 4.1 number density, Sec. 4.2 energy density,
  * Sec. 4.3 spectra).  Inputs: n_bins, e_min_eV, e_max_eV, region, spectrum;

@@ -1029,7 +1029,7 @@ void or_collide_pass(or_sim *s) {
     long gn[2] = {0, 0};
     grp[0] = malloc(n * sizeof(coll_item));
     grp[1] = malloc(n * sizeof(coll_item));
-    double dens[2] = {0, 0}, wsum[2] = {0, 0}, vm[2][3] = {{0, 0, 0}, {0, 0, 0}}, T[2] = {0, 0};
+    double dens[2] = {0, 0}, wsum[2] = {0, 0}, wm[2] = {0, 0}, T[2] = {0, 0};
     for (long q = cnt[c]; q < cnt[c + 1]; q++) {
       long p = idx[q];
       int sp = (int)(s->ptag[p] & 1u), L = (int)(s->ptag[p] >> 1);
@@ -1040,36 +1040,36 @@ void or_collide_pass(or_sim *s) {
       grp[sp][gn[sp]].id = s->pid[p];
       grp[sp][gn[sp]].p = p;
       gn[sp]++;
-      double w = s->wmac[L];
-      const double *u = &s->pu[3 * p];
-      double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (OR_C * OR_C));
-      wsum[sp] += w;
-      for (int d = 0; d < 3; d++) vm[sp][d] += w * u[d] / g;
+      wsum[sp] += s->wmac[L];
+      wm[sp] += s->wmac[L] * s->mass[L][sp];
     }
     for (int sp = 0; sp < 2; sp++) {
       qsort(grp[sp], gn[sp], sizeof(coll_item), cmp_coll);
       dens[sp] = wsum[sp] / s->V;
-      if (wsum[sp] > 0.0)
-        for (int d = 0; d < 3; d++) vm[sp][d] /= wsum[sp];
     }
-    /* kinetic temperatures from the velocity variance about the mean */
-    for (long q = cnt[c]; q < cnt[c + 1]; q++) {
-      long p = idx[q];
-      int sp = (int)(s->ptag[p] & 1u), L = (int)(s->ptag[p] >> 1);
-      const double *u = &s->pu[3 * p];
-      double g = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (OR_C * OR_C));
-      double dv2 = 0.0;
-      for (int d = 0; d < 3; d++) {
-        double dv = u[d] / g - vm[sp][d];
-        dv2 += dv * dv;
-      }
-      T[sp] += s->wmac[L] * s->mass[L][sp] * dv2;
+    /* kinetic temperature of each group: mean mass times the weighted
+     * velocity variance, written as a sum over pairs so that it is exactly 0
+     * for one particle or equal velocities (no cancellation) */
+    for (int sp = 0; sp < 2; sp++) {
+      double S = 0.0;
+      for (long i = 0; i < gn[sp]; i++)
+        for (long j = i + 1; j < gn[sp]; j++) {
+          long pi = grp[sp][i].p, pj = grp[sp][j].p;
+          const double *ui = &s->pu[3 * pi], *uj = &s->pu[3 * pj];
+          double gi = sqrt(1.0 + (ui[0] * ui[0] + ui[1] * ui[1] + ui[2] * ui[2]) / (OR_C * OR_C));
+          double gj = sqrt(1.0 + (uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]) / (OR_C * OR_C));
+          double dv2 = 0.0;
+          for (int d = 0; d < 3; d++) {
+            double dv = ui[d] / gi - uj[d] / gj;
+            dv2 += dv * dv;
+          }
+          S += s->wmac[s->ptag[pi] >> 1] * s->wmac[s->ptag[pj] >> 1] * dv2;
+        }
+      if (wsum[sp] > 0.0) T[sp] = wm[sp] / wsum[sp] * S / (3.0 * wsum[sp] * wsum[sp]);
     }
     double inv_l2 = 0.0;
-    for (int sp = 0; sp < 2; sp++) {
-      if (wsum[sp] > 0.0) T[sp] /= 3.0 * wsum[sp];
+    for (int sp = 0; sp < 2; sp++)
       if (T[sp] > 0.0) inv_l2 += dens[sp] * OR_QE * OR_QE / (OR_EPS0 * T[sp]);
-    }
     /* screening no shorter than the interparticle spacing of the holes (the
      * ions), or of the electrons in a cell without holes */
     double ni = dens[1] > 0.0 ? dens[1] : dens[0];

@@ -72,7 +72,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   if (g.precision != PIC_FP64 && g.precision != PIC_FP32)
     return fail(PIC_EINVAL, "unknown precision");
   if (!(g.pool_factor >= 0)) return fail(PIC_EINVAL, "pool_factor must be >= 0");
-  if (g.keldysh_terms < 0 || g.sort_interval < 0) return fail(PIC_EINVAL, "negative count");
+  if (g.keldysh_terms < 0 || g.sort_interval < 0 || g.coll_every < 0)
+    return fail(PIC_EINVAL, "negative count");
   if (mat->n_layers < 0 || mat->n_layers > PIC_MAX_LAYERS || (mat->n_layers && !mat->layers))
     return fail(PIC_EINVAL, "bad layer count");
   if (!(pulse->lambda > 0 && pulse->fwhm > 0 && pulse->fluence >= 0) ||
@@ -459,6 +460,16 @@ int enqueue(pic_ctx *h, int mask) {
     prof_end(h);
     h->launches += 1;
   }
+  if ((mask & PIC_PHASE_COLLIDE) && P.g.coll_every > 0 && (h->step + 1) % P.g.coll_every == 0) {
+    // pairs are formed per cell: the pool is sorted first (cell ends in cnt)
+    const int rc = sort_pool<R>(h);
+    if (rc) return rc;
+    prof_begin(h, PIC_PROF_COLLIDE);
+    k_collide<R><<<(unsigned)((P.ncell + kCollWarps - 1) / kCollWarps), 32 * kCollWarps, 0, s>>>(
+        X, (const unsigned int *)(h->arena + P.off_cnt), P.dt * P.g.coll_every);
+    prof_end(h);
+    h->launches += 1;
+  }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
     if constexpr (sizeof(R) == 4) {
@@ -558,8 +569,11 @@ int check_sticky(pic_ctx *h) {
   h->d2h_bytes += (long long)sizeof(int);
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   if (e & kErrPool) h->sticky = PIC_EPOOL;
+  if (e & kErrColl) h->sticky = PIC_ECOLL;
   if (h->sticky == PIC_EPOOL)
     return fail(PIC_EPOOL, "ionisation outgrew the charged-particle pool (raise pool_factor)");
+  if (h->sticky == PIC_ECOLL)
+    return fail(PIC_ECOLL, "a cell held more charged particles than a collision pass handles");
   return PIC_OK;
 }
 
@@ -776,8 +790,14 @@ int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *
       delete b;
       return fail(PIC_ESTATE, "a batch member is profiling");
     }
+    // the host schedule (pool sorts, collision passes) and the parity of the
+    // double-buffered pool repeat after lcm(2 sort_interval, 2 coll_every)
     const long long p2 = 2ll * h->P.g.sort_interval;
     per = per / gcd_ll(per, p2) * p2;
+    if (h->P.g.coll_every > 0) {
+      const long long p3 = 2ll * h->P.g.coll_every;
+      per = per / gcd_ll(per, p3) * p3;
+    }
     b->m.push_back(h);
   }
   if (per > 4096) {

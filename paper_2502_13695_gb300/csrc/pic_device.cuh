@@ -17,8 +17,15 @@ constexpr double kHbar = 1.054571817e-34;
 constexpr double kAmu = 1.66053906660e-27;
 constexpr double kPi = 3.14159265358979323846;
 
-enum : uint32_t { kStreamPos = 1u, kStreamVel = 2u, kStreamIon = 3u, kStreamIonLow = 4u };
-enum : int { kErrPool = 1, kErrBadCell = 2 };
+enum : uint32_t {
+  kStreamPos = 1u,
+  kStreamVel = 2u,
+  kStreamIon = 3u,
+  kStreamIonLow = 4u,
+  kStreamCollOrder = 5u,
+  kStreamCollPair = 6u
+};
+enum : int { kErrPool = 1, kErrBadCell = 2, kErrColl = 4 };
 
 // Per-layer constants, prepared on the host in double precision.
 struct LayerK {

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
     stv<V>(D.B[1] + o, b);
     if constexpr (kRecord) {
       const int every = D.imax_every;
-      if (every > 0 && (*D.step + 1) % every == 0) {
+      if (every > 0 && ((unsigned)*D.step + 1u) % (unsigned)every == 0u) {
         // cell-centred |E|: mean of the four edge values of each component
         const long long ojv = (i + V == nx) ? oj + V - nx : oj + V;
         R exjk[V], a2[V], im[V];
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
     // sliding maximum: slots <= s hold this block's samples, slots > s the
     // suffix maxima of the previous block; pm is the running block prefix max
     const int NW = D.NW;
-    const int s = (int)(*D.step % NW);
+    const int s = (int)((unsigned)*D.step % (unsigned)NW);
     R *__restrict__ W = D.win + m;
     const long long st = D.nmat;
     stv<V>(W + s * st, a);
@@ -1263,6 +1263,291 @@ __global__ void __launch_bounds__(256) k_diag_grid(Ctx<R> X, const double *ne, c
     p[2] = v2;
     p[3] = v3;
     p[4] = v4;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Binary collisions among electrons and holes (Sec. 2.2).  Nanbu's
+// cumulative small-angle scattering (Phys. Rev. E 55, 4642, 1997) in the
+// relativistic centre-of-mass frame of Perez et al. (Phys. Plasmas 19,
+// 083104, 2012), Coulomb logarithm bounded below by 1 (Sec. 2.2), screening
+// no shorter than the interparticle spacing and the low-temperature cap on
+// the collision parameter.  One warp per cell of the cell-sorted pool; the
+// per-pair arithmetic is double in both precisions (e^4 / (eps0^2 c^4 m^2)
+// is below the float range).
+// ---------------------------------------------------------------------------
+constexpr int kCollMax = 128;  // charged particles per cell a pass handles
+constexpr int kCollWarps = 4;  // cells per block
+
+// Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s) (bisection in
+// log A).
+__device__ double nanbu_A(double s) {
+  const double target = exp(-s);
+  double lo = 1e-12, hi = 1e12;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = sqrt(lo * hi);
+    const double g =
+        mid < 1e-4 ? mid / 3.0 - mid * mid * mid / 45.0 : 1.0 / tanh(mid) - 1.0 / mid;
+    if (g < target)
+      lo = mid;
+    else
+      hi = mid;
+    if (hi / lo < 1.0 + 4e-16) break;
+  }
+  return sqrt(lo * hi);
+}
+
+// cos chi for parameter s and uniform U: 1 + s ln U for s < 0.1, isotropic
+// for s >= 6, otherwise the inverse of A exp(A cos chi) / (2 sinh A).
+__device__ double nanbu_cos(double s, double U) {
+  double c;
+  if (s < 0.1) {
+    c = 1.0 + s * log(U);
+  } else if (s < 6.0) {
+    const double A = nanbu_A(s);
+    c = log(exp(-A) + 2.0 * U * sinh(A)) / A;
+  } else {
+    c = 2.0 * U - 1.0;
+  }
+  return fmin(1.0, fmax(-1.0, c));
+}
+
+// One collision of a and b (u = gamma v per unit mass, masses m, weights w):
+// centre-of-mass momentum rotated by (chi, phi), then back to the lab frame;
+// each side moves with probability w_other / max(w_a, w_b).
+__device__ void collide_pair(double ua[3], double ub[3], double ma, double mb, double wa,
+                             double wb, double neff, double na, double nb, double lD, double dtc,
+                             const double U[4]) {
+  const double c2 = kC * kC;
+  const double ga = sqrt(1.0 + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]) / c2);
+  const double gb = sqrt(1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]) / c2);
+  const double Et = ma * ga + mb * gb;
+  double vc[3], va[3], vb[3], pa[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    pa[d] = ma * ua[d];
+    va[d] = ua[d] / ga;
+    vb[d] = ub[d] / gb;
+    vc[d] = (pa[d] + mb * ub[d]) / Et;
+  }
+  const double vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
+  const double gc = 1.0 / sqrt(1.0 - vc2 / c2);
+  const double kc = gc * gc / (c2 * (gc + 1.0));  // (gamma_c - 1) / v_c^2
+  const double vcva = vc[0] * va[0] + vc[1] * va[1] + vc[2] * va[2];
+  const double vcvb = vc[0] * vb[0] + vc[1] * vb[1] + vc[2] * vb[2];
+  double ps[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ps[d] = pa[d] + (kc * vcva - gc) * ma * ga * vc[d];
+  const double gsa = (1.0 - vcva / c2) * gc * ga, gsb = (1.0 - vcvb / c2) * gc * gb;
+  const double p2 = ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2];
+  const double pm = sqrt(p2);
+  if (!(pm > 0.0)) return;
+  const double e2 = kQe * kQe;
+  const double mm = ma * gsa * mb * gsb * c2 / p2 + 1.0;
+  const double b0 = e2 / (4.0 * kPi * kEps0 * c2) * gc / Et * mm;
+  const double bmin = fmax(2.0 * kPi * kHbar / (2.0 * pm), b0);
+  const double lnL = fmax(1.0, 0.5 * log(1.0 + lD * lD / (bmin * bmin)));
+  const double sv = neff * dtc * lnL * e2 * e2 /
+                    (4.0 * kPi * kEps0 * kEps0 * c2 * c2 * ma * ga * mb * gb) * gc * pm / Et *
+                    mm * mm;
+  const double vrel = Et * pm / (ma * gsa * mb * gsb * gc);
+  const double dens = fmax(ma * pow(na, 2.0 / 3.0), mb * pow(nb, 2.0 / 3.0));
+  const double scap = neff * dtc * pow(4.0 * kPi / 3.0, 1.0 / 3.0) * (ma + mb) / dens * vrel;
+  const double s = fmin(sv, scap);
+  const double cx = nanbu_cos(s, U[0]);
+  const double sx = sqrt(fmax(0.0, 1.0 - cx * cx));
+  const double phi = 2.0 * kPi * U[1];
+  const double u[3] = {ps[0] / pm, ps[1] / pm, ps[2] / pm};
+  double e1[3], e2v[3];
+  if (fabs(u[2]) < 0.9) {
+    const double n = sqrt(u[0] * u[0] + u[1] * u[1]);
+    e1[0] = u[1] / n;
+    e1[1] = -u[0] / n;
+    e1[2] = 0.0;
+  } else {
+    const double n = sqrt(u[1] * u[1] + u[2] * u[2]);
+    e1[0] = 0.0;
+    e1[1] = u[2] / n;
+    e1[2] = -u[1] / n;
+  }
+  e2v[0] = u[1] * e1[2] - u[2] * e1[1];
+  e2v[1] = u[2] * e1[0] - u[0] * e1[2];
+  e2v[2] = u[0] * e1[1] - u[1] * e1[0];
+  const double cp = cos(phi), sp = sin(phi);
+  double pn[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) pn[d] = pm * (cx * u[d] + sx * (cp * e1[d] + sp * e2v[d]));
+  const double vpa = vc[0] * pn[0] + vc[1] * pn[1] + vc[2] * pn[2];
+  const double wmax = fmax(wa, wb);
+  if (U[2] * wmax < wb) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) / ma;
+  }
+  if (U[3] * wmax < wa) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) / mb;
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Pair q of cell c: both particles read from and written back to the pool.
+template <class R>
+__device__ void collide_slots(const Dev<R> &D, unsigned long long pa, unsigned long long pb,
+                              uint32_t step, uint32_t c, uint32_t q, double neff, double na,
+                              double nb, double lD, double dtc) {
+  const uint32_t ta = D.ptag[pa], tb = D.ptag[pb];
+  const LayerK &La = D.layers[ta >> 1], &Lb = D.layers[tb >> 1];
+  double ua[3], ub[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ua[d] = (double)D.pu[d][pa];
+    ub[d] = (double)D.pu[d][pb];
+  }
+  const uint4 w = draw(D.seed, step, c, q, kStreamCollPair);
+  const double U[4] = {unit_open<double>(w.x), unit_open<double>(w.y), unit_open<double>(w.z),
+                       unit_open<double>(w.w)};
+  collide_pair(ua, ub, La.mass[ta & 1u], Lb.mass[tb & 1u], La.wmac, Lb.wmac, neff, na, nb, lD,
+               dtc, U);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    D.pu[d][pa] = R(ua[d]);
+    D.pu[d][pb] = R(ub[d]);
+  }
+}
+
+// One warp per cell: electrons and holes each ordered by a Philox key of
+// their id; like pairs (0,1), (2,3), ... (an odd count's first three collide
+// pairwise at half strength), then unlike pairs (A_i, B_{i mod |B|}) in
+// rounds of |B| disjoint pairs.  Pair q (in that order) draws Philox
+// (step, cell, q) stream 6.  cend[c] is the end of cell c in the sorted pool.
+template <class R>
+__global__ void __launch_bounds__(32 * kCollWarps) k_collide(Ctx<R> X, const unsigned int *cend,
+                                                              double dtc) {
+  __shared__ uint32_t skey[kCollWarps][kCollMax];
+  __shared__ unsigned long long sid[kCollWarps][kCollMax];
+  __shared__ uint8_t ssp[kCollWarps][kCollMax];
+  __shared__ short sord[kCollWarps][2][kCollMax];
+  const Dev<R> &D = X.d;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c = (long long)blockIdx.x * kCollWarps + wp;
+  if (c >= D.ncell) return;
+  const unsigned int st = c ? cend[c - 1] : 0u, en = cend[c];
+  const int n = (int)(en - st);
+  if (n < 2) return;
+  if (n > kCollMax) {
+    if (lane == 0) atomicOr(D.err, kErrColl);
+    return;
+  }
+  const uint32_t step = (uint32_t)*D.step;
+  int cnt[2] = {0, 0};
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    uint8_t sp = 2;
+    if (i < n) {
+      const unsigned long long p = st + i;
+      const unsigned long long id = D.pid[p];
+      sid[wp][i] = id;
+      skey[wp][i] = draw(D.seed, step, (uint32_t)id, (uint32_t)(id >> 32), kStreamCollOrder).x;
+      sp = (uint8_t)(D.ptag[p] & 1u);
+      ssp[wp][i] = sp;
+    }
+    cnt[0] += __popc(__ballot_sync(0xffffffffu, sp == 0));
+    cnt[1] += __popc(__ballot_sync(0xffffffffu, sp == 1));
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const uint32_t ki = skey[wp][i];
+    const unsigned long long idi = sid[wp][i];
+    const uint8_t si = ssp[wp][i];
+    int r = 0;
+    for (int j = 0; j < n; ++j)
+      if (ssp[wp][j] == si && (skey[wp][j] < ki || (skey[wp][j] == ki && sid[wp][j] < idi))) ++r;
+    sord[wp][si][r] = (short)i;
+  }
+  __syncwarp();
+  // densities and kinetic temperatures of the two groups: mean mass times
+  // the weighted velocity variance, written as a sum over pairs (exactly 0
+  // for one particle or equal velocities, no cancellation)
+  double ws[2] = {0.0, 0.0}, wm[2] = {0.0, 0.0}, S[2] = {0.0, 0.0};
+  for (int i = lane; i < n; i += 32) {
+    const unsigned long long pi = st + i;
+    const uint32_t ti = D.ptag[pi];
+    const int sp = ti & 1u;
+    const LayerK &Li = D.layers[ti >> 1];
+    ws[sp] += Li.wmac;
+    wm[sp] += Li.wmac * Li.mass[sp];
+    const double a0 = D.pu[0][pi], a1 = D.pu[1][pi], a2 = D.pu[2][pi];
+    const double gi = sqrt(1.0 + (a0 * a0 + a1 * a1 + a2 * a2) / (kC * kC));
+    for (int j = i + 1; j < n; ++j) {
+      if (ssp[wp][j] != sp) continue;
+      const unsigned long long pj = st + j;
+      const double b0 = D.pu[0][pj], b1 = D.pu[1][pj], b2 = D.pu[2][pj];
+      const double gj = sqrt(1.0 + (b0 * b0 + b1 * b1 + b2 * b2) / (kC * kC));
+      const double d0 = a0 / gi - b0 / gj, d1 = a1 / gi - b1 / gj, d2 = a2 / gi - b2 / gj;
+      S[sp] += Li.wmac * D.layers[D.ptag[pj] >> 1].wmac * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+  }
+  double T[2];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    ws[sp] = warp_sum_d(ws[sp]);
+    wm[sp] = warp_sum_d(wm[sp]);
+    S[sp] = warp_sum_d(S[sp]);
+    T[sp] = ws[sp] > 0.0 ? wm[sp] / ws[sp] * S[sp] / (3.0 * ws[sp] * ws[sp]) : 0.0;
+  }
+  const double V = D.V_d;
+  double dens[2], inv_l2 = 0.0;
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    dens[sp] = ws[sp] / V;
+    if (T[sp] > 0.0) inv_l2 += dens[sp] * kQe * kQe / (kEps0 * T[sp]);
+  }
+  const double ni = dens[1] > 0.0 ? dens[1] : dens[0];
+  const double ra = pow(4.0 * kPi * ni / 3.0, -1.0 / 3.0);
+  const double lD = inv_l2 > 0.0 ? fmax(1.0 / sqrt(inv_l2), ra) : ra;
+  uint32_t qb = 0;
+  // like pairs
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const int m = cnt[sp];
+    if (m < 2) continue;
+    const short *ord = sord[wp][sp];
+    const int start = (m & 1) ? 3 : 0;
+    if ((m & 1) && lane == 0) {
+      const int tri[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+      for (int t = 0; t < 3; ++t)
+        collide_slots(D, st + ord[tri[t][0]], st + ord[tri[t][1]], step, (uint32_t)c, qb + t,
+                      0.5 * dens[sp], dens[sp], dens[sp], lD, dtc);
+    }
+    for (int k = lane; start + 2 * k + 1 < m; k += 32)
+      collide_slots(D, st + ord[start + 2 * k], st + ord[start + 2 * k + 1], step, (uint32_t)c,
+                    qb + start + k, dens[sp], dens[sp], dens[sp], lD, dtc);
+    qb += (m & 1) ? 3 + (m - 3) / 2 : m / 2;
+    __syncwarp();
+  }
+  // unlike pairs: every particle of the larger group once
+  if (cnt[0] > 0 && cnt[1] > 0) {
+    const int A = cnt[0] >= cnt[1] ? 0 : 1, B = 1 - A;
+    const int nA = cnt[A], nB = cnt[B];
+    const short *oA = sord[wp][A], *oB = sord[wp][B];
+    double nab = 0.0;
+    for (int i = lane; i < nA; i += 32)
+      nab += fmin(D.layers[D.ptag[st + oA[i]] >> 1].wmac, D.layers[D.ptag[st + oB[i % nB]] >> 1].wmac) / V;
+    nab = warp_sum_d(nab);
+    const double neff = dens[0] * dens[1] / nab;
+    for (int r0 = 0; r0 < nA; r0 += nB) {
+      for (int i = r0 + lane; i < min(r0 + nB, nA); i += 32) {
+        const unsigned long long pA = st + oA[i], pB = st + oB[i % nB];
+        const unsigned long long pe = A == 0 ? pA : pB, ph = A == 0 ? pB : pA;
+        collide_slots(D, pe, ph, step, (uint32_t)c, qb + i, neff, dens[0], dens[1], lD, dtc);
+      }
+      __syncwarp();
+    }
   }
 }
 

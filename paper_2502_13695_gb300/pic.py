@@ -16,9 +16,11 @@ import numpy as np
 from . import build as _build
 
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_EPOOL, PIC_ETIMEOUT, PIC_ECUDA, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PIC_ECOLL = -7
 PIC_FP64, PIC_FP32 = 0, 1
 PHASE_PARTICLES, PHASE_FIELDS, PHASE_WINDOW, PHASE_IONIZE, PHASE_ADVANCE = 1, 2, 4, 8, 16
-PHASE_ALL = 31
+PHASE_COLLIDE = 32
+PHASE_ALL = 63
 MAX_LAYERS = 128
 EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_diagnostics", "pic_info_get", "pic_destroy", "pic_last_error",
@@ -27,7 +29,7 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
            "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
            "pic_damage", "pic_get_intensity_max"]
-PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other"]
+PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other", "collide"]
 
 
 class PicError(RuntimeError):
@@ -42,7 +44,7 @@ class Grid(ctypes.Structure):
                 ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("pool_factor", ctypes.c_double),
                 ("keldysh_terms", ctypes.c_int), ("sort_interval", ctypes.c_int),
-                ("imax_every", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int)]
 
 
 class Layer(ctypes.Structure):
@@ -157,6 +159,7 @@ def c_structs(cfg: dict):
     g.keldysh_terms = cfg.get("keldysh_terms", 500)
     g.sort_interval = cfg.get("sort_interval", 0)
     g.imax_every = cfg.get("imax_every", 0)
+    g.coll_every = cfg.get("coll_every", 0)
     layers = (Layer * max(1, len(cfg["layers"])))()
     for n, ly in enumerate(cfg["layers"]):
         L = layers[n]
