@@ -214,6 +214,8 @@ def run_native(args, rank, local, world, dist):
         cfg["pool_factor"] = args.pool_factor
     if args.coll_every:
         cfg["coll_every"] = args.coll_every
+    if args.sort_interval:
+        cfg["sort_interval"] = args.sort_interval
     sim = pic.Simulation(cfg)
     st = sim.static
     sim.step(args.prerun + args.warmup)
@@ -288,6 +290,7 @@ def run_native(args, rank, local, world, dist):
         "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
                    "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
                    "collisions_every": args.coll_every,
+                   "sort_interval": args.sort_interval or 16,
                    "l2": "state larger than L2 (%.1f GB), no flush" % (st["arena_bytes"] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "cell_updates_per_s": cells_all / t,
@@ -469,6 +472,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sort-interval", type=int, default=0,
+                    help="steps between pool sorts (0: the library default)")
     ap.add_argument("--coll-every", type=int, default=0,
                     help="binary-collision pass every N steps (0: none, as the workload defines)")
     ap.add_argument("--workload", choices=["silica", "scan", "serve"], default="silica")

@@ -55,6 +55,7 @@ struct Plan {
   size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
   size_t off_work, off_work_n, off_leave16;
   size_t off_imax, off_prof;
+  size_t off_clist, off_cn;  // collision cell list and its count / work counter
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
@@ -170,6 +171,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_leave16 = take(std::max<long long>(P.nmat, 1) * P.ppc_max * 2);
   P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
   P.off_imax = take(P.ncell * R);
+  P.off_clist = take(g.coll_every > 0 ? P.ncell * 4 : 4);
+  P.off_cn = take(16);
   P.off_prof = take((size_t)(2 * (g.nz + 1) + g.nz) * 8);
   P.off_work_n = take(16);
   P.off_cnt = take(P.ncell * 4);
@@ -293,6 +296,7 @@ struct pic_ctx {
   long long launches = 0;
   long long h2d_bytes = 0, d2h_bytes = 0;  // host <-> device bytes copied so far
   int push_blocks = 0;                      // resident blocks of k_push on this device
+  int coll_blocks = 0;                      // resident blocks of k_collide
   int field_v = 1;  // x points per thread of the field and window kernels
   // profiling: (class, start, stop) event triples, reused across reads
   bool profiling = false;
@@ -465,10 +469,20 @@ int enqueue(pic_ctx *h, int mask) {
     const int rc = sort_pool<R>(h);
     if (rc) return rc;
     prof_begin(h, PIC_PROF_COLLIDE);
-    k_collide<R><<<(unsigned)((P.ncell + kCollWarps - 1) / kCollWarps), 32 * kCollWarps, 0, s>>>(
-        X, (const unsigned int *)(h->arena + P.off_cnt), P.dt * P.g.coll_every);
+    CollConst K;
+    K.K1 = kQe * kQe * kQe * kQe / (4.0 * kPi * kEps0 * kEps0 * kC * kC * kC * kMe * kMe);
+    K.re = kQe * kQe / (4.0 * kPi * kEps0 * kMe * kC * kC);
+    K.lc = 2.0 * kPi * kHbar / (kMe * kC);
+    K.kD = 4.0 * kPi * K.re;
+    K.capc = std::cbrt(4.0 * kPi / 3.0) * kC;
+    const unsigned int *cend = (const unsigned int *)(h->arena + P.off_cnt);
+    int *clist = (int *)(h->arena + P.off_clist), *cn = (int *)(h->arena + P.off_cn);
+    PIC_CUDA(cudaMemsetAsync(cn, 0, 2 * sizeof(int), s));
+    k_coll_cells<<<grid_blocks(P.ncell), kThreads, 0, s>>>(cend, P.ncell, clist, cn);
+    k_collide<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, clist, cn, cn + 1, K,
+                                                            P.dt * P.g.coll_every);
     prof_end(h);
-    h->launches += 1;
+    h->launches += 2;
   }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
@@ -539,6 +553,8 @@ int init_state(pic_ctx *h) {
   PIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<R>, kThreads, 0));
   h->push_blocks = std::max(1, nsm) * std::max(1, per_sm);
+  PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide<R>, 32 * kCollWarps, 0));
+  h->coll_blocks = std::max(1, nsm) * std::max(1, per_sm);
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_mplane, P.mplane.data(), P.mplane.size() * sizeof(int),

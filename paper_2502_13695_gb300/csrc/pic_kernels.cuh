@@ -1272,57 +1272,84 @@ __global__ void __launch_bounds__(256) k_diag_grid(Ctx<R> X, const double *ne, c
 // relativistic centre-of-mass frame of Perez et al. (Phys. Plasmas 19,
 // 083104, 2012), Coulomb logarithm bounded below by 1 (Sec. 2.2), screening
 // no shorter than the interparticle spacing and the low-temperature cap on
-// the collision parameter.  One warp per cell of the cell-sorted pool; the
-// per-pair arithmetic is double in both precisions (e^4 / (eps0^2 c^4 m^2)
-// is below the float range).
+// the collision parameter.  One warp per cell of the cell-sorted pool.  The
+// arithmetic is in the working precision with momenta in units of m_e c and
+// masses in m_e (every float quantity then stays in range); the SI
+// prefactors come from the host in double.
 // ---------------------------------------------------------------------------
 constexpr int kCollMax = 128;  // charged particles per cell a pass handles
 constexpr int kCollWarps = 4;  // cells per block
 
+// SI constants of the normalised collision arithmetic (host-computed).
+struct CollConst {
+  double K1;    // e^4 / (4 pi eps0^2 c^3 m_e^2)            [m^3 / s]
+  double re;    // e^2 / (4 pi eps0 m_e c^2)                 [m]
+  double lc;    // h / (m_e c)                               [m]
+  double kD;    // e^2 / (eps0 m_e c^2) = 4 pi re            [m]
+  double capc;  // (4 pi / 3)^(1/3) c                         [m/s]
+};
+
+template <class R> struct CollTol;
+template <> struct CollTol<double> { static constexpr double v = 4e-16, small = 1e-4; };
+template <> struct CollTol<float> { static constexpr float v = 4e-7f, small = 0.5f; };
+
+// Langevin function coth A - 1/A (its series where the difference cancels).
+template <class R>
+__device__ __forceinline__ R langevin(R A) {
+  if (A < CollTol<R>::small) {
+    const R A2 = A * A;
+    if (sizeof(R) == 8) return A / R(3) - A * A2 / R(45);
+    return A * (R(1) / R(3) + A2 * (R(-1) / R(45) + A2 * (R(2) / R(945) +
+                A2 * (R(-1) / R(4725) + A2 * (R(2) / R(93555))))));
+  }
+  return R(1) / tanh(A) - R(1) / A;
+}
+
 // Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s) (bisection in
-// log A).
-__device__ double nanbu_A(double s) {
-  const double target = exp(-s);
-  double lo = 1e-12, hi = 1e12;
+// log A to the working precision).
+template <class R>
+__device__ R nanbu_A(R s) {
+  const R target = exp(-s);
+  R lo = R(1e-12), hi = R(1e12);
   for (int it = 0; it < 200; ++it) {
-    const double mid = sqrt(lo * hi);
-    const double g =
-        mid < 1e-4 ? mid / 3.0 - mid * mid * mid / 45.0 : 1.0 / tanh(mid) - 1.0 / mid;
-    if (g < target)
+    const R mid = sqrt(lo * hi);
+    if (langevin(mid) < target)
       lo = mid;
     else
       hi = mid;
-    if (hi / lo < 1.0 + 4e-16) break;
+    if (hi / lo < R(1) + CollTol<R>::v) break;
   }
   return sqrt(lo * hi);
 }
 
 // cos chi for parameter s and uniform U: 1 + s ln U for s < 0.1, isotropic
 // for s >= 6, otherwise the inverse of A exp(A cos chi) / (2 sinh A).
-__device__ double nanbu_cos(double s, double U) {
-  double c;
-  if (s < 0.1) {
-    c = 1.0 + s * log(U);
-  } else if (s < 6.0) {
-    const double A = nanbu_A(s);
-    c = log(exp(-A) + 2.0 * U * sinh(A)) / A;
+template <class R>
+__device__ R nanbu_cos(R s, R U) {
+  R c;
+  if (s < R(0.1)) {
+    c = R(1) + s * log(U);
+  } else if (s < R(6)) {
+    const R A = nanbu_A(s);
+    c = log(exp(-A) + R(2) * U * sinh(A)) / A;
   } else {
-    c = 2.0 * U - 1.0;
+    c = R(2) * U - R(1);
   }
-  return fmin(1.0, fmax(-1.0, c));
+  return fmin(R(1), fmax(R(-1), c));
 }
 
-// One collision of a and b (u = gamma v per unit mass, masses m, weights w):
-// centre-of-mass momentum rotated by (chi, phi), then back to the lab frame;
-// each side moves with probability w_other / max(w_a, w_b).
-__device__ void collide_pair(double ua[3], double ub[3], double ma, double mb, double wa,
-                             double wb, double neff, double na, double nb, double lD, double dtc,
-                             const double U[4]) {
-  const double c2 = kC * kC;
-  const double ga = sqrt(1.0 + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]) / c2);
-  const double gb = sqrt(1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]) / c2);
-  const double Et = ma * ga + mb * gb;
-  double vc[3], va[3], vb[3], pa[3];
+// One collision of a and b: normalised momenta u (units of c, u = gamma v),
+// masses m (units of m_e), weights w; centre-of-mass momentum rotated by
+// (chi, phi), then back to the lab frame; each side moves with probability
+// w_other / max(w_a, w_b).  nd = neff * dtc (density factor times the
+// collision interval); na, nb the group densities; lD the screening length.
+template <class R>
+__device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R na, R nb, R lD,
+                             const CollConst &K, const R U[4]) {
+  const R ga = sqrt(R(1) + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]));
+  const R gb = sqrt(R(1) + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]));
+  const R Et = ma * ga + mb * gb;
+  R vc[3], va[3], vb[3], pa[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     pa[d] = ma * ua[d];
@@ -1330,93 +1357,104 @@ __device__ void collide_pair(double ua[3], double ub[3], double ma, double mb, d
     vb[d] = ub[d] / gb;
     vc[d] = (pa[d] + mb * ub[d]) / Et;
   }
-  const double vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
-  const double gc = 1.0 / sqrt(1.0 - vc2 / c2);
-  const double kc = gc * gc / (c2 * (gc + 1.0));  // (gamma_c - 1) / v_c^2
-  const double vcva = vc[0] * va[0] + vc[1] * va[1] + vc[2] * va[2];
-  const double vcvb = vc[0] * vb[0] + vc[1] * vb[1] + vc[2] * vb[2];
-  double ps[3];
+  const R vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
+  const R gc = R(1) / sqrt(R(1) - vc2);
+  const R kc = gc * gc / (gc + R(1));  // (gamma_c - 1) / v_c^2
+  const R vcva = vc[0] * va[0] + vc[1] * va[1] + vc[2] * va[2];
+  const R vcvb = vc[0] * vb[0] + vc[1] * vb[1] + vc[2] * vb[2];
+  R ps[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) ps[d] = pa[d] + (kc * vcva - gc) * ma * ga * vc[d];
-  const double gsa = (1.0 - vcva / c2) * gc * ga, gsb = (1.0 - vcvb / c2) * gc * gb;
-  const double p2 = ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2];
-  const double pm = sqrt(p2);
-  if (!(pm > 0.0)) return;
-  const double e2 = kQe * kQe;
-  const double mm = ma * gsa * mb * gsb * c2 / p2 + 1.0;
-  const double b0 = e2 / (4.0 * kPi * kEps0 * c2) * gc / Et * mm;
-  const double bmin = fmax(2.0 * kPi * kHbar / (2.0 * pm), b0);
-  const double lnL = fmax(1.0, 0.5 * log(1.0 + lD * lD / (bmin * bmin)));
-  const double sv = neff * dtc * lnL * e2 * e2 /
-                    (4.0 * kPi * kEps0 * kEps0 * c2 * c2 * ma * ga * mb * gb) * gc * pm / Et *
-                    mm * mm;
-  const double vrel = Et * pm / (ma * gsa * mb * gsb * gc);
-  const double dens = fmax(ma * pow(na, 2.0 / 3.0), mb * pow(nb, 2.0 / 3.0));
-  const double scap = neff * dtc * pow(4.0 * kPi / 3.0, 1.0 / 3.0) * (ma + mb) / dens * vrel;
-  const double s = fmin(sv, scap);
-  const double cx = nanbu_cos(s, U[0]);
-  const double sx = sqrt(fmax(0.0, 1.0 - cx * cx));
-  const double phi = 2.0 * kPi * U[1];
-  const double u[3] = {ps[0] / pm, ps[1] / pm, ps[2] / pm};
-  double e1[3], e2v[3];
-  if (fabs(u[2]) < 0.9) {
-    const double n = sqrt(u[0] * u[0] + u[1] * u[1]);
+  const R gsa = (R(1) - vcva) * gc * ga, gsb = (R(1) - vcvb) * gc * gb;
+  const R p2 = ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2];
+  const R pm = sqrt(p2);
+  if (!(pm > R(0))) return;
+  const R mm = ma * gsa * mb * gsb / p2 + R(1);
+  const R b0 = R(K.re) * gc / Et * mm;
+  const R bmin = fmax(R(K.lc) / (R(2) * pm), b0);
+  const R lnL = fmax(R(1), R(0.5) * log(R(1) + lD * lD / (bmin * bmin)));
+  const R sv = nd * R(K.K1) * lnL * gc * pm / (ma * ga * mb * gb * Et) * mm * mm;
+  const R vrel = Et * pm / (ma * gsa * mb * gsb * gc);
+  const R dens = fmax(ma * pow(na, R(2) / R(3)), mb * pow(nb, R(2) / R(3)));
+  const R scap = nd * R(K.capc) * (ma + mb) / dens * vrel;
+  const R s = fmin(sv, scap);
+  const R cx = nanbu_cos(s, U[0]);
+  const R sx = sqrt(fmax(R(0), R(1) - cx * cx));
+  const R phi = R(2 * kPi) * U[1];
+  const R u[3] = {ps[0] / pm, ps[1] / pm, ps[2] / pm};
+  R e1[3], e2v[3];
+  if (fabs(u[2]) < R(0.9)) {
+    const R n = sqrt(u[0] * u[0] + u[1] * u[1]);
     e1[0] = u[1] / n;
     e1[1] = -u[0] / n;
-    e1[2] = 0.0;
+    e1[2] = R(0);
   } else {
-    const double n = sqrt(u[1] * u[1] + u[2] * u[2]);
-    e1[0] = 0.0;
+    const R n = sqrt(u[1] * u[1] + u[2] * u[2]);
+    e1[0] = R(0);
     e1[1] = u[2] / n;
     e1[2] = -u[1] / n;
   }
   e2v[0] = u[1] * e1[2] - u[2] * e1[1];
   e2v[1] = u[2] * e1[0] - u[0] * e1[2];
   e2v[2] = u[0] * e1[1] - u[1] * e1[0];
-  const double cp = cos(phi), sp = sin(phi);
-  double pn[3];
+  const R cp = cos(phi), sp = sin(phi);
+  R pn[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) pn[d] = pm * (cx * u[d] + sx * (cp * e1[d] + sp * e2v[d]));
-  const double vpa = vc[0] * pn[0] + vc[1] * pn[1] + vc[2] * pn[2];
-  const double wmax = fmax(wa, wb);
-  if (U[2] * wmax < wb) {
+  const R vpa = vc[0] * pn[0] + vc[1] * pn[1] + vc[2] * pn[2];
+  // (a side whose partner weighs at least as much always moves: the same
+  // as U w_max < w_other for every U < 1, and safe when a float U rounds to 1)
+  const R wmax = fmax(wa, wb);
+  if (wb >= wmax || U[2] * wmax < wb) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) / ma;
   }
-  if (U[3] * wmax < wa) {
+  if (wa >= wmax || U[3] * wmax < wa) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) / mb;
   }
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Pair q of cell c: both particles read from and written back to the pool.
+// Per-warp shared state of one cell.
 template <class R>
-__device__ void collide_slots(const Dev<R> &D, unsigned long long pa, unsigned long long pb,
-                              uint32_t step, uint32_t c, uint32_t q, double neff, double na,
-                              double nb, double lD, double dtc) {
-  const uint32_t ta = D.ptag[pa], tb = D.ptag[pb];
-  const LayerK &La = D.layers[ta >> 1], &Lb = D.layers[tb >> 1];
-  double ua[3], ub[3];
+struct CollCell {
+  uint32_t key[kCollMax];
+  unsigned long long id[kCollMax];
+  R v[3][kCollMax];  // velocity / c
+  R m[kCollMax];     // mass / m_e
+  R w[kCollMax];     // weight
+  uint8_t sp[kCollMax];
+  short ord[2][kCollMax];
+};
+
+// Pair q of cell c (slots i, j of the cell): both particles read from and
+// written back to the pool.
+template <class R>
+__device__ void collide_slots(const Dev<R> &D, const CollCell<R> &S, unsigned long long st, int i,
+                              int j, uint32_t step, uint32_t c, uint32_t q, R nd, R na, R nb,
+                              R lD, const CollConst &K) {
+  const unsigned long long pa = st + i, pb = st + j;
+  const R ic = R(1.0 / kC);
+  R ua[3], ub[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    ua[d] = (double)D.pu[d][pa];
-    ub[d] = (double)D.pu[d][pb];
+    ua[d] = D.pu[d][pa] * ic;
+    ub[d] = D.pu[d][pb] * ic;
   }
   const uint4 w = draw(D.seed, step, c, q, kStreamCollPair);
-  const double U[4] = {unit_open<double>(w.x), unit_open<double>(w.y), unit_open<double>(w.z),
-                       unit_open<double>(w.w)};
-  collide_pair(ua, ub, La.mass[ta & 1u], Lb.mass[tb & 1u], La.wmac, Lb.wmac, neff, na, nb, lD,
-               dtc, U);
+  const R U[4] = {unit_open<R>(w.x), unit_open<R>(w.y), unit_open<R>(w.z), unit_open<R>(w.w)};
+  collide_pair(ua, ub, S.m[i], S.m[j], S.w[i], S.w[j], nd, na, nb, lD, K, U);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    D.pu[d][pa] = R(ua[d]);
-    D.pu[d][pb] = R(ub[d]);
+    D.pu[d][pa] = ua[d] * R(kC);
+    D.pu[d][pb] = ub[d] * R(kC);
   }
 }
 
@@ -1425,17 +1463,45 @@ __device__ void collide_slots(const Dev<R> &D, unsigned long long pa, unsigned l
 // pairwise at half strength), then unlike pairs (A_i, B_{i mod |B|}) in
 // rounds of |B| disjoint pairs.  Pair q (in that order) draws Philox
 // (step, cell, q) stream 6.  cend[c] is the end of cell c in the sorted pool.
+// Cells that hold two or more charged particles after the sort.
+__global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *list, int *nlist) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool two = c < ncell && cend[c] - (c ? cend[c - 1] : 0u) >= 2u;
+  const unsigned act = __ballot_sync(0xffffffffu, two);
+  if (!act) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(act) - 1) base = atomicAdd(nlist, __popc(act));
+  base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
+  if (two) list[base + __popc(act & ((1u << lane) - 1u))] = (int)c;
+}
+
+template <class R>
+__device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int *cend, long long c,
+                             const CollConst &K, double dtc);
+
+// Persistent: each warp takes the next listed cell from a shared counter.
 template <class R>
 __global__ void __launch_bounds__(32 * kCollWarps) k_collide(Ctx<R> X, const unsigned int *cend,
-                                                              double dtc) {
-  __shared__ uint32_t skey[kCollWarps][kCollMax];
-  __shared__ unsigned long long sid[kCollWarps][kCollMax];
-  __shared__ uint8_t ssp[kCollWarps][kCollMax];
-  __shared__ short sord[kCollWarps][2][kCollMax];
-  const Dev<R> &D = X.d;
+                                                              const int *list, const int *nlist,
+                                                              int *next, CollConst K, double dtc) {
+  __shared__ CollCell<R> cells[kCollWarps];
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long c = (long long)blockIdx.x * kCollWarps + wp;
-  if (c >= D.ncell) return;
+  const int nl = *nlist;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(next, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nl) return;
+    collide_cell(X.d, cells[wp], cend, (long long)list[q], K, dtc);
+    __syncwarp();
+  }
+}
+
+template <class R>
+__device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int *cend, long long c,
+                             const CollConst &K, double dtc) {
+  const int lane = threadIdx.x & 31;
   const unsigned int st = c ? cend[c - 1] : 0u, en = cend[c];
   const int n = (int)(en - st);
   if (n < 2) return;
@@ -1444,6 +1510,7 @@ __global__ void __launch_bounds__(32 * kCollWarps) k_collide(Ctx<R> X, const uns
     return;
   }
   const uint32_t step = (uint32_t)*D.step;
+  const R ic = R(1.0 / kC);
   int cnt[2] = {0, 0};
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int i = i0 + lane;
@@ -1451,100 +1518,108 @@ __global__ void __launch_bounds__(32 * kCollWarps) k_collide(Ctx<R> X, const uns
     if (i < n) {
       const unsigned long long p = st + i;
       const unsigned long long id = D.pid[p];
-      sid[wp][i] = id;
-      skey[wp][i] = draw(D.seed, step, (uint32_t)id, (uint32_t)(id >> 32), kStreamCollOrder).x;
-      sp = (uint8_t)(D.ptag[p] & 1u);
-      ssp[wp][i] = sp;
+      S.id[i] = id;
+      S.key[i] = draw(D.seed, step, (uint32_t)id, (uint32_t)(id >> 32), kStreamCollOrder).x;
+      const uint32_t t = D.ptag[p];
+      sp = (uint8_t)(t & 1u);
+      S.sp[i] = sp;
+      const LayerK &L = D.layers[t >> 1];
+      S.m[i] = R(L.mass[sp] / kMe);
+      S.w[i] = R(L.wmac);
+      const R u0 = D.pu[0][p] * ic, u1 = D.pu[1][p] * ic, u2 = D.pu[2][p] * ic;
+      const R g = sqrt(R(1) + (u0 * u0 + u1 * u1 + u2 * u2));
+      S.v[0][i] = u0 / g;
+      S.v[1][i] = u1 / g;
+      S.v[2][i] = u2 / g;
     }
     cnt[0] += __popc(__ballot_sync(0xffffffffu, sp == 0));
     cnt[1] += __popc(__ballot_sync(0xffffffffu, sp == 1));
   }
   __syncwarp();
   for (int i = lane; i < n; i += 32) {
-    const uint32_t ki = skey[wp][i];
-    const unsigned long long idi = sid[wp][i];
-    const uint8_t si = ssp[wp][i];
+    const uint32_t ki = S.key[i];
+    const unsigned long long idi = S.id[i];
+    const uint8_t si = S.sp[i];
     int r = 0;
     for (int j = 0; j < n; ++j)
-      if (ssp[wp][j] == si && (skey[wp][j] < ki || (skey[wp][j] == ki && sid[wp][j] < idi))) ++r;
-    sord[wp][si][r] = (short)i;
+      if (S.sp[j] == si && (S.key[j] < ki || (S.key[j] == ki && S.id[j] < idi))) ++r;
+    S.ord[si][r] = (short)i;
   }
-  __syncwarp();
   // densities and kinetic temperatures of the two groups: mean mass times
   // the weighted velocity variance, written as a sum over pairs (exactly 0
-  // for one particle or equal velocities, no cancellation)
-  double ws[2] = {0.0, 0.0}, wm[2] = {0.0, 0.0}, S[2] = {0.0, 0.0};
+  // for one particle or equal velocities, no cancellation); T / (m_e c^2)
+  R ws[2] = {R(0), R(0)}, wm[2] = {R(0), R(0)}, Sv[2] = {R(0), R(0)};
   for (int i = lane; i < n; i += 32) {
-    const unsigned long long pi = st + i;
-    const uint32_t ti = D.ptag[pi];
-    const int sp = ti & 1u;
-    const LayerK &Li = D.layers[ti >> 1];
-    ws[sp] += Li.wmac;
-    wm[sp] += Li.wmac * Li.mass[sp];
-    const double a0 = D.pu[0][pi], a1 = D.pu[1][pi], a2 = D.pu[2][pi];
-    const double gi = sqrt(1.0 + (a0 * a0 + a1 * a1 + a2 * a2) / (kC * kC));
+    const int sp = S.sp[i];
+    ws[sp] += S.w[i];
+    wm[sp] += S.w[i] * S.m[i];
     for (int j = i + 1; j < n; ++j) {
-      if (ssp[wp][j] != sp) continue;
-      const unsigned long long pj = st + j;
-      const double b0 = D.pu[0][pj], b1 = D.pu[1][pj], b2 = D.pu[2][pj];
-      const double gj = sqrt(1.0 + (b0 * b0 + b1 * b1 + b2 * b2) / (kC * kC));
-      const double d0 = a0 / gi - b0 / gj, d1 = a1 / gi - b1 / gj, d2 = a2 / gi - b2 / gj;
-      S[sp] += Li.wmac * D.layers[D.ptag[pj] >> 1].wmac * (d0 * d0 + d1 * d1 + d2 * d2);
+      if (S.sp[j] != sp) continue;
+      const R d0 = S.v[0][i] - S.v[0][j], d1 = S.v[1][i] - S.v[1][j], d2 = S.v[2][i] - S.v[2][j];
+      Sv[sp] += S.w[i] * S.w[j] * (d0 * d0 + d1 * d1 + d2 * d2);
     }
   }
-  double T[2];
+  const R V = R(D.V_d);
+  R dens[2], inv_l2 = R(0);
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
-    ws[sp] = warp_sum_d(ws[sp]);
-    wm[sp] = warp_sum_d(wm[sp]);
-    S[sp] = warp_sum_d(S[sp]);
-    T[sp] = ws[sp] > 0.0 ? wm[sp] / ws[sp] * S[sp] / (3.0 * ws[sp] * ws[sp]) : 0.0;
-  }
-  const double V = D.V_d;
-  double dens[2], inv_l2 = 0.0;
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
+    ws[sp] = warp_sum(ws[sp]);
+    wm[sp] = warp_sum(wm[sp]);
+    Sv[sp] = warp_sum(Sv[sp]);
+    const R T = ws[sp] > R(0) ? wm[sp] / ws[sp] * Sv[sp] / (R(3) * ws[sp] * ws[sp]) : R(0);
     dens[sp] = ws[sp] / V;
-    if (T[sp] > 0.0) inv_l2 += dens[sp] * kQe * kQe / (kEps0 * T[sp]);
+    if (T > R(0)) inv_l2 += dens[sp] * R(K.kD) / T;
   }
-  const double ni = dens[1] > 0.0 ? dens[1] : dens[0];
-  const double ra = pow(4.0 * kPi * ni / 3.0, -1.0 / 3.0);
-  const double lD = inv_l2 > 0.0 ? fmax(1.0 / sqrt(inv_l2), ra) : ra;
-  uint32_t qb = 0;
-  // like pairs
+  const R ni = dens[1] > R(0) ? dens[1] : dens[0];
+  const R ra = pow(R(4 * kPi / 3) * ni, R(-1) / R(3));
+  const R lD = inv_l2 > R(0) ? fmax(R(1) / sqrt(inv_l2), ra) : ra;
+  const R dt = R(dtc);
+  __syncwarp();
+  // like pairs: electron and hole pairs touch disjoint particles and run
+  // together; an odd group's triplet runs on one lane (lane 0 electrons,
+  // lane 1 holes), every other pair on its own lane
+  const int nlike[2] = {cnt[0] < 2 ? 0 : ((cnt[0] & 1) ? 3 + (cnt[0] - 3) / 2 : cnt[0] / 2),
+                        cnt[1] < 2 ? 0 : ((cnt[1] & 1) ? 3 + (cnt[1] - 3) / 2 : cnt[1] / 2)};
+  const uint32_t qsp[2] = {0u, (uint32_t)nlike[0]};
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const int m = cnt[sp];
-    if (m < 2) continue;
-    const short *ord = sord[wp][sp];
-    const int start = (m & 1) ? 3 : 0;
-    if ((m & 1) && lane == 0) {
+    if ((m & 1) && m >= 3 && lane == sp) {
+      const short *ord = S.ord[sp];
       const int tri[3][2] = {{0, 1}, {0, 2}, {1, 2}};
       for (int t = 0; t < 3; ++t)
-        collide_slots(D, st + ord[tri[t][0]], st + ord[tri[t][1]], step, (uint32_t)c, qb + t,
-                      0.5 * dens[sp], dens[sp], dens[sp], lD, dtc);
+        collide_slots(D, S, st, ord[tri[t][0]], ord[tri[t][1]], step, (uint32_t)c, qsp[sp] + t,
+                      R(0.5) * dens[sp] * dt, dens[sp], dens[sp], lD, K);
     }
-    for (int k = lane; start + 2 * k + 1 < m; k += 32)
-      collide_slots(D, st + ord[start + 2 * k], st + ord[start + 2 * k + 1], step, (uint32_t)c,
-                    qb + start + k, dens[sp], dens[sp], dens[sp], lD, dtc);
-    qb += (m & 1) ? 3 + (m - 3) / 2 : m / 2;
-    __syncwarp();
   }
+  {
+    // remaining like pairs of both groups, numbered k over electrons then holes
+    const int r0 = cnt[0] < 2 ? 0 : (cnt[0] & 1 ? (cnt[0] - 3) / 2 : cnt[0] / 2);
+    const int r1 = cnt[1] < 2 ? 0 : (cnt[1] & 1 ? (cnt[1] - 3) / 2 : cnt[1] / 2);
+    for (int k = lane; k < r0 + r1; k += 32) {
+      const int sp = k < r0 ? 0 : 1, kk = k < r0 ? k : k - r0;
+      const int start = (cnt[sp] & 1) ? 3 : 0;
+      const short *ord = S.ord[sp];
+      collide_slots(D, S, st, ord[start + 2 * kk], ord[start + 2 * kk + 1], step, (uint32_t)c,
+                    qsp[sp] + start + kk, dens[sp] * dt, dens[sp], dens[sp], lD, K);
+    }
+  }
+  __syncwarp();
+  const uint32_t qb = (uint32_t)(nlike[0] + nlike[1]);
   // unlike pairs: every particle of the larger group once
   if (cnt[0] > 0 && cnt[1] > 0) {
     const int A = cnt[0] >= cnt[1] ? 0 : 1, B = 1 - A;
     const int nA = cnt[A], nB = cnt[B];
-    const short *oA = sord[wp][A], *oB = sord[wp][B];
-    double nab = 0.0;
-    for (int i = lane; i < nA; i += 32)
-      nab += fmin(D.layers[D.ptag[st + oA[i]] >> 1].wmac, D.layers[D.ptag[st + oB[i % nB]] >> 1].wmac) / V;
-    nab = warp_sum_d(nab);
-    const double neff = dens[0] * dens[1] / nab;
+    const short *oA = S.ord[A], *oB = S.ord[B];
+    R nab = R(0);
+    for (int i = lane; i < nA; i += 32) nab += fmin(S.w[oA[i]], S.w[oB[i % nB]]) / V;
+    nab = warp_sum(nab);
+    const R nd = dens[0] * (dens[1] / nab) * dt;
     for (int r0 = 0; r0 < nA; r0 += nB) {
       for (int i = r0 + lane; i < min(r0 + nB, nA); i += 32) {
-        const unsigned long long pA = st + oA[i], pB = st + oB[i % nB];
-        const unsigned long long pe = A == 0 ? pA : pB, ph = A == 0 ? pB : pA;
-        collide_slots(D, pe, ph, step, (uint32_t)c, qb + i, neff, dens[0], dens[1], lD, dtc);
+        const int iA = oA[i], iB = oB[i % nB];
+        const int ie = A == 0 ? iA : iB, ih = A == 0 ? iB : iA;
+        collide_slots(D, S, st, ie, ih, step, (uint32_t)c, qb + i, nd, dens[0], dens[1], lD, K);
       }
       __syncwarp();
     }
