@@ -55,7 +55,9 @@ struct Plan {
   size_t off_cnt, off_bsum, off_total, off_nslots, off_step, off_acc, off_err;
   size_t off_work, off_work_n, off_leave16;
   size_t off_imax, off_prof;
-  size_t off_clist, off_cn;  // collision cell list and its count / work counter
+  size_t off_clist, off_cn;  // collision cell list and its counters
+  size_t off_cpar, off_cord, off_clike, off_cunl;  // collision work (coll_every > 0)
+  long long coll_cells_max;
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
@@ -171,8 +173,17 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_leave16 = take(std::max<long long>(P.nmat, 1) * P.ppc_max * 2);
   P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
   P.off_imax = take(P.ncell * R);
-  P.off_clist = take(g.coll_every > 0 ? P.ncell * 4 : 4);
+  // collisions: listed cells hold >= 2 particles, so at most cap / 2 of them,
+  // and as many like items or unlike columns
+  const bool coll = g.coll_every > 0;
+  P.coll_cells_max = coll ? std::min<long long>(P.ncell, P.cap / 2 + 1) : 1;
+  P.off_clist = take(coll ? P.ncell * 4 : 4);
   P.off_cn = take(16);
+  P.off_cpar = take((size_t)P.coll_cells_max *
+                    std::max(sizeof(CollParam<double>), sizeof(CollParam<float>)));
+  P.off_cord = take(coll ? P.cap * 4 : 4);
+  P.off_clike = take((size_t)(coll ? P.cap / 2 + 1 : 1) * 8);
+  P.off_cunl = take((size_t)(coll ? P.cap / 2 + 1 : 1) * 8);
   P.off_prof = take((size_t)(2 * (g.nz + 1) + g.nz) * 8);
   P.off_work_n = take(16);
   P.off_cnt = take(P.ncell * 4);
@@ -267,6 +278,9 @@ std::vector<LayerR<R>> layer_working(const Plan &P, const std::vector<LayerK> &l
     r.kP = R(k.kP);
     r.e_skip = R(k.e_skip);
     r.sig_v = R(k.sigv);
+    r.mhat[0] = R(k.mass[0] / kMe);
+    r.mhat[1] = R(k.mass[1] / kMe);
+    r.wmac = R(k.wmac);
     out.push_back(r);
   }
   return out;
@@ -476,13 +490,22 @@ int enqueue(pic_ctx *h, int mask) {
     K.kD = 4.0 * kPi * K.re;
     K.capc = std::cbrt(4.0 * kPi / 3.0) * kC;
     const unsigned int *cend = (const unsigned int *)(h->arena + P.off_cnt);
-    int *clist = (int *)(h->arena + P.off_clist), *cn = (int *)(h->arena + P.off_cn);
-    PIC_CUDA(cudaMemsetAsync(cn, 0, 2 * sizeof(int), s));
-    k_coll_cells<<<grid_blocks(P.ncell), kThreads, 0, s>>>(cend, P.ncell, clist, cn);
-    k_collide<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, clist, cn, cn + 1, K,
-                                                            P.dt * P.g.coll_every);
+    CollWork<R> W;
+    int *clist = (int *)(h->arena + P.off_clist);
+    W.list = clist;
+    W.n = (int *)(h->arena + P.off_cn);
+    W.par = (CollParam<R> *)(h->arena + P.off_cpar);
+    W.ord = (int *)(h->arena + P.off_cord);
+    W.like = (unsigned long long *)(h->arena + P.off_clike);
+    W.unl = (unsigned long long *)(h->arena + P.off_cunl);
+    PIC_CUDA(cudaMemsetAsync(W.n, 0, 4 * sizeof(int), s));
+    k_coll_cells<<<grid_blocks(P.ncell), kThreads, 0, s>>>(cend, P.ncell, clist, W.n);
+    const double dtc = P.dt * P.g.coll_every;
+    k_coll_prep<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, W, dtc);
+    k_coll_like<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
+    k_coll_unlike<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
     prof_end(h);
-    h->launches += 2;
+    h->launches += 4;
   }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
@@ -553,7 +576,7 @@ int init_state(pic_ctx *h) {
   PIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<R>, kThreads, 0));
   h->push_blocks = std::max(1, nsm) * std::max(1, per_sm);
-  PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide<R>, 32 * kCollWarps, 0));
+  PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coll_prep<R>, 32 * kCollWarps, 0));
   h->coll_blocks = std::max(1, nsm) * std::max(1, per_sm);
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));

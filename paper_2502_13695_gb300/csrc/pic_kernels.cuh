@@ -25,6 +25,8 @@ struct LayerR {
   R kG, kX, kP, e_skip;
   R sig_v;
   R inv_mass_c2[2];
+  R mhat[2];  // carrier masses / m_e (collisions)
+  R wmac;     // real particles per macroparticle (collisions)
 };
 
 template <class R>
@@ -1289,6 +1291,9 @@ struct CollConst {
   double capc;  // (4 pi / 3)^(1/3) c                         [m/s]
 };
 
+// e^2 / (eps0 m_e c^2) = 4 pi r_e [m]: the Debye sum in normalised units.
+constexpr double K_KD = kQe * kQe / (kEps0 * kMe * kC * kC);
+
 template <class R> struct CollTol;
 template <> struct CollTol<double> { static constexpr double v = 4e-16, small = 1e-4; };
 template <> struct CollTol<float> { static constexpr float v = 4e-7f, small = 0.5f; };
@@ -1422,7 +1427,7 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// Per-warp shared state of one cell.
+// Per-warp shared state of one cell while it is prepared.
 template <class R>
 struct CollCell {
   uint32_t key[kCollMax];
@@ -1431,16 +1436,39 @@ struct CollCell {
   R m[kCollMax];     // mass / m_e
   R w[kCollMax];     // weight
   uint8_t sp[kCollMax];
-  short ord[2][kCollMax];
 };
 
-// Pair q of cell c (slots i, j of the cell): both particles read from and
-// written back to the pool.
+// A prepared cell: where its particles start in the sorted pool, its group
+// sizes, the collision parameters shared by its pairs and the Philox index
+// of its first unlike pair.  ord (global, indexed like the pool) lists the
+// cell's slots in pairing order: electrons, then holes.
 template <class R>
-__device__ void collide_slots(const Dev<R> &D, const CollCell<R> &S, unsigned long long st, int i,
-                              int j, uint32_t step, uint32_t c, uint32_t q, R nd, R na, R nb,
-                              R lD, const CollConst &K) {
-  const unsigned long long pa = st + i, pb = st + j;
+struct CollParam {
+  unsigned int st, cell;
+  int nE, nH;
+  R ndl[2];  // like pairs: group density x collision interval
+  R ndu;     // unlike pairs: n_e n_h / n_ab x collision interval
+  R dens[2], lD;
+  uint32_t qu;
+};
+
+// Work items: bits 0-31 the prepared cell, bit 32 the group, bit 33 a
+// triplet, bits 34-49 the pair (or unlike column) index.
+__device__ __forceinline__ unsigned long long coll_item(int cidx, int sp, int tri, int k) {
+  return (unsigned long long)(unsigned)cidx | ((unsigned long long)sp << 32) |
+         ((unsigned long long)tri << 33) | ((unsigned long long)k << 34);
+}
+
+// Pair q of a cell (pool slots pa, pb): both particles read from and written
+// back to the pool.  Out of line: one copy of the pair arithmetic for all
+// call sites keeps the kernels within the instruction cache.
+template <class R>
+__device__ __noinline__ void collide_pool(const Dev<R> &D, const LayerR<R> *__restrict__ lr,
+                                          unsigned long long pa, unsigned long long pb,
+                                          uint32_t step, uint32_t c, uint32_t q, R nd, R na, R nb,
+                                          R lD, const CollConst &K) {
+  const uint32_t ta = D.ptag[pa], tb = D.ptag[pb];
+  const LayerR<R> &La = lr[ta >> 1], &Lb = lr[tb >> 1];
   const R ic = R(1.0 / kC);
   R ua[3], ub[3];
 #pragma unroll
@@ -1450,7 +1478,7 @@ __device__ void collide_slots(const Dev<R> &D, const CollCell<R> &S, unsigned lo
   }
   const uint4 w = draw(D.seed, step, c, q, kStreamCollPair);
   const R U[4] = {unit_open<R>(w.x), unit_open<R>(w.y), unit_open<R>(w.z), unit_open<R>(w.w)};
-  collide_pair(ua, ub, S.m[i], S.m[j], S.w[i], S.w[j], nd, na, nb, lD, K, U);
+  collide_pair(ua, ub, La.mhat[ta & 1u], Lb.mhat[tb & 1u], La.wmac, Lb.wmac, nd, na, nb, lD, K, U);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     D.pu[d][pa] = ua[d] * R(kC);
@@ -1458,11 +1486,6 @@ __device__ void collide_slots(const Dev<R> &D, const CollCell<R> &S, unsigned lo
   }
 }
 
-// One warp per cell: electrons and holes each ordered by a Philox key of
-// their id; like pairs (0,1), (2,3), ... (an odd count's first three collide
-// pairwise at half strength), then unlike pairs (A_i, B_{i mod |B|}) in
-// rounds of |B| disjoint pairs.  Pair q (in that order) draws Philox
-// (step, cell, q) stream 6.  cend[c] is the end of cell c in the sorted pool.
 // Cells that hold two or more charged particles after the sort.
 __global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *list, int *nlist) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1476,35 +1499,38 @@ __global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *lis
   if (two) list[base + __popc(act & ((1u << lane) - 1u))] = (int)c;
 }
 
+// Collision work of one pass, in global memory.
 template <class R>
-__device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int *cend, long long c,
-                             const CollConst &K, double dtc);
+struct CollWork {
+  const int *list;               // listed cells, count n[0]
+  int *n;                        // [0] listed cells [1] like items [2] unlike columns [3] next
+  CollParam<R> *par;             // one per listed cell
+  int *ord;                      // pool-indexed pairing order of every listed cell
+  unsigned long long *like, *unl;  // work items
+};
 
-// Persistent: each warp takes the next listed cell from a shared counter.
-template <class R>
-__global__ void __launch_bounds__(32 * kCollWarps) k_collide(Ctx<R> X, const unsigned int *cend,
-                                                              const int *list, const int *nlist,
-                                                              int *next, CollConst K, double dtc) {
-  __shared__ CollCell<R> cells[kCollWarps];
-  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nl = *nlist;
-  for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(next, 1);
-    q = __shfl_sync(0xffffffffu, q, 0);
-    if (q >= nl) return;
-    collide_cell(X.d, cells[wp], cend, (long long)list[q], K, dtc);
-    __syncwarp();
-  }
+__device__ __forceinline__ void append_item(unsigned long long *items, int *count, bool have,
+                                            unsigned long long item) {
+  const unsigned act = __ballot_sync(0xffffffffu, have);
+  if (!act) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(act) - 1) base = atomicAdd(count, __popc(act));
+  base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
+  if (have) items[base + __popc(act & ((1u << lane) - 1u))] = item;
 }
 
+// Prepare one listed cell (one warp): order each group by its Philox keys,
+// take the group densities, kinetic temperatures and screening length, and
+// append the cell's like pairs, triplets and unlike columns as work items.
 template <class R>
-__device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int *cend, long long c,
-                             const CollConst &K, double dtc) {
+__device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr, CollCell<R> &S,
+                               const unsigned int *cend, int cidx, const CollWork<R> &W,
+                               double dtc) {
   const int lane = threadIdx.x & 31;
+  const long long c = W.list[cidx];
   const unsigned int st = c ? cend[c - 1] : 0u, en = cend[c];
   const int n = (int)(en - st);
-  if (n < 2) return;
   if (n > kCollMax) {
     if (lane == 0) atomicOr(D.err, kErrColl);
     return;
@@ -1523,9 +1549,8 @@ __device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int
       const uint32_t t = D.ptag[p];
       sp = (uint8_t)(t & 1u);
       S.sp[i] = sp;
-      const LayerK &L = D.layers[t >> 1];
-      S.m[i] = R(L.mass[sp] / kMe);
-      S.w[i] = R(L.wmac);
+      S.m[i] = lr[t >> 1].mhat[sp];
+      S.w[i] = lr[t >> 1].wmac;
       const R u0 = D.pu[0][p] * ic, u1 = D.pu[1][p] * ic, u2 = D.pu[2][p] * ic;
       const R g = sqrt(R(1) + (u0 * u0 + u1 * u1 + u2 * u2));
       S.v[0][i] = u0 / g;
@@ -1543,7 +1568,7 @@ __device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int
     int r = 0;
     for (int j = 0; j < n; ++j)
       if (S.sp[j] == si && (S.key[j] < ki || (S.key[j] == ki && S.id[j] < idi))) ++r;
-    S.ord[si][r] = (short)i;
+    W.ord[st + (si ? cnt[0] : 0) + r] = (int)(st + i);
   }
   // densities and kinetic temperatures of the two groups: mean mass times
   // the weighted velocity variance, written as a sum over pairs (exactly 0
@@ -1568,60 +1593,123 @@ __device__ void collide_cell(const Dev<R> &D, CollCell<R> &S, const unsigned int
     Sv[sp] = warp_sum(Sv[sp]);
     const R T = ws[sp] > R(0) ? wm[sp] / ws[sp] * Sv[sp] / (R(3) * ws[sp] * ws[sp]) : R(0);
     dens[sp] = ws[sp] / V;
-    if (T > R(0)) inv_l2 += dens[sp] * R(K.kD) / T;
+    if (T > R(0)) inv_l2 += dens[sp] * R(K_KD) / T;
   }
+  __syncwarp();  // ord is complete
   const R ni = dens[1] > R(0) ? dens[1] : dens[0];
   const R ra = pow(R(4 * kPi / 3) * ni, R(-1) / R(3));
   const R lD = inv_l2 > R(0) ? fmax(R(1) / sqrt(inv_l2), ra) : ra;
   const R dt = R(dtc);
-  __syncwarp();
-  // like pairs: electron and hole pairs touch disjoint particles and run
-  // together; an odd group's triplet runs on one lane (lane 0 electrons,
-  // lane 1 holes), every other pair on its own lane
   const int nlike[2] = {cnt[0] < 2 ? 0 : ((cnt[0] & 1) ? 3 + (cnt[0] - 3) / 2 : cnt[0] / 2),
                         cnt[1] < 2 ? 0 : ((cnt[1] & 1) ? 3 + (cnt[1] - 3) / 2 : cnt[1] / 2)};
-  const uint32_t qsp[2] = {0u, (uint32_t)nlike[0]};
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    const int m = cnt[sp];
-    if ((m & 1) && m >= 3 && lane == sp) {
-      const short *ord = S.ord[sp];
-      const int tri[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-      for (int t = 0; t < 3; ++t)
-        collide_slots(D, S, st, ord[tri[t][0]], ord[tri[t][1]], step, (uint32_t)c, qsp[sp] + t,
-                      R(0.5) * dens[sp] * dt, dens[sp], dens[sp], lD, K);
-    }
-  }
-  {
-    // remaining like pairs of both groups, numbered k over electrons then holes
-    const int r0 = cnt[0] < 2 ? 0 : (cnt[0] & 1 ? (cnt[0] - 3) / 2 : cnt[0] / 2);
-    const int r1 = cnt[1] < 2 ? 0 : (cnt[1] & 1 ? (cnt[1] - 3) / 2 : cnt[1] / 2);
-    for (int k = lane; k < r0 + r1; k += 32) {
-      const int sp = k < r0 ? 0 : 1, kk = k < r0 ? k : k - r0;
-      const int start = (cnt[sp] & 1) ? 3 : 0;
-      const short *ord = S.ord[sp];
-      collide_slots(D, S, st, ord[start + 2 * kk], ord[start + 2 * kk + 1], step, (uint32_t)c,
-                    qsp[sp] + start + kk, dens[sp] * dt, dens[sp], dens[sp], lD, K);
-    }
-  }
-  __syncwarp();
-  const uint32_t qb = (uint32_t)(nlike[0] + nlike[1]);
-  // unlike pairs: every particle of the larger group once
+  R ndu = R(0);
   if (cnt[0] > 0 && cnt[1] > 0) {
     const int A = cnt[0] >= cnt[1] ? 0 : 1, B = 1 - A;
     const int nA = cnt[A], nB = cnt[B];
-    const short *oA = S.ord[A], *oB = S.ord[B];
+    const int *oA = W.ord + st + (A ? cnt[0] : 0), *oB = W.ord + st + (B ? cnt[0] : 0);
     R nab = R(0);
-    for (int i = lane; i < nA; i += 32) nab += fmin(S.w[oA[i]], S.w[oB[i % nB]]) / V;
+    for (int i = lane; i < nA; i += 32)
+      nab += fmin(lr[D.ptag[oA[i]] >> 1].wmac, lr[D.ptag[oB[i % nB]] >> 1].wmac) / V;
     nab = warp_sum(nab);
-    const R nd = dens[0] * (dens[1] / nab) * dt;
-    for (int r0 = 0; r0 < nA; r0 += nB) {
-      for (int i = r0 + lane; i < min(r0 + nB, nA); i += 32) {
-        const int iA = oA[i], iB = oB[i % nB];
-        const int ie = A == 0 ? iA : iB, ih = A == 0 ? iB : iA;
-        collide_slots(D, S, st, ie, ih, step, (uint32_t)c, qb + i, nd, dens[0], dens[1], lD, K);
-      }
-      __syncwarp();
+    ndu = dens[0] * (dens[1] / nab) * dt;
+  }
+  if (lane == 0) {
+    CollParam<R> P;
+    P.st = st;
+    P.cell = (unsigned)c;
+    P.nE = cnt[0];
+    P.nH = cnt[1];
+    P.ndl[0] = dens[0] * dt;
+    P.ndl[1] = dens[1] * dt;
+    P.ndu = ndu;
+    P.dens[0] = dens[0];
+    P.dens[1] = dens[1];
+    P.lD = lD;
+    P.qu = (uint32_t)(nlike[0] + nlike[1]);
+    W.par[cidx] = P;
+  }
+  // work items: triplets and like pairs of each group, then unlike columns
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const int m = cnt[sp];
+    const bool tri = m >= 3 && (m & 1);
+    const int rest = m < 2 ? 0 : (tri ? (m - 3) / 2 : m / 2);
+    append_item(W.like, W.n + 1, lane == 0 && tri, coll_item(cidx, sp, 1, 0));
+    for (int k0 = 0; k0 < rest; k0 += 32)
+      append_item(W.like, W.n + 1, k0 + lane < rest, coll_item(cidx, sp, 0, k0 + lane));
+  }
+  if (cnt[0] > 0 && cnt[1] > 0) {
+    const int nB = min(cnt[0], cnt[1]);
+    for (int j0 = 0; j0 < nB; j0 += 32)
+      append_item(W.unl, W.n + 2, j0 + lane < nB, coll_item(cidx, 0, 0, j0 + lane));
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(32 * kCollWarps) k_coll_prep(Ctx<R> X, const unsigned int *cend,
+                                                                CollWork<R> W, double dtc) {
+  __shared__ CollCell<R> cells[kCollWarps];
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = W.n[0];
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(W.n + 3, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nl) return;
+    coll_prep_cell(X.d, X.lr, cells[wp], cend, q, W, dtc);
+    __syncwarp();
+  }
+}
+
+// Like pairs (one thread per pair) and triplets (one thread each, three
+// pairs in order).  Pair q: electrons' like pairs first, then the holes'.
+template <class R>
+__global__ void __launch_bounds__(256) k_coll_like(Ctx<R> X, CollWork<R> W, CollConst K) {
+  const Dev<R> &D = X.d;
+  const int nitems = W.n[1];
+  const uint32_t step = (uint32_t)*D.step;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x) {
+    const unsigned long long it = W.like[t];
+    const int cidx = (int)(unsigned)it, sp = (int)(it >> 32) & 1, tri = (int)(it >> 33) & 1;
+    const int k = (int)(it >> 34) & 0xFFFF;
+    const CollParam<R> P = W.par[cidx];
+    const int m = sp ? P.nH : P.nE;
+    const int *ord = W.ord + P.st + (sp ? P.nE : 0);
+    const uint32_t q0 = sp ? (uint32_t)(P.nE < 2 ? 0 : ((P.nE & 1) ? 3 + (P.nE - 3) / 2 : P.nE / 2))
+                           : 0u;
+    if (tri) {
+      const int a[3] = {0, 0, 1}, b[3] = {1, 2, 2};
+      for (int r = 0; r < 3; ++r)
+        collide_pool(D, X.lr, ord[a[r]], ord[b[r]], step, P.cell, q0 + r, R(0.5) * P.ndl[sp],
+                     P.dens[sp], P.dens[sp], P.lD, K);
+    } else {
+      const int start = (m & 1) ? 3 : 0;
+      collide_pool(D, X.lr, ord[start + 2 * k], ord[start + 2 * k + 1], step, P.cell,
+                   q0 + start + k, P.ndl[sp], P.dens[sp], P.dens[sp], P.lD, K);
+    }
+  }
+}
+
+// Unlike pairs (A_i, B_{i mod |B|}), A the larger group: one thread per
+// column j of B takes i = j, j + |B|, ... in order, which is the order of the
+// rounds; columns share no particle.
+template <class R>
+__global__ void __launch_bounds__(256) k_coll_unlike(Ctx<R> X, CollWork<R> W, CollConst K) {
+  const Dev<R> &D = X.d;
+  const int nitems = W.n[2];
+  const uint32_t step = (uint32_t)*D.step;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x) {
+    const unsigned long long it = W.unl[t];
+    const int cidx = (int)(unsigned)it, j = (int)(it >> 34) & 0xFFFF;
+    const CollParam<R> P = W.par[cidx];
+    const int A = P.nE >= P.nH ? 0 : 1;
+    const int nA = A ? P.nH : P.nE, nB = A ? P.nE : P.nH;
+    const int *oE = W.ord + P.st, *oH = W.ord + P.st + P.nE;
+    const int *oA = A ? oH : oE, *oB = A ? oE : oH;
+    for (int i = j; i < nA; i += nB) {
+      const unsigned long long pA = oA[i], pB = oB[j];
+      collide_pool(D, X.lr, A == 0 ? pA : pB, A == 0 ? pB : pA, step, P.cell, P.qu + i, P.ndu,
+                   P.dens[0], P.dens[1], P.lD, K);
     }
   }
 }
