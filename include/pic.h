@@ -117,8 +117,14 @@ typedef struct {
   const pic_layer *layers;  /* host array, copied by pic_create */
 } pic_material;
 
-/* Laser (Sec. 3): plane wave along +z, Gaussian intensity envelope of
- * intensity FWHM fwhm, peak fluence F = int c eps0 E^2 dt at z = 0. */
+/* Laser (Sec. 3): a wave along +z injected through the z = 0 face.  Time
+ * envelope: Gaussian in intensity with FWHM fwhm, or the paper's
+ * sine-squared pulse (field envelope cos^2(pi (t - t_peak) / T) for
+ * |t - t_peak| < T / 2, T chosen so that the intensity FWHM is fwhm).
+ * Transverse profile: plane wave, or a Gaussian spot exp(-r^2 / w0^2) about
+ * the box centre (x and y stay periodic).  fluence is the peak fluence
+ * F = int c eps0 E^2 dt at the spot centre (for a spot, F = 2 E_las /
+ * (pi w0^2), Sec. 3). */
 typedef struct {
   double lambda;   /* wavelength [m] */
   double fwhm;     /* intensity FWHM [s] */
@@ -126,7 +132,8 @@ typedef struct {
   double cep;      /* carrier-envelope phase [rad] */
   double t_peak;   /* time of the envelope peak at z = 0 [s] */
   int pol;         /* 0: E along x, 1: E along y */
-  int reserved;
+  int shape;       /* 0: Gaussian, 1: sine-squared */
+  double w0;       /* spot radius [m] (1/e^2 of the intensity); 0: plane wave */
 } pic_pulse;
 
 /* Sizes and derived constants of a configuration (pic_query / pic_info). */

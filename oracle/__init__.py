@@ -83,6 +83,7 @@ class Config(ctypes.Structure):
                 ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("keldysh_terms", ctypes.c_int), ("n_layers", ctypes.c_int),
                 ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int),
+                ("shape", ctypes.c_int), ("pad_shape", ctypes.c_int), ("w0", ctypes.c_double),
                 ("layers", Layer * MAX_LAYERS)]
 
 
@@ -127,6 +128,8 @@ def lib():
             L.or_damage.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_damage.restype = d
             L.or_get_imax.argtypes = [vp, vp]
+            L.or_spot.argtypes = [vp, d, d]
+            L.or_spot.restype = d
             L.or_nanbu_A.argtypes = [d]
             L.or_nanbu_A.restype = d
             L.or_nanbu_cos.argtypes = [d, d]
@@ -241,6 +244,8 @@ def make_config(cfg: dict) -> Config:
     c.keldysh_terms = cfg.get("keldysh_terms", 500)
     c.imax_every = cfg.get("imax_every", 0)
     c.coll_every = cfg.get("coll_every", 0)
+    c.shape = 1 if p.get("shape", "gauss") == "sin2" else 0
+    c.w0 = float(p.get("w0", 0.0))
     layers = cfg["layers"]
     c.n_layers = len(layers)
     for n, ly in enumerate(layers):
@@ -383,6 +388,9 @@ class Sim:
 
     def incident(self, t: float) -> float:
         return lib().or_incident(self._h, float(t))
+
+    def spot(self, x: float, y: float) -> float:
+        return lib().or_spot(self._h, float(x), float(y))
 
     def intensity_max(self) -> np.ndarray:
         """Recorded maximum of |E|^2 / E0^2 per cell, shape (nz, ny, nx)."""

@@ -76,6 +76,9 @@ typedef struct {
   int n_layers;
   int imax_every; /* intensity record interval in steps: 0 = 0.5 fs, < 0 off */
   int coll_every; /* steps between binary-collision passes, 0 = none */
+  int shape;      /* temporal envelope: 0 Gaussian, 1 sine-squared (Sec. 3) */
+  int pad_shape;
+  double w0;      /* Gaussian spot radius (1/e^2 of the intensity), 0 = plane wave */
   or_layer layers[OR_MAX_LAYERS];
 } or_config;
 
@@ -358,6 +361,7 @@ typedef struct {
   /* maximum over the recorded steps of |E|^2 / E0^2 at each cell centre */
   double *imax;
   int imax_every;
+  double Tsin2; /* full duration of the sine-squared field envelope */
 } or_sim;
 
 static long fidx(const or_sim *s, int i, int j, int k) {
@@ -381,12 +385,30 @@ static void grow(or_sim *s, long need) {
   s->cap = nc;
 }
 
-/* Incident field at the z_min plane, Sec. 3 and reading K14: Gaussian
- * intensity envelope of FWHM tau, E0 from the fluence F = int c eps0 E^2 dt. */
+/* Incident field at the z_min plane (Sec. 3), at the spot centre: a
+ * Gaussian intensity envelope of FWHM tau (reading K14), or the paper's
+ * sine-squared pulse read as the field envelope cos^2(pi (t - t_peak) / T)
+ * on |t - t_peak| < T / 2, whose intensity (cos^4) has FWHM tau; E0 from
+ * the peak fluence F = int c eps0 E^2 dt. */
 static double e_inc(const or_sim *s, double t) {
-  double tau = s->cfg.fwhm, tt = t - s->cfg.t_peak;
-  return s->E0 * exp(-2.0 * log(2.0) * tt * tt / (tau * tau)) *
-         cos(s->omega * tt + s->cfg.cep);
+  double tau = s->cfg.fwhm, tt = t - s->cfg.t_peak, env;
+  if (s->cfg.shape == 1) {
+    double x = OR_PI * tt / s->Tsin2;
+    env = fabs(tt) < 0.5 * s->Tsin2 ? cos(x) * cos(x) : 0.0;
+  } else {
+    env = exp(-2.0 * log(2.0) * tt * tt / (tau * tau));
+  }
+  return s->E0 * env * cos(s->omega * tt + s->cfg.cep);
+}
+
+/* Transverse profile of the incident field, exp(-r^2 / w0^2) about the box
+ * centre (the spot radius of Sec. 3, where F = 2 E_las / (pi w0^2) is the
+ * peak fluence); 1 for a plane wave. */
+double or_spot(const or_sim *s, double x, double y) {
+  if (!(s->cfg.w0 > 0.0)) return 1.0;
+  double xc = 0.5 * s->cfg.nx * s->cfg.dx, yc = 0.5 * s->cfg.ny * s->cfg.dy;
+  double r2 = (x - xc) * (x - xc) + (y - yc) * (y - yc);
+  return exp(-r2 / (s->cfg.w0 * s->cfg.w0));
 }
 
 or_sim *or_create(const or_config *cfg) {
@@ -405,8 +427,13 @@ or_sim *or_create(const or_config *cfg) {
   s->alpha = OR_C * s->dt / cfg->dz;
   s->V = cfg->dx * cfg->dy * cfg->dz;
   s->NW = (int)ceil(cfg->lambda / (OR_C * s->dt));
-  s->E0 = sqrt(2.0 * cfg->fluence /
-               (OR_C * OR_EPS0 * cfg->fwhm * sqrt(OR_PI / (4.0 * log(2.0)))));
+  /* cos^4 falls to one half at pi t / T = acos(2^(-1/4)) */
+  s->Tsin2 = cfg->fwhm / (2.0 * acos(pow(2.0, -0.25)) / OR_PI);
+  if (cfg->shape == 1) /* int cos^4 over the pulse = 3 T / 8 */
+    s->E0 = sqrt(16.0 * cfg->fluence / (3.0 * OR_C * OR_EPS0 * s->Tsin2));
+  else
+    s->E0 = sqrt(2.0 * cfg->fluence /
+                 (OR_C * OR_EPS0 * cfg->fwhm * sqrt(OR_PI / (4.0 * log(2.0)))));
   for (int c = 0; c < NCOMP; c++) s->F[c] = calloc(s->nfield, sizeof(double));
   s->layer_of_plane = malloc(nz * sizeof(int));
   s->mplane = malloc(nz * sizeof(int));
@@ -677,10 +704,13 @@ static void e_full(or_sim *s) {
         double dBz_dx = (Bz[o] - Bz[fidx(s, i - 1, j, k)]) / dx;
         double ex0 = Ex[o], ey0 = Ey[o], ex1, ey1;
         if (k == 0) {
-          ex1 = ((1.0 - al) * ex0 - 2.0 * al * OR_C * By[o] + 4.0 * al * exi +
+          /* the polarised component's own node: Ex at ((i + 1/2) dx, j dy),
+           * Ey at (i dx, (j + 1/2) dy) */
+          double spx = or_spot(s, (i + 0.5) * dx, j * dy), spy = or_spot(s, i * dx, (j + 0.5) * dy);
+          ex1 = ((1.0 - al) * ex0 - 2.0 * al * OR_C * By[o] + 4.0 * al * exi * spx +
                  dt * (c2 * dBz_dy - Jx[o] / OR_EPS0)) /
                 (1.0 + al);
-          ey1 = ((1.0 - al) * ey0 + 2.0 * al * OR_C * Bx[o] + 4.0 * al * eyi -
+          ey1 = ((1.0 - al) * ey0 + 2.0 * al * OR_C * Bx[o] + 4.0 * al * eyi * spy -
                  dt * (c2 * dBz_dx + Jy[o] / OR_EPS0)) /
                 (1.0 + al);
         } else if (k == nz) {
@@ -1326,7 +1356,17 @@ void or_diagnostics(const or_sim *s, or_diag *dg, int n_bins, double e_min_eV,
   dg->U_kinetic = kin;
   dg->U_ionization = s->U_ion;
   dg->U_absorbed = kin + s->U_ion;
-  dg->U_incident = s->cfg.fluence * (nx * s->cfg.dx) * (ny * s->cfg.dy);
+  /* incident energy: the peak fluence times the sum over the entrance
+   * nodes of the polarised component of spot^2 dx dy (F Lx Ly for a plane
+   * wave, pi w0^2 F / 2 for a spot well inside the box) */
+  double area = 0.0;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      double sp = s->cfg.pol == 0 ? or_spot(s, (i + 0.5) * s->cfg.dx, j * s->cfg.dy)
+                                  : or_spot(s, i * s->cfg.dx, (j + 0.5) * s->cfg.dy);
+      area += sp * sp * s->cfg.dx * s->cfg.dy;
+    }
+  dg->U_incident = s->cfg.fluence * area;
   dg->frac_absorbed = dg->U_absorbed / dg->U_incident;
   dg->U_joule = s->U_joule;
   dg->N_pairs = s->N_pairs;

@@ -43,6 +43,7 @@ struct Plan {
   pic_pulse pulse;
   int rsz;  // bytes per real
   double dt, omega, E0, V;
+  double Tsin2;  // sine-squared envelope duration
   int NW, n_mplanes;
   long long nxy, nfield, ncell, nmat, n_neutrals, cap;
   std::vector<int> lop, mplane, kplane;
@@ -57,7 +58,6 @@ struct Plan {
   size_t off_imax, off_prof;
   size_t off_clist, off_cn;  // collision cell list and its counters
   size_t off_cpar, off_cord, off_clike, off_cunl;  // collision work (coll_every > 0)
-  long long coll_cells_max;
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
@@ -100,7 +100,14 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.imax_every = g.imax_every > 0
                      ? g.imax_every
                      : (g.imax_every == 0 ? (int)std::max(1.0, std::round(0.5e-15 / P.dt)) : 0);
-  P.E0 = std::sqrt(2.0 * pulse->fluence /
+  if (pulse->shape != 0 && pulse->shape != 1) return fail(PIC_EINVAL, "unknown pulse shape");
+  if (!(pulse->w0 >= 0.0)) return fail(PIC_EINVAL, "spot radius must be >= 0");
+  // cos^4 falls to one half at pi t / T = acos(2^(-1/4)); int cos^4 = 3 T / 8
+  P.Tsin2 = pulse->fwhm / (2.0 * std::acos(std::pow(2.0, -0.25)) / kPi);
+  if (pulse->shape == 1)
+    P.E0 = std::sqrt(16.0 * pulse->fluence / (3.0 * kC * kEps0 * P.Tsin2));
+  else
+    P.E0 = std::sqrt(2.0 * pulse->fluence /
                    (kC * kEps0 * pulse->fwhm * std::sqrt(kPi / (4.0 * std::log(2.0)))));
   P.lop.assign(g.nz, -1);
   P.n_neutrals = 0;
@@ -173,13 +180,12 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_leave16 = take(std::max<long long>(P.nmat, 1) * P.ppc_max * 2);
   P.off_work = take(std::max<long long>(P.nmat, 1) * 4);
   P.off_imax = take(P.ncell * R);
-  // collisions: listed cells hold >= 2 particles, so at most cap / 2 of them,
-  // and as many like items or unlike columns
+  // collisions: per-cell parameters indexed by cell; listed cells hold >= 2
+  // particles, so there are at most cap / 2 like items or unlike columns
   const bool coll = g.coll_every > 0;
-  P.coll_cells_max = coll ? std::min<long long>(P.ncell, P.cap / 2 + 1) : 1;
-  P.off_clist = take(coll ? P.ncell * 4 : 4);
-  P.off_cn = take(16);
-  P.off_cpar = take((size_t)P.coll_cells_max *
+  P.off_clist = take(coll ? P.ncell * 2 * 4 : 4);
+  P.off_cn = take(32);
+  P.off_cpar = take((size_t)(coll ? P.ncell : 1) *
                     std::max(sizeof(CollParam<double>), sizeof(CollParam<float>)));
   P.off_cord = take(coll ? P.cap * 4 : 4);
   P.off_clike = take((size_t)(coll ? P.cap / 2 + 1 : 1) * 8);
@@ -367,6 +373,11 @@ void bind(pic_ctx *h) {
   D.omega = P.omega;
   D.fwhm = P.pulse.fwhm;
   D.t_peak = P.pulse.t_peak;
+  D.shape = P.pulse.shape;
+  D.Tsin2 = P.Tsin2;
+  D.w0 = P.pulse.w0;
+  D.xc = 0.5 * P.g.nx * P.g.dx;
+  D.yc = 0.5 * P.g.ny * P.g.dy;
   D.cep = P.pulse.cep;
   for (int d = 0; d < 3; ++d) {
     D.E[d] = (R *)(A + P.off_E[d]);
@@ -494,18 +505,20 @@ int enqueue(pic_ctx *h, int mask) {
     int *clist = (int *)(h->arena + P.off_clist);
     W.list = clist;
     W.n = (int *)(h->arena + P.off_cn);
+    W.ncell = P.ncell;
     W.par = (CollParam<R> *)(h->arena + P.off_cpar);
     W.ord = (int *)(h->arena + P.off_cord);
     W.like = (unsigned long long *)(h->arena + P.off_clike);
     W.unl = (unsigned long long *)(h->arena + P.off_cunl);
-    PIC_CUDA(cudaMemsetAsync(W.n, 0, 4 * sizeof(int), s));
+    PIC_CUDA(cudaMemsetAsync(W.n, 0, 8 * sizeof(int), s));
     k_coll_cells<<<grid_blocks(P.ncell), kThreads, 0, s>>>(cend, P.ncell, clist, W.n);
     const double dtc = P.dt * P.g.coll_every;
+    k_coll_prep_small<R><<<kPersistentBlocks, 128, 0, s>>>(X, cend, W, dtc);
     k_coll_prep<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, W, dtc);
     k_coll_like<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
     k_coll_unlike<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
     prof_end(h);
-    h->launches += 4;
+    h->launches += 5;
   }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
@@ -1146,7 +1159,21 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
     mrho = std::max(mrho, pg5[5 * b + 3]);
     mg = std::max(mg, pg5[5 * b + 4]);
   }
-  dg->U_incident = P.pulse.fluence * (P.g.nx * P.g.dx) * (P.g.ny * P.g.dy);
+  // the peak fluence times the sum of spot^2 dx dy over the entrance nodes
+  // of the polarised component (F Lx Ly for a plane wave)
+  double area = 0.0;
+  for (int j = 0; j < P.g.ny; ++j)
+    for (int i = 0; i < P.g.nx; ++i) {
+      const double x = (i + (P.pulse.pol == 0 ? 0.5 : 0.0)) * P.g.dx;
+      const double y = (j + (P.pulse.pol == 0 ? 0.0 : 0.5)) * P.g.dy;
+      double sp = 1.0;
+      if (P.pulse.w0 > 0.0) {
+        const double xc = 0.5 * P.g.nx * P.g.dx, yc = 0.5 * P.g.ny * P.g.dy;
+        sp = std::exp(-((x - xc) * (x - xc) + (y - yc) * (y - yc)) / (P.pulse.w0 * P.pulse.w0));
+      }
+      area += sp * sp * P.g.dx * P.g.dy;
+    }
+  dg->U_incident = P.pulse.fluence * area;
   dg->U_kinetic = kin;
   dg->U_ionization = acc[2];
   dg->U_absorbed = kin + acc[2];

@@ -56,6 +56,9 @@ struct Dev {
   R dtdx, dtdy, dtdz;             // dt / dx ...
   double dt_d, V_d, dx_d, dy_d, dz_d;
   double E0, omega, fwhm, t_peak, cep;
+  int shape;             // 0 Gaussian, 1 sine-squared envelope
+  double Tsin2;          // full duration of the sine-squared field envelope
+  double w0, xc, yc;     // spot radius (0: plane wave) and centre
   // fields: nfield each (E, B), J interleaved (Jx, Jy, Jz, 0) per point,
   // nmat each (P, Q)
   R *E[3], *B[3], *J4, *P[3], *Q[3];

@@ -495,13 +495,27 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
       const R al = D.alpha, cc = R(kC);
       const R inv = R(1) / (R(1) + al);
       if (k == 0) {
-        // incident field at t^{n+1/2}, computed in double
+        // incident field at t^{n+1/2}, computed in double: Gaussian or
+        // sine-squared envelope, times the spot profile at the polarised
+        // component's node (Ex at ((i + 1/2) dx, j dy), Ey at (i dx, (j + 1/2) dy))
         const double t = ((double)(*D.step) + 0.5) * D.dt_d - D.t_peak;
-        const double env = exp(-2.0 * 0.69314718055994531 * t * t / (D.fwhm * D.fwhm));
+        double env;
+        if (D.shape == 1) {
+          const double x = kPi * t / D.Tsin2;
+          env = fabs(t) < 0.5 * D.Tsin2 ? cos(x) * cos(x) : 0.0;
+        } else {
+          env = exp(-2.0 * 0.69314718055994531 * t * t / (D.fwhm * D.fwhm));
+        }
         const double einc = D.E0 * env * cos(D.omega * t + D.cep);
-        const R exi = D.pol == 0 ? R(einc) : R(0), eyi = D.pol == 0 ? R(0) : R(einc);
 #pragma unroll
         for (int l = 0; l < V; ++l) {
+          double sp = 1.0;
+          if (D.w0 > 0.0) {
+            const double x = (i + l + (D.pol == 0 ? 0.5 : 0.0)) * D.dx_d - D.xc;
+            const double y = (j + (D.pol == 0 ? 0.0 : 0.5)) * D.dy_d - D.yc;
+            sp = exp(-(x * x + y * y) / (D.w0 * D.w0));
+          }
+          const R exi = D.pol == 0 ? R(einc * sp) : R(0), eyi = D.pol == 0 ? R(0) : R(einc * sp);
           ex1[l] = ((R(1) - al) * ex0[l] - R(2) * al * cc * by[l] + R(4) * al * exi +
                     (c2dt * dBz_dy[l] - dtie * jx[l])) * inv;
           ey1[l] = ((R(1) - al) * ey0[l] + R(2) * al * cc * bx[l] + R(4) * al * eyi -
@@ -1310,21 +1324,32 @@ __device__ __forceinline__ R langevin(R A) {
   return R(1) / tanh(A) - R(1) / A;
 }
 
-// Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s) (bisection in
-// log A to the working precision).
+// Derivative of the Langevin function, 1/A^2 - 1/sinh^2 A (its series
+// where the difference cancels).
+template <class R>
+__device__ __forceinline__ R langevin_d(R A) {
+  if (A < R(sizeof(R) == 8 ? 1e-2 : 0.5)) {
+    const R A2 = A * A;
+    return R(1) / R(3) + A2 * (R(-1) / R(15) + A2 * (R(2) / R(189) + A2 * (R(-1) / R(675))));
+  }
+  const R sh = sinh(A);
+  return R(1) / (A * A) - R(1) / (sh * sh);
+}
+
+// Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s).  Newton from
+// the left (the function is increasing and concave, so the iterates rise
+// monotonically to the root), started below both asymptotes A = 3 exp(-s)
+// and A = 1 / (1 - exp(-s)); at most 40 steps.
 template <class R>
 __device__ R nanbu_A(R s) {
-  const R target = exp(-s);
-  R lo = R(1e-12), hi = R(1e12);
-  for (int it = 0; it < 200; ++it) {
-    const R mid = sqrt(lo * hi);
-    if (langevin(mid) < target)
-      lo = mid;
-    else
-      hi = mid;
-    if (hi / lo < R(1) + CollTol<R>::v) break;
+  const R t = exp(-s);
+  R A = fmin(R(3) * t, R(1) / (R(1) - t)) * R(0.5);
+  for (int it = 0; it < 40; ++it) {
+    const R dA = (t - langevin(A)) / langevin_d(A);
+    A += dA;
+    if (!(fabs(dA) > CollTol<R>::v * A)) break;
   }
-  return sqrt(lo * hi);
+  return A;
 }
 
 // cos chi for parameter s and uniform U: 1 + s ln U for s < 0.1, isotropic
@@ -1452,8 +1477,8 @@ struct CollParam {
   uint32_t qu;
 };
 
-// Work items: bits 0-31 the prepared cell, bit 32 the group, bit 33 a
-// triplet, bits 34-49 the pair (or unlike column) index.
+// Work items: bits 0-31 the cell, bit 32 the group, bit 33 a triplet,
+// bits 34-49 the pair (or unlike column) index.
 __device__ __forceinline__ unsigned long long coll_item(int cidx, int sp, int tri, int k) {
   return (unsigned long long)(unsigned)cidx | ((unsigned long long)sp << 32) |
          ((unsigned long long)tri << 33) | ((unsigned long long)k << 34);
@@ -1486,25 +1511,35 @@ __device__ __noinline__ void collide_pool(const Dev<R> &D, const LayerR<R> *__re
   }
 }
 
-// Cells that hold two or more charged particles after the sort.
-__global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *list, int *nlist) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool two = c < ncell && cend[c] - (c ? cend[c - 1] : 0u) >= 2u;
-  const unsigned act = __ballot_sync(0xffffffffu, two);
+constexpr int kCollSmall = 8;  // cells up to this size are prepared by one thread
+
+__device__ __forceinline__ void append_cell(int *list, int *count, bool have, int c) {
+  const unsigned act = __ballot_sync(0xffffffffu, have);
   if (!act) return;
   const int lane = threadIdx.x & 31;
   int base = 0;
-  if (lane == __ffs(act) - 1) base = atomicAdd(nlist, __popc(act));
+  if (lane == __ffs(act) - 1) base = atomicAdd(count, __popc(act));
   base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
-  if (two) list[base + __popc(act & ((1u << lane) - 1u))] = (int)c;
+  if (have) list[base + __popc(act & ((1u << lane) - 1u))] = c;
+}
+
+// Cells that hold two or more charged particles after the sort: those of at
+// most kCollSmall in list (count n[0]), larger ones in list + ncell (n[4]).
+__global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *list, int *n) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned int m = c < ncell ? cend[c] - (c ? cend[c - 1] : 0u) : 0u;
+  append_cell(list, n, m >= 2u && m <= (unsigned)kCollSmall, (int)c);
+  append_cell(list + ncell, n + 4, m > (unsigned)kCollSmall, (int)c);
 }
 
 // Collision work of one pass, in global memory.
 template <class R>
 struct CollWork {
-  const int *list;               // listed cells, count n[0]
-  int *n;                        // [0] listed cells [1] like items [2] unlike columns [3] next
-  CollParam<R> *par;             // one per listed cell
+  const int *list;               // listed cells: small ones (count n[0]), large at + ncell (n[4])
+  int *n;                        // [0] small cells [1] like items [2] unlike columns
+                                 // [3] next large cell [4] large cells
+  long long ncell;
+  CollParam<R> *par;             // indexed by cell
   int *ord;                      // pool-indexed pairing order of every listed cell
   unsigned long long *like, *unl;  // work items
 };
@@ -1528,7 +1563,7 @@ __device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr
                                const unsigned int *cend, int cidx, const CollWork<R> &W,
                                double dtc) {
   const int lane = threadIdx.x & 31;
-  const long long c = W.list[cidx];
+  const long long c = cidx;
   const unsigned int st = c ? cend[c - 1] : 0u, en = cend[c];
   const int n = (int)(en - st);
   if (n > kCollMax) {
@@ -1626,7 +1661,7 @@ __device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr
     P.dens[1] = dens[1];
     P.lD = lD;
     P.qu = (uint32_t)(nlike[0] + nlike[1]);
-    W.par[cidx] = P;
+    W.par[c] = P;
   }
   // work items: triplets and like pairs of each group, then unlike columns
 #pragma unroll
@@ -1650,14 +1685,141 @@ __global__ void __launch_bounds__(32 * kCollWarps) k_coll_prep(Ctx<R> X, const u
                                                                 CollWork<R> W, double dtc) {
   __shared__ CollCell<R> cells[kCollWarps];
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nl = W.n[0];
+  const int nl = W.n[4];
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(W.n + 3, 1);
     q = __shfl_sync(0xffffffffu, q, 0);
     if (q >= nl) return;
-    coll_prep_cell(X.d, X.lr, cells[wp], cend, q, W, dtc);
+    coll_prep_cell(X.d, X.lr, cells[wp], cend, W.list[W.ncell + q], W, dtc);
     __syncwarp();
+  }
+}
+
+// Warp-aggregated append of k items per lane (all lanes take part).
+__device__ __forceinline__ int reserve_items(int *count, int k) {
+  const int lane = threadIdx.x & 31;
+  int incl = k;
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, sft);
+    if (lane >= sft) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total) base = atomicAdd(count, total);
+  return __shfl_sync(0xffffffffu, base, 31) + incl - k;
+}
+
+// Small cells (2 .. kCollSmall particles): one thread each, the same
+// ordering, statistics and work items as the warp version.
+template <class R>
+__global__ void __launch_bounds__(128) k_coll_prep_small(Ctx<R> X, const unsigned int *cend,
+                                                         CollWork<R> W, double dtc) {
+  const Dev<R> &D = X.d;
+  const LayerR<R> *__restrict__ lr = X.lr;
+  const int ns = W.n[0];
+  const uint32_t step = (uint32_t)*D.step;
+  const R ic = R(1.0 / kC), V = R(D.V_d), dt = R(dtc);
+  const int stride = gridDim.x * blockDim.x;
+  for (int t0 = blockIdx.x * blockDim.x; t0 < ns; t0 += stride) {
+    const int t = t0 + threadIdx.x;
+    const bool have = t < ns;
+    int nl = 0, nu = 0, c = 0, cnt[2] = {0, 0};
+    unsigned int st = 0;
+    bool tri[2] = {false, false};
+    int rest[2] = {0, 0};
+    if (have) {
+      c = W.list[t];
+      st = c ? cend[c - 1] : 0u;
+      const int n = (int)(cend[c] - st);
+      uint32_t key[kCollSmall];
+      unsigned long long id[kCollSmall];
+      int sp[kCollSmall];
+      R m[kCollSmall], w[kCollSmall], v[3][kCollSmall];
+      for (int i = 0; i < n; ++i) {
+        const unsigned long long p = st + i;
+        id[i] = D.pid[p];
+        key[i] = draw(D.seed, step, (uint32_t)id[i], (uint32_t)(id[i] >> 32), kStreamCollOrder).x;
+        const uint32_t tg = D.ptag[p];
+        sp[i] = (int)(tg & 1u);
+        ++cnt[sp[i]];
+        m[i] = lr[tg >> 1].mhat[sp[i]];
+        w[i] = lr[tg >> 1].wmac;
+        const R u0 = D.pu[0][p] * ic, u1 = D.pu[1][p] * ic, u2 = D.pu[2][p] * ic;
+        const R g = sqrt(R(1) + (u0 * u0 + u1 * u1 + u2 * u2));
+        v[0][i] = u0 / g;
+        v[1][i] = u1 / g;
+        v[2][i] = u2 / g;
+      }
+      int ordl[2][kCollSmall];
+      for (int i = 0; i < n; ++i) {
+        int r = 0;
+        for (int j = 0; j < n; ++j)
+          if (sp[j] == sp[i] && (key[j] < key[i] || (key[j] == key[i] && id[j] < id[i]))) ++r;
+        ordl[sp[i]][r] = i;
+        W.ord[st + (sp[i] ? cnt[0] : 0) + r] = (int)(st + i);
+      }
+      R ws[2] = {R(0), R(0)}, wm[2] = {R(0), R(0)}, Sv[2] = {R(0), R(0)};
+      for (int i = 0; i < n; ++i) {
+        ws[sp[i]] += w[i];
+        wm[sp[i]] += w[i] * m[i];
+        for (int j = i + 1; j < n; ++j) {
+          if (sp[j] != sp[i]) continue;
+          const R d0 = v[0][i] - v[0][j], d1 = v[1][i] - v[1][j], d2 = v[2][i] - v[2][j];
+          Sv[sp[i]] += w[i] * w[j] * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+      }
+      R dens[2], inv_l2 = R(0);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const R T = ws[g] > R(0) ? wm[g] / ws[g] * Sv[g] / (R(3) * ws[g] * ws[g]) : R(0);
+        dens[g] = ws[g] / V;
+        if (T > R(0)) inv_l2 += dens[g] * R(K_KD) / T;
+      }
+      const R ni = dens[1] > R(0) ? dens[1] : dens[0];
+      const R ra = pow(R(4 * kPi / 3) * ni, R(-1) / R(3));
+      const R lD = inv_l2 > R(0) ? fmax(R(1) / sqrt(inv_l2), ra) : ra;
+      R ndu = R(0);
+      if (cnt[0] > 0 && cnt[1] > 0) {
+        const int A = cnt[0] >= cnt[1] ? 0 : 1, B = 1 - A;
+        R nab = R(0);
+        for (int i = 0; i < cnt[A]; ++i) nab += fmin(w[ordl[A][i]], w[ordl[B][i % cnt[B]]]) / V;
+        ndu = dens[0] * (dens[1] / nab) * dt;
+        nu = cnt[B];
+      }
+      int nlike[2];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        tri[g] = cnt[g] >= 3 && (cnt[g] & 1);
+        rest[g] = cnt[g] < 2 ? 0 : (tri[g] ? (cnt[g] - 3) / 2 : cnt[g] / 2);
+        nlike[g] = cnt[g] < 2 ? 0 : (tri[g] ? 3 + rest[g] : rest[g]);
+        nl += (tri[g] ? 1 : 0) + rest[g];
+      }
+      CollParam<R> P;
+      P.st = st;
+      P.cell = (unsigned)c;
+      P.nE = cnt[0];
+      P.nH = cnt[1];
+      P.ndl[0] = dens[0] * dt;
+      P.ndl[1] = dens[1] * dt;
+      P.ndu = ndu;
+      P.dens[0] = dens[0];
+      P.dens[1] = dens[1];
+      P.lD = lD;
+      P.qu = (uint32_t)(nlike[0] + nlike[1]);
+      W.par[c] = P;
+    }
+    int bl = reserve_items(W.n + 1, nl);
+    const int bu = reserve_items(W.n + 2, nu);
+    if (have) {
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        if (tri[g]) W.like[bl++] = coll_item(c, g, 1, 0);
+        for (int k = 0; k < rest[g]; ++k) W.like[bl++] = coll_item(c, g, 0, k);
+      }
+      for (int j = 0; j < nu; ++j) W.unl[bu + j] = coll_item(c, 0, 0, j);
+    }
   }
 }
 

@@ -64,7 +64,7 @@ class Pulse(ctypes.Structure):
     _fields_ = [("lam", ctypes.c_double), ("fwhm", ctypes.c_double),
                 ("fluence", ctypes.c_double), ("cep", ctypes.c_double),
                 ("t_peak", ctypes.c_double), ("pol", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("shape", ctypes.c_int), ("w0", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -176,6 +176,8 @@ def c_structs(cfg: dict):
     pl = cfg["pulse"]
     p.lam, p.fwhm, p.fluence = pl["lambda"], pl["fwhm"], pl["fluence"]
     p.cep, p.t_peak, p.pol = pl.get("cep", 0.0), pl["t_peak"], pl.get("pol", 0)
+    p.shape = 1 if pl.get("shape", "gauss") == "sin2" else 0
+    p.w0 = float(pl.get("w0", 0.0))
     return g, m, p, layers
 
 

@@ -37,14 +37,17 @@ def layer(z0, z1, material, ppc, temp_eV, **over):
     return d
 
 
-def pulse(fwhm, fluence_Jcm2, t_peak, cep=0.0, pol=0, lam=LAMBDA):
+def pulse(fwhm, fluence_Jcm2, t_peak, cep=0.0, pol=0, lam=LAMBDA, shape="gauss", w0=0.0):
+    """shape "gauss" or "sin2" (the paper's sine-squared pulse); w0 the spot
+    radius (0: plane wave)."""
     return {"lambda": lam, "fwhm": fwhm, "fluence": fluence_Jcm2 * 1e4,
-            "t_peak": t_peak, "cep": cep, "pol": pol}
+            "t_peak": t_peak, "cep": cep, "pol": pol, "shape": shape, "w0": w0}
 
 
 def grid(nx, ny, nz, d, layers, pls, seed, precision="fp32", cfl=0.95,
-         pool_factor=3.0, keldysh_terms=500, name="", imax_every=0):
-    return dict(name=name, nx=nx, ny=ny, nz=nz, dx=d, dy=d, dz=d, cfl=cfl,
+         pool_factor=3.0, keldysh_terms=500, name="", imax_every=0, dz=None):
+    """d: transverse (and, unless dz is given, longitudinal) cell size."""
+    return dict(name=name, nx=nx, ny=ny, nz=nz, dx=d, dy=d, dz=d if dz is None else dz, cfl=cfl,
                 layers=layers, pulse=pls, seed=int(seed),
                 precision=precision, pool_factor=pool_factor,
                 keldysh_terms=keldysh_terms, imax_every=imax_every)
@@ -211,3 +214,64 @@ def random_fields(cfg, seed, e_amp=1e10, b_amp=30.0, j_amp=0.0, p_amp=0.0):
     for c in (2, 3, 4, 8, 11, 14):  # Ez, Bx, By, Jz, Pz, Qz live on k+1/2
         F[c, nz] = 0.0
     return F
+
+
+# --------------------------------------------------------------------------
+# The paper's own geometry (Sec. 3): Table 1 materials with a static
+# permittivity (Sec. 2.3), 7 fs sine-squared pulse with a 4.65 um spot,
+# 40 nm transverse cells, 24 fs of simulated time.  The laser runs along z
+# here (the paper's y); x and y stay periodic where the paper has outflow
+# boundaries, and the paper's 1000 neutrals per cell are reduced to ppc.
+# --------------------------------------------------------------------------
+NA = 6.02214076e23
+SIO2_TABLE1 = dict(n_index=1.477, gap_eV=9.0, me_star=0.6, mh_star=8.0,
+                   n_mol=2.2e6 / 60.08 * NA, omega0_eV=math.inf, damping=0.0,
+                   mol_mass_amu=60.08, e_melt=5.7e9, e_boil=34.7e9, e_dissoc=54e9)
+HFO2_TABLE1 = dict(n_index=2.021, gap_eV=5.7, me_star=1.09, mh_star=1.12,
+                   n_mol=9.68e6 / 210.49 * NA, omega0_eV=math.inf, damping=0.0,
+                   mol_mass_amu=210.49, e_melt=10.7e9, e_boil=49.9e9, e_dissoc=54e9)
+T_SIN2_7FS = 7e-15 / (2.0 * math.acos(2.0 ** -0.25) / math.pi)  # full envelope duration
+
+
+def paper_pulse(fluence_Jcm2):
+    """7 fs FWHM sine-squared pulse, spot radius 4.65 um, starting at t = 0."""
+    return pulse(7e-15, fluence_Jcm2, 0.5 * T_SIN2_7FS, shape="sin2", w0=4.65e-6)
+
+
+def paper_steps(cfg, t_end=24e-15):
+    dt = cfg["cfl"] / (299792458.0 * math.sqrt(1 / cfg["dx"] ** 2 + 1 / cfg["dy"] ** 2 +
+                                               1 / cfg["dz"] ** 2))
+    return int(math.ceil(t_end / dt))
+
+
+def paper_silica(fluence_Jcm2=1.2, ppc=2, collisions=False, precision="fp32", seed=9):
+    """Bulk fused silica (Sec. 3.1, Fig. 1a): 9.6 um x 9.6 um at 40 nm, along
+    the laser 0.1 um of vacuum and 0.9 um of silica at 5 nm (plus the two-cell
+    outflow bands), 300 K."""
+    T300 = 300.0 * KB_EV_PER_K
+    cfg = grid(240, 240, 206, 40e-9, [layer(22, 202, SIO2_TABLE1, ppc, T300)],
+               paper_pulse(fluence_Jcm2), seed=seed, precision=precision, pool_factor=2.0,
+               dz=5e-9, name="paper-silica-240x240x206-5nm")
+    cfg["coll_every"] = 1 if collisions else 0
+    cfg["steps"] = paper_steps(cfg)
+    return cfg
+
+
+def paper_mirror(fluence_Jcm2=0.7, pairs=5, ppc=2, collisions=False, precision="fp32", seed=10):
+    """Quarter-wave mirror (Sec. 3.1, Fig. 1b/d): 13.8 nm cells along the laser,
+    0.1 um of vacuum, a lambda/(2n) SiO2 cap, then HfO2 / SiO2 quarter-wave
+    pairs (the pair count is not printed; five fill the paper's 1.533 um)."""
+    d = 13.8e-9
+    T300 = 300.0 * KB_EV_PER_K
+    z = 2 + int(round(0.1e-6 / d))
+    lay = [layer(z, z + layer_cells(SIO2_TABLE1["n_index"], 0.5, d), SIO2_TABLE1, ppc, T300)]
+    z = lay[-1]["z1"]
+    for _ in range(pairs):
+        for mat in (HFO2_TABLE1, SIO2_TABLE1):
+            lay.append(layer(z, z + layer_cells(mat["n_index"], 0.25, d), mat, ppc, T300))
+            z = lay[-1]["z1"]
+    cfg = grid(240, 240, z + 4, 40e-9, lay, paper_pulse(fluence_Jcm2), seed=seed,
+               precision=precision, pool_factor=2.0, dz=d, name=f"paper-mirror-{pairs}pairs")
+    cfg["coll_every"] = 1 if collisions else 0
+    cfg["steps"] = paper_steps(cfg)
+    return cfg

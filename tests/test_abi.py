@@ -61,6 +61,7 @@ def test_query_sizes(pic):
     (lambda c: c["layers"][0].update(omega0_eV=1.0), "pole below laser"),
     (lambda c: c["layers"].append(dict(c["layers"][0])), "overlap"),
     (lambda c: c["pulse"].update(fwhm=0.0), "pulse"),
+    (lambda c: c["pulse"].update(w0=-1e-6), "spot radius"),
     (lambda c: c["layers"][0].update(n_mol=-1.0), "density"),
 ])
 def test_query_rejects_invalid(pic, mutate, what):

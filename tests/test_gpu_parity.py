@@ -206,6 +206,28 @@ def test_hot_neutrals_crossing_faces(pic, oracle_mod, precision):
     assert o.scalars()["n_events"] > 50
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sine_squared_pulse_with_spot(pic, oracle_mod, precision):
+    """The paper's sine-squared pulse with a Gaussian spot on a static-eps
+    slab (Sec. 2.3, Sec. 3): fields and incident energy against the oracle."""
+    cfg = wl.grid(12, 12, 40, 20e-9, [wl.layer(12, 30, dict(wl.SILICA, omega0_eV=math.inf), 2,
+                                               0.025)],
+                  wl.pulse(7e-15, 3.0, 2e-15, shape="sin2", w0=80e-9), seed=23, precision="fp64")
+    o = oracle_mod.Sim(cfg)
+    g = pic.Simulation(dict(cfg, precision=precision))
+    o.step(120)
+    g.step(120)
+    assert o.scalars()["n_events"] > 0
+    Fg, Fo = g.fields(), o.fields()
+    assert np.abs(Fo[0]).max() > 0
+    tol = TOL64 if precision == "fp64" else TOL32
+    for sl in (slice(0, 3), slice(3, 6), slice(9, 12)):
+        assert rel_l2(Fg[sl], Fo[sl]) <= tol
+    assert g.diagnostics()["U_incident"] == pytest.approx(o.diagnostics()["U_incident"], rel=1e-14)
+    if precision == "fp64":
+        assert np.array_equal(g.material()["alive"], o.material()["alive"])
+
+
 def test_vacuum_box_matches(pic, oracle_mod):
     cfg = wl.vacuum_box(nx=4, ny=4, nz=48)
     g, o = _pair(pic, oracle_mod, cfg)
