@@ -424,8 +424,18 @@ def run_paper(args):
     c0 = cfg["nx"] // 2
     # centre of the spot, averaged over 6 x 6 nodes as the paper's profiles
     dmg = sim.damage([c0 - 3, c0 + 3, c0 - 3, c0 + 3])
-    diag = sim.diagnostics()
+    # electron spectrum of a (200 nm)^2 column through the first layer at
+    # the spot centre (the region of the paper's spectra, Sec. 4.3)
+    half = max(1, int(round(100e-9 / cfg["dx"])))
+    ly0 = cfg["layers"][0]
+    nb, emax = 400, 200.0
+    diag = sim.diagnostics(n_bins=nb, e_min_eV=0.0, e_max_eV=emax,
+                           region=[c0 - half, c0 + half, c0 - half, c0 + half, ly0["z0"], ly0["z1"]])
     t_job = time.perf_counter() - t0
+    import numpy as np
+    from paper_2502_13695_gb300.analysis import fit_chi2
+    spec = diag["spectrum"]
+    fit = fit_chi2(np.linspace(0.0, emax, nb + 1), spec) if spec.sum() > 0 else None
     ms = ev0.elapsed_time(ev1)
     info = sim.info()
     cells = cfg["nx"] * cfg["ny"] * cfg["nz"] * steps
@@ -445,7 +455,10 @@ def run_paper(args):
                        "pulse": "7 fs sine-squared, w0 4.65 um", "collisions_every": cfg.get("coll_every", 0)},
             "cell_updates_per_s": cells / (ms / 1e3), "time_to_result_s": t_job,
             "absorbed_fraction": diag["frac_absorbed"], "U_incident_J": diag["U_incident"],
-            "n_crit_m3": dmg["n_crit"], "layers": layers[:6]}
+            "n_crit_m3": dmg["n_crit"], "layers": layers[:6],
+            "spectrum_chi2_fit": None if fit is None else
+            {"k": fit["k"], "sigma_eV": fit["sigma"], "mean_eV": fit["mean"],
+             "region": "(200 nm)^2 x first layer at the spot centre"}}
     print(json.dumps(line), flush=True)
     sim.close()
 
