@@ -342,6 +342,51 @@ __device__ __forceinline__ void stv(R *p, const R *d) {
   }
 }
 
+// Fold |E|^2 / E0^2 at the V cell centres from point o into the intensity
+// map: each component is the mean of its four edge values around the centre.
+// Kept out of line and reloading its operands so that the B half step it is
+// called from keeps close to the register count (and occupancy) of the plain
+// step.
+template <int V, class R>
+__device__ __noinline__ void record_intensity(const R *ex0, const R *ey0, const R *ez0, R *imax,
+                                              long long o, long long oj, long long ov,
+                                              long long ojv, int nxy, R inv_e0sq) {
+  R a[V], b[V], c[V], d[V], a2[V];
+  ldv<V>(a, ex0 + o);
+  ldv<V>(b, ex0 + oj);
+  ldv<V>(c, ex0 + o + nxy);
+  ldv<V>(d, ex0 + oj + nxy);
+#pragma unroll
+  for (int l = 0; l < V; ++l) {
+    const R ax = R(0.25) * (((a[l] + b[l]) + c[l]) + d[l]);
+    a2[l] = ax * ax;
+  }
+  R e[V + 1], f[V + 1];
+  ldv<V>(e, ey0 + o);
+  e[V] = ey0[ov];
+  ldv<V>(f, ey0 + o + nxy);
+  f[V] = ey0[ov + nxy];
+#pragma unroll
+  for (int l = 0; l < V; ++l) {
+    const R ay = R(0.25) * (((e[l] + e[l + 1]) + f[l]) + f[l + 1]);
+    a2[l] += ay * ay;
+  }
+  ldv<V>(e, ez0 + o);
+  e[V] = ez0[ov];
+  ldv<V>(f, ez0 + oj);
+  f[V] = ez0[ojv];
+#pragma unroll
+  for (int l = 0; l < V; ++l) {
+    const R az = R(0.25) * (((e[l] + e[l + 1]) + f[l]) + f[l + 1]);
+    a2[l] = (a2[l] + az * az) * inv_e0sq;
+  }
+  R *const cell = imax + o;
+  ldv<V>(a, cell);
+#pragma unroll
+  for (int l = 0; l < V; ++l) a[l] = fmax(a[l], a2[l]);
+  stv<V>(cell, a);
+}
+
 // B half step (Faraday) on V points of plane blockIdx.y.  kRecord (the half
 // step after the E update): on the steps where the intensity map is
 // recorded, also fold |E^{n+1}|^2 / E0^2 at the V cell centres into it.
@@ -382,25 +427,9 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
     stv<V>(D.B[1] + o, b);
     if constexpr (kRecord) {
       const int every = D.imax_every;
-      if (every > 0 && ((unsigned)*D.step + 1u) % (unsigned)every == 0u) {
-        // cell-centred |E|: mean of the four edge values of each component
-        const long long ojv = (i + V == nx) ? oj + V - nx : oj + V;
-        R exjk[V], a2[V], im[V];
-        ldv<V>(exjk, D.E[0] + oj + nxy);
-        const R eyk_v = D.E[1][ov + nxy], ezj_v = D.E[2][ojv];
-#pragma unroll
-        for (int l = 0; l < V; ++l) {
-          const R ax = R(0.25) * (((ex[l] + exj[l]) + exk[l]) + exjk[l]);
-          const R ay = R(0.25) * (((ey[l] + ey[l + 1]) + eyk[l]) + (l + 1 < V ? eyk[l + 1] : eyk_v));
-          const R az = R(0.25) * (((ez[l] + ez[l + 1]) + ezj[l]) + (l + 1 < V ? ezj[l + 1] : ezj_v));
-          a2[l] = (ax * ax + ay * ay + az * az) * D.inv_e0sq;
-        }
-        R *const cell = D.imax + (long long)k * nxy + r;
-        ldv<V>(im, cell);
-#pragma unroll
-        for (int l = 0; l < V; ++l) im[l] = fmax(im[l], a2[l]);
-        stv<V>(cell, im);
-      }
+      if (every > 0 && ((unsigned)*D.step + 1u) % (unsigned)every == 0u)
+        record_intensity<V, R>(D.E[0], D.E[1], D.E[2], D.imax, o, oj, ov,
+                               (i + V == nx) ? oj + V - nx : oj + V, nxy, D.inv_e0sq);
     }
   }
 }
