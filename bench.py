@@ -124,7 +124,9 @@ class Clocks:
                 "samples": len(self.rows), "reasons": reasons}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """(rank, local rank, world size, torch.distributed or None) from the
+    torchrun environment; one process per GPU under NCCL (gloo: host only)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 0, 1, None
@@ -132,18 +134,48 @@ def dist_setup(n_gpus):
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
     local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
     return rank, local, ws, dist
 
 
 def allreduce(dist, x, op):
+    """All-reduce one float over the ranks (on the GPU under NCCL, on the
+    host under gloo); x itself with no process group."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def replica_seed(seed, rank):
+    """Seed of rank's independent replica of the workload."""
+    return seed + 7919 * rank
+
+
+def aggregate(dist, ms, psteps, events):
+    """Whole-job totals over the ranks: the slowest rank's time (ms) and the
+    particle steps and ionisation events summed; value = particle-steps/s of
+    all ranks together."""
+    ms_max = allreduce(dist, ms, _op(dist, "max"))
+    psteps_all = allreduce(dist, psteps, _op(dist, "sum"))
+    events_all = allreduce(dist, events, _op(dist, "sum"))
+    return {"ms_max": ms_max, "psteps_all": psteps_all, "events_all": events_all,
+            "value": psteps_all / (ms_max / 1e3)}
+
+
+def emit(line, rank):
+    """Rank 0 prints the JSON line; the other ranks print nothing."""
+    if rank != 0:
+        return False
+    print(json.dumps(line), flush=True)
+    return True
 
 
 # ---------------------------------------------------------------------------
@@ -209,7 +241,7 @@ def run_native(args, rank, local, world, dist):
     build.build()
     torch.cuda.set_device(local)
     cfg = wl.config2()
-    cfg["seed"] = cfg["seed"] + 7919 * rank  # independent replica per rank
+    cfg["seed"] = replica_seed(cfg["seed"], rank)  # independent replica per rank
     if args.pool_factor is not None:
         cfg["pool_factor"] = args.pool_factor
     if args.coll_every:
@@ -242,9 +274,8 @@ def run_native(args, rank, local, world, dist):
     psteps = i1["particle_steps"] - i0["particle_steps"]
     events = s1["n_events"] - s0["n_events"]
     launches = i1["launches"] - i0["launches"]
-    ms_max = allreduce(dist, ms, _op(dist, "max"))
-    psteps_all = allreduce(dist, psteps, _op(dist, "sum"))
-    events_all = allreduce(dist, events, _op(dist, "sum"))
+    agg = aggregate(dist, ms, psteps, events)
+    ms_max, psteps_all, events_all = agg["ms_max"], agg["psteps_all"], agg["events_all"]
     t = ms_max / 1e3
     ncell = cfg["nx"] * cfg["ny"] * cfg["nz"]
     cells_all = ncell * args.steps * world
@@ -283,7 +314,7 @@ def run_native(args, rank, local, world, dist):
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": psteps_all / t, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -315,7 +346,7 @@ def run_native(args, rank, local, world, dist):
         line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": info["cores"],
                                 "kind": "oracle", "sample": info["sample"],
                                 "cell_updates_per_s": cu}
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
 
 
 def run_scan(args):
