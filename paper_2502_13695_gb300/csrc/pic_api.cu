@@ -49,7 +49,7 @@ struct Plan {
   std::vector<int> lop, mplane, kplane;
   int nb_scan, diag_blocks_p, diag_blocks_g;
   // arena offsets
-  size_t off_E[3], off_B[3], off_J4, off_P[3], off_Q[3];
+  size_t off_E[3], off_B[3], off_Bh[3], off_J4, off_P[3], off_Q[3];
   size_t off_lop, off_mplane, off_kplane, off_lk, off_lr;
   size_t off_win, off_pm, off_eamp, off_ckey, off_T, off_alive, off_leave;
   size_t off_pc[2], off_po[2][3], off_pu[2][3], off_pt[2], off_pid[2];
@@ -152,6 +152,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   const size_t R = P.rsz;
   for (int d = 0; d < 3; ++d) P.off_E[d] = take(P.nfield * R);
   for (int d = 0; d < 3; ++d) P.off_B[d] = take(P.nfield * R);
+  for (int d = 0; d < 3; ++d) P.off_Bh[d] = take(P.nfield * R);
   P.off_J4 = take(P.nfield * 4 * R);
   for (int d = 0; d < 3; ++d) P.off_P[d] = take(P.nmat * R);
   for (int d = 0; d < 3; ++d) P.off_Q[d] = take(P.nmat * R);
@@ -318,6 +319,9 @@ struct pic_ctx {
   int push_blocks = 0;                      // resident blocks of k_push on this device
   int coll_blocks = 0;                      // resident blocks of k_collide
   int field_v = 1;  // x points per thread of the field and window kernels
+  // Bh = B - (dt/2) curl E holds (B^{n+1/2} from B^n, E^n): set by each
+  // field pass, cleared when the host writes E or B
+  bool bh_valid = false;
   // profiling: (class, start, stop) event triples, reused across reads
   bool profiling = false;
   struct Rec {
@@ -382,6 +386,7 @@ void bind(pic_ctx *h) {
   for (int d = 0; d < 3; ++d) {
     D.E[d] = (R *)(A + P.off_E[d]);
     D.B[d] = (R *)(A + P.off_B[d]);
+    D.Bh[d] = (R *)(A + P.off_Bh[d]);
     D.P[d] = (R *)(A + P.off_P[d]);
     D.Q[d] = (R *)(A + P.off_Q[d]);
   }
@@ -478,6 +483,30 @@ int sort_pool(pic_ctx *h) {
   return PIC_OK;
 }
 
+// Bh = B - (dt/2) curl E from the current fields, unless the last field
+// pass left it valid (nothing but the host writes E or B between passes).
+template <class R>
+int prime_bh(pic_ctx *h) {
+  if (h->bh_valid) return PIC_OK;
+  const Plan &P = h->P;
+  Ctx<R> &X = ctx_of<R>(h);
+  cudaStream_t s = h->stream;
+  if constexpr (sizeof(R) == 4) {
+    if (h->field_v == 4) {
+      const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
+      k_bstep<4, kPrime, R><<<grid, kThreads, 0, s>>>(X.d);
+    }
+  }
+  if (h->field_v == 1) {
+    const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
+    k_bstep<1, kPrime, R><<<grid, kThreads, 0, s>>>(X.d);
+  }
+  PIC_CUDA(cudaGetLastError());
+  h->launches += 1;
+  h->bh_valid = true;
+  return PIC_OK;
+}
+
 template <class R>
 int enqueue(pic_ctx *h, int mask) {
   Ctx<R> &X = ctx_of<R>(h);
@@ -522,22 +551,23 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (mask & PIC_PHASE_FIELDS) {
     prof_begin(h, PIC_PROF_FIELDS);
+    const int rp = prime_bh<R>(h);
+    if (rp) return rp;
     if constexpr (sizeof(R) == 4) {
       if (h->field_v == 4) {
         const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
-        k_bhalf<4, false, R><<<grid, kThreads, 0, s>>>(X.d);
         k_efull<4, R><<<grid, kThreads, 0, s>>>(X);
-        k_bhalf<4, true, R><<<grid, kThreads, 0, s>>>(X.d);
+        k_bstep<4, kFullRecord, R><<<grid, kThreads, 0, s>>>(X.d);
       }
     }
     if (h->field_v == 1) {
       const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
-      k_bhalf<1, false, R><<<grid, kThreads, 0, s>>>(X.d);
       k_efull<1, R><<<grid, kThreads, 0, s>>>(X);
-      k_bhalf<1, true, R><<<grid, kThreads, 0, s>>>(X.d);
+      k_bstep<1, kFullRecord, R><<<grid, kThreads, 0, s>>>(X.d);
     }
     prof_end(h);
-    h->launches += 3;
+    h->launches += 2;
+    h->bh_valid = true;
   }
   if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
     prof_begin(h, PIC_PROF_WINDOW);
@@ -772,6 +802,11 @@ int batch_capture(pic_batch_ctx *b) {
     b->exec = nullptr;
   }
   cudaStream_t s = b->stream;
+  // Bh is made valid outside the graph, so that replays do not recompute it
+  for (pic_ctx *h : b->m) {
+    const int rp = h->fp64 ? prime_bh<double>(h) : prime_bh<float>(h);
+    if (rp) return rp;
+  }
   std::vector<long long> l0;
   for (pic_ctx *h : b->m) l0.push_back(h->launches);
   if (const int rj = join_members_into_batch(b)) return rj;
@@ -1431,6 +1466,7 @@ int pic_get_fields(pic_handle h, double *dst) {
 int pic_set_fields(pic_handle h, const double *src) {
   if (!h || !src) return fail(PIC_EINVAL, "null pointer");
   PIC_CUDA(cudaStreamSynchronize(h->stream));
+  h->bh_valid = false;  // the next field pass recomputes Bh from the new E, B
   return h->fp64 ? set_fields_t<double>(h, src) : set_fields_t<float>(h, src);
 }
 

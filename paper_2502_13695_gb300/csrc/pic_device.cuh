@@ -59,9 +59,9 @@ struct Dev {
   int shape;             // 0 Gaussian, 1 sine-squared envelope
   double Tsin2;          // full duration of the sine-squared field envelope
   double w0, xc, yc;     // spot radius (0: plane wave) and centre
-  // fields: nfield each (E, B), J interleaved (Jx, Jy, Jz, 0) per point,
-  // nmat each (P, Q)
-  R *E[3], *B[3], *J4, *P[3], *Q[3];
+  // fields: nfield each (E, B at integer time, Bh at the next half time),
+  // J interleaved (Jx, Jy, Jz, 0) per point, nmat each (P, Q)
+  R *E[3], *B[3], *Bh[3], *J4, *P[3], *Q[3];
   const int *layer_of_plane;      // nz, -1 vacuum
   const int *mplane;              // nz, -1 vacuum
   const int *kplane;              // n_mplanes: z plane of material plane

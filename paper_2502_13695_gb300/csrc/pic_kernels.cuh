@@ -1,6 +1,6 @@
 // Kernels of one PIC step on sm_103a.  Every step of the hot path runs here:
 //   k_push      gather (TSC) + relativistic Boris + move + Esirkepov deposit
-//   k_bhalf     B half step (Faraday)
+//   k_bstep     B half steps (Faraday): B and Bh around the particle phase
 //   k_efull     E step with the Lorentz polarisation current (trapezoidal
 //               oscillator), Silver-Mueller z faces with the laser source,
 //               Joule work, J cleared
@@ -399,11 +399,38 @@ __device__ __noinline__ void record_intensity(const R *ex0, const R *ey0, const 
   stv<V>(cell, a);
 }
 
-// B half step (Faraday) on V points of plane blockIdx.y.  kRecord (the half
-// step after the E update): on the steps where the intensity map is
-// recorded, also fold |E^{n+1}|^2 / E0^2 at the V cell centres into it.
-template <int V, bool kRecord, class R>
-__global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
+// Faraday half steps on V points of plane blockIdx.y, t = curl E / 2 dt.
+// Both half steps of B around the particle phase use the same E: the one
+// after the E update (B^{n+1} = B^{n+1/2} - t) and the one that opens the
+// next step (B^{n+3/2} = B^{n+1} - t).  So a field pass keeps B at integer
+// time (read by the push and the diagnostics) and Bh at the next half time
+// (read by the E update), and kFull computes both from Bh and E^{n+1} in one
+// pass, each rounded as two separate half steps would be.  kPrime sets Bh =
+// B - t from the current B and E (at creation, and after the host has
+// written the fields).  kRecord (with kFull): on the steps where the
+// intensity map is recorded, also fold |E^{n+1}|^2 / E0^2 at the V cell
+// centres into it.
+enum { kPrime = 0, kFull = 1, kFullRecord = 2 };
+
+template <int V, int kMode, class R>
+__device__ __forceinline__ void b_out(const Dev<R> &D, int d, long long o, const R *t) {
+  const R h = R(0.5) * D.dt;
+  R b[V];
+  ldv<V>(b, (kMode == kPrime ? D.B[d] : D.Bh[d]) + o);
+#pragma unroll
+  for (int l = 0; l < V; ++l) b[l] -= h * t[l];
+  if constexpr (kMode == kPrime) {
+    stv<V>(D.Bh[d] + o, b);
+  } else {
+    stv<V>(D.B[d] + o, b);
+#pragma unroll
+    for (int l = 0; l < V; ++l) b[l] -= h * t[l];
+    stv<V>(D.Bh[d] + o, b);
+  }
+}
+
+template <int V, int kMode, class R>
+__global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (r >= nxy) return;
@@ -412,16 +439,14 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
   const long long o = (long long)k * nxy + r;
   const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
   const long long ov = (i + V == nx) ? o + V - nx : o + V;  // x + 1 of the last point
-  const R h = R(0.5) * D.dt;
-  R ex[V], ey[V + 1], exj[V], b[V];
+  R ex[V], ey[V + 1], exj[V], t[V];
   ldv<V>(ex, D.E[0] + o);
   ldv<V>(ey, D.E[1] + o);
   ey[V] = D.E[1][ov];
   ldv<V>(exj, D.E[0] + oj);
-  ldv<V>(b, D.B[2] + o);
 #pragma unroll
-  for (int l = 0; l < V; ++l) b[l] -= h * ((ey[l + 1] - ey[l]) * D.idx - (exj[l] - ex[l]) * D.idy);
-  stv<V>(D.B[2] + o, b);
+  for (int l = 0; l < V; ++l) t[l] = (ey[l + 1] - ey[l]) * D.idx - (exj[l] - ex[l]) * D.idy;
+  b_out<V, kMode>(D, 2, o, t);
   if (k < D.nz) {
     R ez[V + 1], ezj[V], eyk[V], exk[V];
     ldv<V>(ez, D.E[2] + o);
@@ -429,15 +454,13 @@ __global__ void __launch_bounds__(256) k_bhalf(Dev<R> D) {
     ldv<V>(ezj, D.E[2] + oj);
     ldv<V>(eyk, D.E[1] + o + nxy);
     ldv<V>(exk, D.E[0] + o + nxy);
-    ldv<V>(b, D.B[0] + o);
 #pragma unroll
-    for (int l = 0; l < V; ++l) b[l] -= h * ((ezj[l] - ez[l]) * D.idy - (eyk[l] - ey[l]) * D.idz);
-    stv<V>(D.B[0] + o, b);
-    ldv<V>(b, D.B[1] + o);
+    for (int l = 0; l < V; ++l) t[l] = (ezj[l] - ez[l]) * D.idy - (eyk[l] - ey[l]) * D.idz;
+    b_out<V, kMode>(D, 0, o, t);
 #pragma unroll
-    for (int l = 0; l < V; ++l) b[l] -= h * ((exk[l] - ex[l]) * D.idz - (ez[l + 1] - ez[l]) * D.idx);
-    stv<V>(D.B[1] + o, b);
-    if constexpr (kRecord) {
+    for (int l = 0; l < V; ++l) t[l] = (exk[l] - ex[l]) * D.idz - (ez[l + 1] - ez[l]) * D.idx;
+    b_out<V, kMode>(D, 1, o, t);
+    if constexpr (kMode == kFullRecord) {
       const int every = D.imax_every;
       if (every > 0 && ((unsigned)*D.step + 1u) % (unsigned)every == 0u)
         record_intensity<V, R>(D.E[0], D.E[1], D.E[2], D.imax, o, oj, ov,
@@ -495,8 +518,8 @@ __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) 
   return e0 + a - dp;
 }
 
-// E step on V points of plane blockIdx.y: Ampere with J and the polarisation
-// current, Silver-Mueller faces at k = 0 (with the incident field) and k = nz,
+// E step on V points of plane blockIdx.y: Ampere with B^{n+1/2} (Bh), J and
+// the polarisation current, Silver-Mueller faces at k = 0 (with the incident field) and k = nz,
 // Joule work J.(E^n + E^{n+1})/2, J cleared for the next deposit.  Three
 // blocks per SM (80 registers) measured faster than two at 100 registers.
 template <int V, class R>
@@ -514,11 +537,11 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
     const R c2dt = D.c2dt, dtie = R(D.dt_d / kEps0);
     // bz[0] is the x - 1 neighbour of the first point, bz[1..V] the points
     R bz[V + 1], bzj[V], bx[V], by[V];
-    bz[0] = D.B[2][omv];
-    ldv<V>(bz + 1, D.B[2] + o);
-    ldv<V>(bzj, D.B[2] + omj);
-    ldv<V>(bx, D.B[0] + o);
-    ldv<V>(by, D.B[1] + o);
+    bz[0] = D.Bh[2][omv];
+    ldv<V>(bz + 1, D.Bh[2] + o);
+    ldv<V>(bzj, D.Bh[2] + omj);
+    ldv<V>(bx, D.Bh[0] + o);
+    ldv<V>(by, D.Bh[1] + o);
     R jx[V], jy[V], jz[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) load_j3(D.J4 + 4 * (o + l), jx[l], jy[l], jz[l]);
@@ -564,8 +587,8 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
         }
       } else {
         R bxm[V], bym[V];
-        ldv<V>(bxm, D.B[0] + o - nxy);
-        ldv<V>(bym, D.B[1] + o - nxy);
+        ldv<V>(bxm, D.Bh[0] + o - nxy);
+        ldv<V>(bym, D.Bh[1] + o - nxy);
 #pragma unroll
         for (int l = 0; l < V; ++l) {
           ex1[l] = ((R(1) - al) * ex0[l] + R(2) * al * cc * bym[l] +
@@ -576,8 +599,8 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
       }
     } else {
       R bxm[V], bym[V], ax[V], ay[V];
-      ldv<V>(bxm, D.B[0] + o - nxy);
-      ldv<V>(bym, D.B[1] + o - nxy);
+      ldv<V>(bxm, D.Bh[0] + o - nxy);
+      ldv<V>(bym, D.Bh[1] + o - nxy);
 #pragma unroll
       for (int l = 0; l < V; ++l) {
         ax[l] = c2dt * (dBz_dy[l] - (by[l] - bym[l]) * D.idz) - dtie * jx[l];
@@ -616,8 +639,8 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
     stv<V>(D.E[1] + o, ey1);
     if (k < nz) {
       R bxj[V], ez0[V], ez1[V], az[V];
-      const R byp = D.B[1][omv];
-      ldv<V>(bxj, D.B[0] + omj);
+      const R byp = D.Bh[1][omv];
+      ldv<V>(bxj, D.Bh[0] + omj);
       ldv<V>(ez0, D.E[2] + o);
 #pragma unroll
       for (int l = 0; l < V; ++l)
