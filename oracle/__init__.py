@@ -124,6 +124,7 @@ def lib():
             L.or_rho.argtypes = [vp, vp]
             L.or_incident.restype = d
             L.or_incident.argtypes = [vp, d]
+            L.or_cell_threshold.argtypes = [vp, i, d, vp, vp]
             L.or_philox.argtypes = [vp, vp, vp]
             L.or_damage.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_damage.restype = d
@@ -388,6 +389,14 @@ class Sim:
 
     def incident(self, t: float) -> float:
         return lib().or_incident(self._h, float(t))
+
+    def threshold(self, layer: int, E: float) -> int:
+        """Ionisation threshold T = floor(p 2^64) of a cell of this layer at
+        window amplitude E (2^64 - 1 when p reaches 1)."""
+        T = np.zeros(1, dtype=np.uint64)
+        a = np.zeros(1, dtype=np.int32)
+        lib().or_cell_threshold(self._h, int(layer), float(E), _ptr(T), _ptr(a))
+        return (1 << 64) - 1 if a[0] else int(T[0])
 
     def spot(self, x: float, y: float) -> float:
         return lib().or_spot(self._h, float(x), float(y))

@@ -1470,3 +1470,13 @@ void or_set_scalars(or_sim *s, long step, const double in[4]) {
 
 /* Incident field value, for the boundary tests. */
 double or_incident(const or_sim *s, double t) { return e_inc(s, t); }
+
+/* Ionisation threshold of a cell of layer L at window amplitude E: the rate
+ * and the threshold exactly as the window/Keldysh pass computes them (for
+ * item-by-item checks of a larger run's thresholds). */
+void or_cell_threshold(const or_sim *s, int L, double E, uint64_t *T, int *always) {
+  uint8_t a = 0;
+  double W = or_keldysh_W(E, s->omega, s->gapJ[L], s->mstar[L], s->cfg.keldysh_terms, NULL);
+  ion_threshold(W, s->cfg.layers[L].n_mol, s->dt, T, &a);
+  *always = a;
+}

@@ -916,22 +916,27 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
   const bool active = r < D.nxy;
   const long long step = *D.step;
   uint32_t alive = 0, ion = 0;
-  int i = 0, j = 0, k = 0, L = 0;
+  int i = 0, j = 0;
+  const int k = D.kplane[mp], L = D.layer_of_plane[k];
   uint32_t c = 0;
   R t1 = R(0);
-  if (active) alive = D.alive[m];
+  // the cell's three words are loaded together (one round trip)
+  unsigned long long Town = 0;
+  uint32_t leave = 0;
+  if (active) {
+    alive = D.alive[m];
+    Town = D.T[m];
+    leave = D.leave_step[m];
+  }
   if (alive) {
     const int nx = D.nx, nxy = D.nxy;
     j = r / nx;
     i = r - j * nx;
-    k = D.kplane[mp];
-    L = D.layer_of_plane[k];
     c = (uint32_t)((long long)k * nxy + r);
-    const unsigned long long Town = D.T[m];
     // neutrals that may have left the birth cell by t^{n+1}: their own
     // leave step (64-step units, rounded down) has been reached
     uint32_t exc = 0;
-    if ((unsigned long long)(step + 1) >= (unsigned long long)D.leave_step[m]) {
+    if ((unsigned long long)(step + 1) >= (unsigned long long)leave) {
       const uint16_t *ls = X.leave16 + m * X.ppc_max;
       for (uint32_t bits = alive; bits; bits &= bits - 1) {
         const uint32_t s = __ffs(bits) - 1;
@@ -981,7 +986,8 @@ __global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
       if (ionises(ion_h16(w, s), Tuse, D.seed, (uint32_t)step, c, s)) ion |= 1u << s;
     }
   }
-  // warp-aggregated reservation of pool slots
+  // warp-aggregated reservation of pool slots (most warps ionise nothing)
+  if (__ballot_sync(0xffffffffu, ion != 0u) == 0u) return;
   const int npair = __popc(ion);
   int incl = npair;
   const int lane = threadIdx.x & 31;

@@ -1,0 +1,194 @@
+"""Parity at the bench workload's full size: bulk silica 128 x 128 x 512 in
+FP32, in the launch configuration bench.py times.  The oracle cannot step
+8.4 M cells and 46 M neutrals in seconds, so the outputs are checked on what
+it can compute item by item:
+
+* before the first ionisation the workload is uniform across the transverse
+  plane: every (x, y) column of E, B, P, Q is bitwise the same, and equals
+  the oracle's 4 x 4 column of the same workload stepped as long;
+* one step from the state at step 705 (2.5 M charged particles), phase by
+  phase, against the oracle on a 16 x 16 column cut from the full grid:
+  every particle whose stencils lie inside the cut (its push), the current
+  deposited on the nodes only those particles reach, and the field pass on
+  the nodes whose stencils lie inside the cut;
+* for sampled material cells of the full grid, the ionisation threshold
+  against the oracle's Keldysh rate at the GPU's own window amplitude, and
+  every draw of those cells against the oracle's Philox uniform and the
+  GPU's threshold (the decision is an integer comparison, taken on the
+  kernel's FP32 threshold).
+"""
+import numpy as np
+import pytest
+
+from paper_2502_13695_gb300 import workloads as wl
+from parity_util import COMP, positions, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5          # FP32 per step (fields, current)
+TOL_RUN = 1e-3        # FP32 after S_PRE steps from the same initial state
+S_PRE = 350           # the pulse is in the slab, no pair created yet
+STEP = 705            # the bench's timed region starts here
+W = 16                # transverse size of the cut column
+I0, J0 = 40, 72       # its corner in the full grid
+
+
+@pytest.fixture(scope="module")
+def pic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2502_13695_gb300 import build, pic as picmod
+    build.build()
+    return picmod
+
+
+def _cut(F):
+    return np.ascontiguousarray(F[:, :, J0:J0 + W, I0:I0 + W])
+
+
+def test_uniform_columns_before_ionisation(pic, oracle_mod):
+    cfg = wl.config2()
+    g = pic.Simulation(cfg)
+    g.step(S_PRE)
+    g.sync()
+    assert g.info()["n_particles"] == 0, "a pair was created before the comparison step"
+    F = g.fields()
+    g.close()
+    o = oracle_mod.Sim(dict(cfg, nx=4, ny=4))
+    o.step(S_PRE)
+    assert o.np == 0
+    Fo = o.fields()
+    assert np.abs(F[9]).max() > 0.0, "the pulse has not reached the slab"
+    for c in (0, 1, 2, 3, 4, 5, 9, 10, 11, 12, 13, 14):
+        col = F[c][:, :1, :1]
+        assert np.array_equal(F[c], np.broadcast_to(col, F[c].shape)), \
+            f"{COMP[c]} differs between transverse columns"
+    assert not np.any(F[6:9]), "current without particles"
+    for name, sl in (("E", slice(0, 3)), ("B", slice(3, 6)), ("P", slice(9, 12)),
+                     ("Q", slice(12, 15))):
+        err = rel_l2(F[sl, :, 0, 0], Fo[sl, :, 0, 0])
+        print(f"column after {S_PRE} steps: {name} rel-L2 {err:.2e}")
+        assert err <= TOL_RUN, (name, err)
+
+
+def _particles_in_cut(P, nx, ny):
+    c = P["cell"].astype(np.int64)
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    inside = (i >= I0) & (i < I0 + W) & (j >= J0) & (j < J0 + W)
+    sub = {key: v[inside] for key, v in P.items()}
+    sub["cell"] = ((k[inside] * W + (j[inside] - J0)) * W + (i[inside] - I0)).astype(np.int32)
+    return sub
+
+
+def _interior_ids(sub, lo, hi):
+    c = sub["cell"].astype(np.int64)
+    i, j = c % W, (c // W) % W
+    keep = (i >= lo) & (i <= hi) & (j >= lo) & (j <= hi)
+    return sub["id"][keep]
+
+
+def test_one_step_at_full_size(pic, oracle_mod):
+    cfg = wl.config2()
+    nx, ny, nxy = cfg["nx"], cfg["ny"], cfg["nx"] * cfg["ny"]
+    g = pic.Simulation(cfg)
+    g.step(STEP)
+    g.sync()
+    sc = g.scalars()
+    n = sc["step"]
+    P0 = g.particles()
+    assert len(P0["id"]) > 1_000_000
+    F0 = _cut(g.fields())
+    M0 = g.material()
+    g.phases(pic.PHASE_PARTICLES)
+    P1 = g.particles()
+    F1 = _cut(g.fields())
+    g.phases(pic.PHASE_FIELDS)
+    F2 = _cut(g.fields())
+    g.phases(pic.PHASE_WINDOW | pic.PHASE_IONIZE)
+    M2 = g.material()
+    g.close()
+
+    # ---- push and deposit on the cut column --------------------------------
+    sub = _particles_in_cut(P0, nx, ny)
+    o = oracle_mod.Sim(dict(cfg, nx=W, ny=W))
+    o.set_scalars(n, sc["U_joule"], sc["N_pairs"], sc["U_ion"], sc["n_events"])
+    o.set_fields(F0)
+    o.set_particles(sub)
+    o.phases(pic.PHASE_PARTICLES)
+    Po = o.particles()
+    ids = _interior_ids(sub, 2, W - 3)  # gather and deposit stencils inside the cut
+    assert len(ids) > 10_000
+    sel_o = np.isin(Po["id"], ids)
+    sel_g = np.isin(P1["id"], ids)
+    assert np.array_equal(Po["id"][sel_o], P1["id"][sel_g]), "different particles left the grid"
+    pg = {k: v[sel_g] for k, v in P1.items()}
+    po = {k: v[sel_o] for k, v in Po.items()}
+    xg = positions(pg, nx, ny)
+    xo = positions(po, W, W) + np.array([I0, J0, 0])
+    ex = np.max(np.abs(xg - xo))
+    eu = np.max(np.abs(pg["u"] - po["u"])) / np.max(np.abs(po["u"]))
+    print(f"push of {len(ids)} particles: position {ex:.2e} cells, momentum {eu:.2e}")
+    assert ex <= 1e-5, ex
+    assert eu <= 1e-5, eu
+    assert np.array_equal(pg["tag"], po["tag"])
+    Fo1 = o.fields()
+    inner = (slice(None), slice(None), slice(4, W - 4), slice(4, W - 4))
+    for c in (6, 7, 8):  # nodes only particles inside the cut reach
+        err = rel_l2(F1[c][inner[1:]], Fo1[c][inner[1:]])
+        print(f"deposit {COMP[c]} rel-L2 {err:.2e}")
+        assert err <= TOL32, (COMP[c], err)
+    assert np.abs(F1[6][inner[1:]]).max() > 0.0
+
+    # ---- field pass on the cut column ---------------------------------------
+    o.set_fields(F1)
+    o.phases(pic.PHASE_FIELDS)
+    Fo2 = o.fields()
+    core = (slice(None), slice(3, W - 3), slice(3, W - 3))
+    for name, comps in (("E", (0, 1, 2)), ("B", (3, 4, 5)), ("P", (9, 10, 11)),
+                        ("Q", (12, 13, 14))):
+        a = np.stack([F2[c][core] for c in comps])
+        b = np.stack([Fo2[c][core] for c in comps])
+        err = rel_l2(a, b)
+        print(f"field pass {name} rel-L2 {err:.2e}")
+        assert err <= TOL32, (name, err)
+
+    # ---- thresholds and draws of sampled cells ------------------------------
+    ref = oracle_mod.Sim(dict(cfg, nx=4, ny=4))
+    rng = np.random.default_rng(705)
+    T = M2["T"]
+    hot = np.flatnonzero(T > 0)
+    assert len(hot) > 1000
+    cold = np.flatnonzero(T == 0)
+    cells = np.concatenate([rng.choice(hot, 3000, replace=False),
+                            rng.choice(cold, min(500, len(cold)), replace=False)])
+    worst = 0.0
+    for m in cells:
+        Tg = int(T[m])
+        To = ref.threshold(0, float(M2["eamp"][m]))
+        if Tg == 0 or To == 0:
+            assert max(Tg, To) < 2**40, (m, Tg, To)  # both at the edge of the skip amplitude
+            continue
+        worst = max(worst, abs(Tg - To) / To)
+    print(f"thresholds of {len(cells)} cells: worst relative difference {worst:.2e}")
+    assert worst <= 1e-3, worst
+    k0 = cfg["layers"][0]["z0"]
+    draws = flips = ionised = 0
+    for m in cells:
+        a0, a2, Tg = int(M0["alive"][m]), int(M2["alive"][m]), int(T[m])
+        mp, r = divmod(int(m), nxy)
+        c = (k0 + mp) * nxy + r
+        for s in range(32):
+            if not (a0 >> s) & 1:
+                continue
+            draws += 1
+            u = oracle_mod.ion_uniform(cfg["seed"], n, c, s)
+            ion = Tg == (1 << 64) - 1 or u < Tg
+            ionised += ion
+            flips += ion != (not (a2 >> s) & 1)
+    print(f"draws {draws}, ionised {ionised}, decisions that differ {flips}")
+    assert draws > 10_000
+    assert ionised > 0
+    # a neutral that has crossed into a neighbour draws against that cell's
+    # threshold; at 300 K that takes a birth offset within ~1e-4 of a face
+    assert flips <= 2 + 1e-4 * draws, (flips, draws)

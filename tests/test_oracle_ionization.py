@@ -180,3 +180,22 @@ def test_ion_uniform_is_uniform_and_independent(oracle_mod):
     assert len({oracle_mod.ion_uniform(1, 2, 3, s) for s in range(32)}) == 32
     assert oracle_mod.ion_uniform(1, 2, 3, 4) != oracle_mod.ion_uniform(1, 3, 3, 4)
     assert oracle_mod.ion_uniform(1, 2, 3, 4) != oracle_mod.ion_uniform(1, 2, 4, 4)
+
+
+def test_cell_threshold_is_the_pass_threshold(oracle_mod):
+    """Sim.threshold(L, E) (for item-by-item checks of large runs) gives, at
+    each cell's window amplitude, the threshold the window/Keldysh pass stored
+    for that cell, hot cells included; it rises with the amplitude."""
+    from paper_2502_13695_gb300 import workloads as wl
+    s = oracle_mod.Sim(wl.small_slab(nx=4, ny=4))
+    s.step(40)
+    mat = s.material()
+    hot = 0
+    for m in range(len(mat["eamp"])):
+        want = (1 << 64) - 1 if mat["Talways"][m] else int(mat["T"][m])
+        assert s.threshold(0, float(mat["eamp"][m])) == want
+        hot += want > 0
+    assert hot > 0
+    e = float(np.max(mat["eamp"]))
+    assert s.threshold(0, 0.5 * e) <= s.threshold(0, e) <= s.threshold(0, 2.0 * e)
+    assert s.threshold(0, 0.0) == 0
