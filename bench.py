@@ -233,6 +233,13 @@ ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
     "sort": ("particle", 80.0),
     "collide": ("particle", 36.0),  # momentum read + write 24, tag 4, id 8
 }
+# what bounds each kernel class in practice, as measured (ncu counters and
+# timing experiments), where it is not DRAM bandwidth
+LIMITER = {
+    "push": "issue rate of the deposit's ~26 global vector reductions per particle",
+    "keldysh": "FP32 issue (series of Dawson terms)",
+    "ionize": "integer issue (Philox draws)",
+}
 
 
 def run_native(args, rank, local, world, dist):
@@ -330,7 +337,8 @@ def run_native(args, rank, local, world, dist):
         "charged_particles": [i0["n_particles"], i1["n_particles"]],
         "ionisation_events": events,
         "per_kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": dom, "bound": "hbm", "limiter": LIMITER.get(dom, "DRAM bandwidth"),
+                     "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "bytes_per_launch": bytes_launch,
                      "unit_of_work": unit_name, "per_unit_bytes": per_unit,

@@ -894,14 +894,17 @@ __device__ __forceinline__ bool ionises(uint32_t h16, unsigned long long T, unsi
 // when its low 48 bits must decide.
 __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32_t &lt,
                                              uint32_t &eq) {
+  // two halves per instruction: __vcmpltu2 / __vcmpeq2 set a halfword to
+  // 0xFFFF where the unsigned comparison holds
   const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+  const uint32_t th2 = th | (th << 16);
   lt = 0;
   eq = 0;
 #pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const uint32_t h = (t & 1) ? (v[t >> 1] >> 16) : (v[t >> 1] & 0xFFFFu);
-    lt |= (uint32_t)(h < th) << t;
-    eq |= (uint32_t)(h == th) << t;
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t l = __vcmpltu2(v[q], th2), e = __vcmpeq2(v[q], th2);
+    lt |= ((l & 1u) | ((l >> 15) & 2u)) << (2 * q);
+    eq |= ((e & 1u) | ((e >> 15) & 2u)) << (2 * q);
   }
 }
 

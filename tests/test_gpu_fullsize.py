@@ -26,7 +26,7 @@ from parity_util import COMP, positions, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL32 = 2e-5          # FP32 per step (fields, current)
-TOL_RUN = 1e-3        # FP32 after S_PRE steps from the same initial state
+TOL_RUN = 1e-5        # FP32 after S_PRE steps from the same state (measured ~1e-6)
 S_PRE = 350           # the pulse is in the slab, no pair created yet
 STEP = 705            # the bench's timed region starts here
 W = 16                # transverse size of the cut column
@@ -129,16 +129,19 @@ def test_one_step_at_full_size(pic, oracle_mod):
     ex = np.max(np.abs(xg - xo))
     eu = np.max(np.abs(pg["u"] - po["u"])) / np.max(np.abs(po["u"]))
     print(f"push of {len(ids)} particles: position {ex:.2e} cells, momentum {eu:.2e}")
-    assert ex <= 1e-5, ex
-    assert eu <= 1e-5, eu
+    assert ex <= 1e-6, ex
+    assert eu <= 1e-6, eu
     assert np.array_equal(pg["tag"], po["tag"])
     Fo1 = o.fields()
-    inner = (slice(None), slice(None), slice(4, W - 4), slice(4, W - 4))
-    for c in (6, 7, 8):  # nodes only particles inside the cut reach
-        err = rel_l2(F1[c][inner[1:]], Fo1[c][inner[1:]])
+    # the current is a difference of shape weights at the old and new
+    # positions (moves of ~1e-3 cells), so its FP32 rounding relative to the
+    # current is about eps32 / move, near 1e-5 here: within the FP32 bound
+    inner = (slice(None), slice(4, W - 4), slice(4, W - 4))  # nodes only the cut's particles reach
+    for c in (6, 7, 8):
+        err = rel_l2(F1[c][inner], Fo1[c][inner])
         print(f"deposit {COMP[c]} rel-L2 {err:.2e}")
         assert err <= TOL32, (COMP[c], err)
-    assert np.abs(F1[6][inner[1:]]).max() > 0.0
+    assert np.abs(F1[6][inner]).max() > 0.0
 
     # ---- field pass on the cut column ---------------------------------------
     o.set_fields(F1)
@@ -160,8 +163,11 @@ def test_one_step_at_full_size(pic, oracle_mod):
     hot = np.flatnonzero(T > 0)
     assert len(hot) > 1000
     cold = np.flatnonzero(T == 0)
-    cells = np.concatenate([rng.choice(hot, 3000, replace=False),
-                            rng.choice(cold, min(500, len(cold)), replace=False)])
+    # every cell with an event this step, and random hot and cold ones
+    changed = np.flatnonzero(M0["alive"] != M2["alive"])
+    assert len(changed) > 50
+    cells = np.unique(np.concatenate([changed, rng.choice(hot, 3000, replace=False),
+                                      rng.choice(cold, min(500, len(cold)), replace=False)]))
     worst = 0.0
     for m in cells:
         Tg = int(T[m])
@@ -188,7 +194,7 @@ def test_one_step_at_full_size(pic, oracle_mod):
             flips += ion != (not (a2 >> s) & 1)
     print(f"draws {draws}, ionised {ionised}, decisions that differ {flips}")
     assert draws > 10_000
-    assert ionised > 0
+    assert ionised >= len(changed)
     # a neutral that has crossed into a neighbour draws against that cell's
     # threshold; at 300 K that takes a birth offset within ~1e-4 of a face
     assert flips <= 2 + 1e-4 * draws, (flips, draws)
