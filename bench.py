@@ -238,7 +238,7 @@ ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
 LIMITER = {
     "push": "issue rate of the deposit's ~26 global vector reductions per particle",
     "keldysh": "FP32 issue (series of Dawson terms)",
-    "ionize": "integer issue (Philox draws)",
+    "ionize": "load latency and integer issue (Philox draws)",
 }
 
 

@@ -909,9 +909,11 @@ __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32
 }
 
 // One thread per material cell (a thread per slot pair measured twice as
-// slow: four threads repeat the cell's index and threshold loads).
+// slow: four threads repeat the cell's index and threshold loads).  FP32:
+// six blocks per SM (40 registers): the kernel waits on its loads, and 64
+// registers (four blocks) measured 22% slower.
 template <class R>
-__global__ void __launch_bounds__(256) k_ionize(Ctx<R> X) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 3) k_ionize(Ctx<R> X) {
   const Dev<R> &D = X.d;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;  // cell in material plane blockIdx.y
   const int mp = blockIdx.y;
