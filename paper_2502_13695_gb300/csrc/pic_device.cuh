@@ -225,6 +225,22 @@ __host__ __device__ __forceinline__ float dawson_w<float>(float z) {
   return dawson<float>(z);
 }
 
+// Square root of a Dawson argument y > 0: in FP32 on the device y rsqrt(y)
+// (within a few ulp; the FP32 Dawson table is good to 1.3e-7 anyway), the
+// correctly rounded root elsewhere.
+template <class R>
+__host__ __device__ __forceinline__ R dawson_arg_sqrt(R y) {
+  return sqrt(y);
+}
+template <>
+__host__ __device__ __forceinline__ float dawson_arg_sqrt<float>(float y) {
+#ifdef __CUDA_ARCH__
+  return y * rsqrtf(y);
+#else
+  return sqrtf(y);
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Keldysh threshold (Sec. 2.1, corrected form) for one cell:
 //   gamma = kG / E, gamma1 = g^2/(1+g^2), gamma2 = 1/(1+g^2),
@@ -259,7 +275,7 @@ __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterm
   R sum = R(0), rn = R(1);
   int n = 0;
   for (; n < nterms; ++n) {
-    const R z = sqrt(cd * (base + R(n)));
+    const R z = dawson_arg_sqrt<R>(cd * (base + R(n)));
     const R term = rn * dawson_w<R>(z);
     sum += term;
     if (z > R(0.9242) && term * tail <= R(0.5) * Eps<R>::v() * sum) {
