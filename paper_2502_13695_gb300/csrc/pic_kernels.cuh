@@ -1411,16 +1411,37 @@ __device__ __forceinline__ R langevin_d(R A) {
   return R(1) / (A * A) - R(1) / (sh * sh);
 }
 
+// The Langevin function and its derivative at A together: the series below
+// the thresholds where the differences cancel, else from one d = 1 -
+// exp(-2A): coth A = (2 - d)/d and 1/sinh^2 A = 4 (1 - d)/d^2.
+template <class R>
+__device__ __forceinline__ void langevin_both(R A, R &L, R &Ld) {
+  const R A2 = A * A;
+  const bool smallL = A < CollTol<R>::small, smallD = A < R(sizeof(R) == 8 ? 1e-2 : 0.5);
+  if (smallL && smallD) {
+    L = langevin(A);
+    Ld = langevin_d(A);
+    return;
+  }
+  const R d = -expm1(R(-2) * A), id = R(1) / d, iA = R(1) / A;
+  L = smallL ? langevin(A) : (R(2) - d) * id - iA;
+  Ld = smallD ? langevin_d(A) : iA * iA - R(4) * (R(1) - d) * id * id;
+}
+
 // Nanbu's parameter A(s): the root of coth A - 1/A = exp(-s).  Newton from
 // the left (the function is increasing and concave, so the iterates rise
-// monotonically to the root), started below both asymptotes A = 3 exp(-s)
-// and A = 1 / (1 - exp(-s)); at most 40 steps.
+// monotonically to the root), started at 0.95 of Cohen's Pade inverse
+// t (3 - t^2) / (1 - t^2) of the Langevin function, t = exp(-s): that lies
+// 0 to 4.94% above the root for 0.1 <= s < 6, so the start is below it, and
+// two steps reach FP32 precision; at most 40 steps.
 template <class R>
 __device__ R nanbu_A(R s) {
   const R t = exp(-s);
-  R A = fmin(R(3) * t, R(1) / (R(1) - t)) * R(0.5);
+  R A = R(0.95) * t * (R(3) - t * t) / (R(1) - t * t);
   for (int it = 0; it < 40; ++it) {
-    const R dA = (t - langevin(A)) / langevin_d(A);
+    R L, Ld;
+    langevin_both(A, L, Ld);
+    const R dA = (t - L) / Ld;
     A += dA;
     if (!(fabs(dA) > CollTol<R>::v * A)) break;
   }
@@ -1447,20 +1468,23 @@ __device__ R nanbu_cos(R s, R U) {
 // masses m (units of m_e), weights w; centre-of-mass momentum rotated by
 // (chi, phi), then back to the lab frame; each side moves with probability
 // w_other / max(w_a, w_b).  nd = neff * dtc (density factor times the
-// collision interval); na, nb the group densities; lD the screening length.
+// collision interval); na23, nb23 the group densities to the power 2/3
+// (per cell); lD the screening length.  Quotients by a common denominator
+// are products with its reciprocal.
 template <class R>
-__device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R na, R nb, R lD,
+__device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R na23, R nb23, R lD,
                              const CollConst &K, const R U[4]) {
   const R ga = sqrt(R(1) + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]));
   const R gb = sqrt(R(1) + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]));
   const R Et = ma * ga + mb * gb;
+  const R iga = R(1) / ga, igb = R(1) / gb, iEt = R(1) / Et;
   R vc[3], va[3], vb[3], pa[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     pa[d] = ma * ua[d];
-    va[d] = ua[d] / ga;
-    vb[d] = ub[d] / gb;
-    vc[d] = (pa[d] + mb * ub[d]) / Et;
+    va[d] = ua[d] * iga;
+    vb[d] = ub[d] * igb;
+    vc[d] = (pa[d] + mb * ub[d]) * iEt;
   }
   const R vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
   const R gc = R(1) / sqrt(R(1) - vc2);
@@ -1474,35 +1498,37 @@ __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R n
   const R p2 = ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2];
   const R pm = sqrt(p2);
   if (!(pm > R(0))) return;
-  const R mm = ma * gsa * mb * gsb / p2 + R(1);
-  const R b0 = R(K.re) * gc / Et * mm;
-  const R bmin = fmax(R(K.lc) / (R(2) * pm), b0);
+  const R ipm = R(1) / pm;
+  const R mab = ma * gsa * mb * gsb;
+  const R mm = mab / p2 + R(1);
+  const R b0 = R(K.re) * gc * iEt * mm;
+  const R bmin = fmax(R(K.lc) * R(0.5) * ipm, b0);
   const R lnL = fmax(R(1), R(0.5) * log(R(1) + lD * lD / (bmin * bmin)));
   const R sv = nd * R(K.K1) * lnL * gc * pm / (ma * ga * mb * gb * Et) * mm * mm;
-  const R vrel = Et * pm / (ma * gsa * mb * gsb * gc);
-  const R dens = fmax(ma * pow(na, R(2) / R(3)), mb * pow(nb, R(2) / R(3)));
+  const R vrel = Et * pm / (mab * gc);
+  const R dens = fmax(ma * na23, mb * nb23);
   const R scap = nd * R(K.capc) * (ma + mb) / dens * vrel;
   const R s = fmin(sv, scap);
   const R cx = nanbu_cos(s, U[0]);
   const R sx = sqrt(fmax(R(0), R(1) - cx * cx));
-  const R phi = R(2 * kPi) * U[1];
-  const R u[3] = {ps[0] / pm, ps[1] / pm, ps[2] / pm};
+  R sp, cp;
+  sincospi(R(2) * U[1], &sp, &cp);  // phi = 2 pi U
+  const R u[3] = {ps[0] * ipm, ps[1] * ipm, ps[2] * ipm};
   R e1[3], e2v[3];
   if (fabs(u[2]) < R(0.9)) {
-    const R n = sqrt(u[0] * u[0] + u[1] * u[1]);
-    e1[0] = u[1] / n;
-    e1[1] = -u[0] / n;
+    const R in = R(1) / sqrt(u[0] * u[0] + u[1] * u[1]);
+    e1[0] = u[1] * in;
+    e1[1] = -u[0] * in;
     e1[2] = R(0);
   } else {
-    const R n = sqrt(u[1] * u[1] + u[2] * u[2]);
+    const R in = R(1) / sqrt(u[1] * u[1] + u[2] * u[2]);
     e1[0] = R(0);
-    e1[1] = u[2] / n;
-    e1[2] = -u[1] / n;
+    e1[1] = u[2] * in;
+    e1[2] = -u[1] * in;
   }
   e2v[0] = u[1] * e1[2] - u[2] * e1[1];
   e2v[1] = u[2] * e1[0] - u[0] * e1[2];
   e2v[2] = u[0] * e1[1] - u[1] * e1[0];
-  const R cp = cos(phi), sp = sin(phi);
   R pn[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) pn[d] = pm * (cx * u[d] + sx * (cp * e1[d] + sp * e2v[d]));
@@ -1511,12 +1537,14 @@ __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R n
   // as U w_max < w_other for every U < 1, and safe when a float U rounds to 1)
   const R wmax = fmax(wa, wb);
   if (wb >= wmax || U[2] * wmax < wb) {
+    const R ima = R(1) / ma;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) / ma;
+    for (int d = 0; d < 3; ++d) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) * ima;
   }
   if (wa >= wmax || U[3] * wmax < wa) {
+    const R imb = R(1) / mb;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) / mb;
+    for (int d = 0; d < 3; ++d) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) * imb;
   }
 }
 
@@ -1548,7 +1576,7 @@ struct CollParam {
   int nE, nH;
   R ndl[2];  // like pairs: group density x collision interval
   R ndu;     // unlike pairs: n_e n_h / n_ab x collision interval
-  R dens[2], lD;
+  R dens23[2], lD;  // group densities to the power 2/3 (collide_pair's spacing cap)
   uint32_t qu;
 };
 
@@ -1565,8 +1593,8 @@ __device__ __forceinline__ unsigned long long coll_item(int cidx, int sp, int tr
 template <class R>
 __device__ __noinline__ void collide_pool(const Dev<R> &D, const LayerR<R> *__restrict__ lr,
                                           unsigned long long pa, unsigned long long pb,
-                                          uint32_t step, uint32_t c, uint32_t q, R nd, R na, R nb,
-                                          R lD, const CollConst &K) {
+                                          uint32_t step, uint32_t c, uint32_t q, R nd, R na23,
+                                          R nb23, R lD, const CollConst &K) {
   const uint32_t ta = D.ptag[pa], tb = D.ptag[pb];
   const LayerR<R> &La = lr[ta >> 1], &Lb = lr[tb >> 1];
   const R ic = R(1.0 / kC);
@@ -1578,7 +1606,8 @@ __device__ __noinline__ void collide_pool(const Dev<R> &D, const LayerR<R> *__re
   }
   const uint4 w = draw(D.seed, step, c, q, kStreamCollPair);
   const R U[4] = {unit_open<R>(w.x), unit_open<R>(w.y), unit_open<R>(w.z), unit_open<R>(w.w)};
-  collide_pair(ua, ub, La.mhat[ta & 1u], Lb.mhat[tb & 1u], La.wmac, Lb.wmac, nd, na, nb, lD, K, U);
+  collide_pair(ua, ub, La.mhat[ta & 1u], Lb.mhat[tb & 1u], La.wmac, Lb.wmac, nd, na23, nb23, lD, K,
+               U);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     D.pu[d][pa] = ua[d] * R(kC);
@@ -1732,8 +1761,8 @@ __device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr
     P.ndl[0] = dens[0] * dt;
     P.ndl[1] = dens[1] * dt;
     P.ndu = ndu;
-    P.dens[0] = dens[0];
-    P.dens[1] = dens[1];
+    P.dens23[0] = pow(dens[0], R(2) / R(3));
+    P.dens23[1] = pow(dens[1], R(2) / R(3));
     P.lD = lD;
     P.qu = (uint32_t)(nlike[0] + nlike[1]);
     W.par[c] = P;
@@ -1879,8 +1908,8 @@ __global__ void __launch_bounds__(128) k_coll_prep_small(Ctx<R> X, const unsigne
       P.ndl[0] = dens[0] * dt;
       P.ndl[1] = dens[1] * dt;
       P.ndu = ndu;
-      P.dens[0] = dens[0];
-      P.dens[1] = dens[1];
+      P.dens23[0] = pow(dens[0], R(2) / R(3));
+      P.dens23[1] = pow(dens[1], R(2) / R(3));
       P.lD = lD;
       P.qu = (uint32_t)(nlike[0] + nlike[1]);
       W.par[c] = P;
@@ -1918,11 +1947,11 @@ __global__ void __launch_bounds__(256) k_coll_like(Ctx<R> X, CollWork<R> W, Coll
       const int a[3] = {0, 0, 1}, b[3] = {1, 2, 2};
       for (int r = 0; r < 3; ++r)
         collide_pool(D, X.lr, ord[a[r]], ord[b[r]], step, P.cell, q0 + r, R(0.5) * P.ndl[sp],
-                     P.dens[sp], P.dens[sp], P.lD, K);
+                     P.dens23[sp], P.dens23[sp], P.lD, K);
     } else {
       const int start = (m & 1) ? 3 : 0;
       collide_pool(D, X.lr, ord[start + 2 * k], ord[start + 2 * k + 1], step, P.cell,
-                   q0 + start + k, P.ndl[sp], P.dens[sp], P.dens[sp], P.lD, K);
+                   q0 + start + k, P.ndl[sp], P.dens23[sp], P.dens23[sp], P.lD, K);
     }
   }
 }
@@ -1946,7 +1975,7 @@ __global__ void __launch_bounds__(256) k_coll_unlike(Ctx<R> X, CollWork<R> W, Co
     for (int i = j; i < nA; i += nB) {
       const unsigned long long pA = oA[i], pB = oB[j];
       collide_pool(D, X.lr, A == 0 ? pA : pB, A == 0 ? pB : pA, step, P.cell, P.qu + i, P.ndu,
-                   P.dens[0], P.dens[1], P.lD, K);
+                   P.dens23[0], P.dens23[1], P.lD, K);
     }
   }
 }
