@@ -540,7 +540,8 @@ int enqueue(pic_ctx *h, int mask) {
     W.like = (unsigned long long *)(h->arena + P.off_clike);
     W.unl = (unsigned long long *)(h->arena + P.off_cunl);
     PIC_CUDA(cudaMemsetAsync(W.n, 0, 8 * sizeof(int), s));
-    k_coll_cells<<<grid_blocks(P.ncell), kThreads, 0, s>>>(cend, P.ncell, clist, W.n);
+    k_coll_cells<<<grid_blocks((P.ncell + kCellsPerThread - 1) / kCellsPerThread), kThreads, 0, s>>>(
+        cend, P.ncell, clist, W.n);
     const double dtc = P.dt * P.g.coll_every;
     k_coll_prep_small<R><<<kPersistentBlocks, 128, 0, s>>>(X, cend, W, dtc);
     k_coll_prep<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, W, dtc);

@@ -1170,22 +1170,48 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(unsigned int *bsum
   if (threadIdx.x == 0) *total_out = carry;
 }
 
+// Each thread scans kScanItems consecutive counts, moved as 16-byte vectors
+// (the arena is 256-byte aligned, so a thread's run starts on a 64-byte
+// boundary); a ragged last run goes element by element.
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, long long n,
                                                               const unsigned int *bsum) {
   const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  const bool full = base + kScanItems <= n;
   unsigned int v[kScanItems];
+  if (full) {
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(cnt + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+      const uint4 t = p4[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = base + q < n ? cnt[base + q] : 0u;
+  }
   unsigned int s = 0;
 #pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    v[q] = base + q < n ? cnt[base + q] : 0u;
-    s += v[q];
-  }
+  for (int q = 0; q < kScanItems; ++q) s += v[q];
   unsigned int tot;
   unsigned int ex = block_excl_scan(s, tot) + bsum[blockIdx.x];
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
-    if (base + q < n) cnt[base + q] = ex;
+    const unsigned int e = ex;
     ex += v[q];
+    v[q] = e;
+  }
+  if (full) {
+    uint4 *p4 = reinterpret_cast<uint4 *>(cnt + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q)
+      p4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+      if (base + q < n) cnt[base + q] = v[q];
   }
 }
 
@@ -1629,11 +1655,58 @@ __device__ __forceinline__ void append_cell(int *list, int *count, bool have, in
 
 // Cells that hold two or more charged particles after the sort: those of at
 // most kCollSmall in list (count n[0]), larger ones in list + ncell (n[4]).
-__global__ void k_coll_cells(const unsigned int *cend, long long ncell, int *list, int *n) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const unsigned int m = c < ncell ? cend[c] - (c ? cend[c - 1] : 0u) : 0u;
-  append_cell(list, n, m >= 2u && m <= (unsigned)kCollSmall, (int)c);
-  append_cell(list + ncell, n + 4, m > (unsigned)kCollSmall, (int)c);
+// Each thread classifies kCellsPerThread consecutive cells and each block
+// reserves its entries with one atomic per list (the order of the lists
+// does not matter: every cell's collisions are independent).
+constexpr int kCellsPerThread = 4;
+
+__global__ void __launch_bounds__(256) k_coll_cells(const unsigned int *cend, long long ncell,
+                                                    int *list, int *n) {
+  __shared__ int wsum[2][8], wbase[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long c0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kCellsPerThread;
+  uint32_t small = 0, large = 0;  // bit q: cell c0 + q
+  unsigned int prev = (c0 > 0 && c0 <= ncell) ? cend[c0 - 1] : 0u;
+#pragma unroll
+  for (int q = 0; q < kCellsPerThread; ++q) {
+    const long long c = c0 + q;
+    const unsigned int e = c < ncell ? cend[c] : prev;
+    const unsigned int m = e - prev;
+    prev = e;
+    small |= (uint32_t)(m >= 2u && m <= (unsigned)kCollSmall) << q;
+    large |= (uint32_t)(m > (unsigned)kCollSmall) << q;
+  }
+  int cnt[2] = {__popc(small), __popc(large)}, incl[2] = {cnt[0], cnt[1]};
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int v = __shfl_up_sync(0xffffffffu, incl[g], sft);
+      if (lane >= sft) incl[g] += v;
+    }
+  }
+  if (lane == 31) {
+    wsum[0][warp] = incl[0];
+    wsum[1][warp] = incl[1];
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int g = threadIdx.x;
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int v = wsum[g][w];
+      wsum[g][w] = tot;
+      tot += v;
+    }
+    wbase[g] = tot ? atomicAdd(n + 4 * g, tot) : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    int at = wbase[g] + wsum[g][warp] + incl[g] - cnt[g];
+    int *const dst = list + g * ncell;
+    for (uint32_t bits = g ? large : small; bits; bits &= bits - 1) dst[at++] = (int)(c0 + __ffs(bits) - 1);
+  }
 }
 
 // Collision work of one pass, in global memory.
