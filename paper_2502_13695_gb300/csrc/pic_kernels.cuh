@@ -1714,23 +1714,12 @@ template <class R>
 struct CollWork {
   const int *list;               // listed cells: small ones (count n[0]), large at + ncell (n[4])
   int *n;                        // [0] small cells [1] like items [2] unlike columns
-                                 // [3] next large cell [4] large cells
+                                 // [3] unused [4] large cells
   long long ncell;
   CollParam<R> *par;             // indexed by cell
   int *ord;                      // pool-indexed pairing order of every listed cell
   unsigned long long *like, *unl;  // work items
 };
-
-__device__ __forceinline__ void append_item(unsigned long long *items, int *count, bool have,
-                                            unsigned long long item) {
-  const unsigned act = __ballot_sync(0xffffffffu, have);
-  if (!act) return;
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == __ffs(act) - 1) base = atomicAdd(count, __popc(act));
-  base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
-  if (have) items[base + __popc(act & ((1u << lane) - 1u))] = item;
-}
 
 // Prepare one listed cell (one warp): order each group by its Philox keys,
 // take the group densities, kinetic temperatures and screening length, and
@@ -1840,34 +1829,40 @@ __device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr
     P.qu = (uint32_t)(nlike[0] + nlike[1]);
     W.par[c] = P;
   }
-  // work items: triplets and like pairs of each group, then unlike columns
+  // work items: the triplet and like pairs of each group, then the unlike
+  // columns, each list's entries reserved with one atomic per cell
+  int tri[2], rest[2];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const int m = cnt[sp];
-    const bool tri = m >= 3 && (m & 1);
-    const int rest = m < 2 ? 0 : (tri ? (m - 3) / 2 : m / 2);
-    append_item(W.like, W.n + 1, lane == 0 && tri, coll_item(cidx, sp, 1, 0));
-    for (int k0 = 0; k0 < rest; k0 += 32)
-      append_item(W.like, W.n + 1, k0 + lane < rest, coll_item(cidx, sp, 0, k0 + lane));
+    tri[sp] = m >= 3 && (m & 1);
+    rest[sp] = m < 2 ? 0 : (tri[sp] ? (m - 3) / 2 : m / 2);
   }
-  if (cnt[0] > 0 && cnt[1] > 0) {
-    const int nB = min(cnt[0], cnt[1]);
-    for (int j0 = 0; j0 < nB; j0 += 32)
-      append_item(W.unl, W.n + 2, j0 + lane < nB, coll_item(cidx, 0, 0, j0 + lane));
+  const int g0 = tri[0] + rest[0], nl = g0 + tri[1] + rest[1];
+  const int nB = (cnt[0] > 0 && cnt[1] > 0) ? min(cnt[0], cnt[1]) : 0;
+  int bl = 0, bu = 0;
+  if (lane == 0) {
+    if (nl) bl = atomicAdd(W.n + 1, nl);
+    if (nB) bu = atomicAdd(W.n + 2, nB);
   }
+  bl = __shfl_sync(0xffffffffu, bl, 0);
+  bu = __shfl_sync(0xffffffffu, bu, 0);
+  for (int e = lane; e < nl; e += 32) {
+    const int sp = e < g0 ? 0 : 1, el = sp ? e - g0 : e;
+    const int t3 = tri[sp] && el == 0;
+    W.like[bl + e] = coll_item(cidx, sp, t3, t3 ? 0 : el - tri[sp]);
+  }
+  for (int j = lane; j < nB; j += 32) W.unl[bu + j] = coll_item(cidx, 0, 0, j);
 }
 
 template <class R>
 __global__ void __launch_bounds__(32 * kCollWarps) k_coll_prep(Ctx<R> X, const unsigned int *cend,
                                                                 CollWork<R> W, double dtc) {
   __shared__ CollCell<R> cells[kCollWarps];
-  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wp = threadIdx.x >> 5;
   const int nl = W.n[4];
-  for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(W.n + 3, 1);
-    q = __shfl_sync(0xffffffffu, q, 0);
-    if (q >= nl) return;
+  // each warp takes every (number of warps)-th large cell
+  for (int q = blockIdx.x * kCollWarps + wp; q < nl; q += gridDim.x * kCollWarps) {
     coll_prep_cell(X.d, X.lr, cells[wp], cend, W.list[W.ncell + q], W, dtc);
     __syncwarp();
   }
