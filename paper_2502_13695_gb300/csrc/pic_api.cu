@@ -539,6 +539,7 @@ int enqueue(pic_ctx *h, int mask) {
     W.ord = (int *)(h->arena + P.off_cord);
     W.like = (unsigned long long *)(h->arena + P.off_clike);
     W.unl = (unsigned long long *)(h->arena + P.off_cunl);
+    W.lcap = (int)(P.cap / 2 + 1);
     PIC_CUDA(cudaMemsetAsync(W.n, 0, 8 * sizeof(int), s));
     k_coll_cells<<<grid_blocks((P.ncell + kCellsPerThread - 1) / kCellsPerThread), kThreads, 0, s>>>(
         cend, P.ncell, clist, W.n);

@@ -1713,9 +1713,15 @@ __global__ void __launch_bounds__(256) k_coll_cells(const unsigned int *cend, lo
 template <class R>
 struct CollWork {
   const int *list;               // listed cells: small ones (count n[0]), large at + ncell (n[4])
-  int *n;                        // [0] small cells [1] like items [2] unlike columns
-                                 // [3] unused [4] large cells
+  int *n;                        // [0] small cells [1] like pairs [2] unlike columns of
+                                 // one collision [3] like triplets [4] large cells
+                                 // [5] unlike columns of two or more collisions
   long long ncell;
+  int lcap;                      // entries of like and unl: pairs and one-collision
+                                 // columns fill them from the front, triplets and
+                                 // longer columns from the back (each list holds at
+                                 // most half the particles, so the ends never meet),
+                                 // so that a warp's threads do equal work
   CollParam<R> *par;             // indexed by cell
   int *ord;                      // pool-indexed pairing order of every listed cell
   unsigned long long *like, *unl;  // work items
@@ -1838,21 +1844,30 @@ __device__ void coll_prep_cell(const Dev<R> &D, const LayerR<R> *__restrict__ lr
     tri[sp] = m >= 3 && (m & 1);
     rest[sp] = m < 2 ? 0 : (tri[sp] ? (m - 3) / 2 : m / 2);
   }
-  const int g0 = tri[0] + rest[0], nl = g0 + tri[1] + rest[1];
+  const int np = rest[0] + rest[1], nt = tri[0] + tri[1];
   const int nB = (cnt[0] > 0 && cnt[1] > 0) ? min(cnt[0], cnt[1]) : 0;
-  int bl = 0, bu = 0;
+  const int nA = max(cnt[0], cnt[1]);
+  const int nm = nB ? max(0, min(nB, nA - nB)) : 0;  // columns j < nA - nB collide twice or more
+  int b[4] = {0, 0, 0, 0};
   if (lane == 0) {
-    if (nl) bl = atomicAdd(W.n + 1, nl);
-    if (nB) bu = atomicAdd(W.n + 2, nB);
+    if (np) b[0] = atomicAdd(W.n + 1, np);
+    if (nt) b[1] = atomicAdd(W.n + 3, nt);
+    if (nB - nm) b[2] = atomicAdd(W.n + 2, nB - nm);
+    if (nm) b[3] = atomicAdd(W.n + 5, nm);
   }
-  bl = __shfl_sync(0xffffffffu, bl, 0);
-  bu = __shfl_sync(0xffffffffu, bu, 0);
-  for (int e = lane; e < nl; e += 32) {
-    const int sp = e < g0 ? 0 : 1, el = sp ? e - g0 : e;
-    const int t3 = tri[sp] && el == 0;
-    W.like[bl + e] = coll_item(cidx, sp, t3, t3 ? 0 : el - tri[sp]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) b[q] = __shfl_sync(0xffffffffu, b[q], 0);
+  for (int e = lane; e < np; e += 32) {
+    const int sp = e < rest[0] ? 0 : 1;
+    W.like[b[0] + e] = coll_item(cidx, sp, 0, sp ? e - rest[0] : e);
   }
-  for (int j = lane; j < nB; j += 32) W.unl[bu + j] = coll_item(cidx, 0, 0, j);
+  if (lane < nt) W.like[W.lcap - 1 - (b[1] + lane)] = coll_item(cidx, (lane == 0 && tri[0]) ? 0 : 1, 1, 0);
+  for (int j = lane; j < nB; j += 32) {
+    if (j < nm)
+      W.unl[W.lcap - 1 - (b[3] + j)] = coll_item(cidx, 0, 0, j);
+    else
+      W.unl[b[2] + j - nm] = coll_item(cidx, 0, 0, j);
+  }
 }
 
 template <class R>
@@ -1982,28 +1997,40 @@ __global__ void __launch_bounds__(128) k_coll_prep_small(Ctx<R> X, const unsigne
       P.qu = (uint32_t)(nlike[0] + nlike[1]);
       W.par[c] = P;
     }
-    int bl = reserve_items(W.n + 1, nl);
-    const int bu = reserve_items(W.n + 2, nu);
+    // pairs and one-collision columns from the front of their lists,
+    // triplets and longer columns from the back
+    const int np = rest[0] + rest[1], nt = nl - np;
+    const int nm = nu ? max(0, min(nu, max(cnt[0], cnt[1]) - nu)) : 0;
+    int bp = reserve_items(W.n + 1, np);
+    int bt = reserve_items(W.n + 3, nt);
+    const int bs = reserve_items(W.n + 2, nu - nm);
+    const int bm = reserve_items(W.n + 5, nm);
     if (have) {
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
-        if (tri[g]) W.like[bl++] = coll_item(c, g, 1, 0);
-        for (int k = 0; k < rest[g]; ++k) W.like[bl++] = coll_item(c, g, 0, k);
+        if (tri[g]) W.like[W.lcap - 1 - bt++] = coll_item(c, g, 1, 0);
+        for (int k = 0; k < rest[g]; ++k) W.like[bp++] = coll_item(c, g, 0, k);
       }
-      for (int j = 0; j < nu; ++j) W.unl[bu + j] = coll_item(c, 0, 0, j);
+      for (int j = 0; j < nu; ++j) {
+        if (j < nm)
+          W.unl[W.lcap - 1 - (bm + j)] = coll_item(c, 0, 0, j);
+        else
+          W.unl[bs + j - nm] = coll_item(c, 0, 0, j);
+      }
     }
   }
 }
 
 // Like pairs (one thread per pair) and triplets (one thread each, three
-// pairs in order).  Pair q: electrons' like pairs first, then the holes'.
+// pairs in order): the pairs first, then the triplets, so that warps do
+// equal work.  Pair q: electrons' like pairs first, then the holes'.
 template <class R>
 __global__ void __launch_bounds__(256) k_coll_like(Ctx<R> X, CollWork<R> W, CollConst K) {
   const Dev<R> &D = X.d;
-  const int nitems = W.n[1];
+  const int npair = W.n[1], nitems = npair + W.n[3];
   const uint32_t step = (uint32_t)*D.step;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x) {
-    const unsigned long long it = W.like[t];
+    const unsigned long long it = W.like[t < npair ? t : W.lcap - 1 - (t - npair)];
     const int cidx = (int)(unsigned)it, sp = (int)(it >> 32) & 1, tri = (int)(it >> 33) & 1;
     const int k = (int)(it >> 34) & 0xFFFF;
     const CollParam<R> P = W.par[cidx];
@@ -2026,14 +2053,15 @@ __global__ void __launch_bounds__(256) k_coll_like(Ctx<R> X, CollWork<R> W, Coll
 
 // Unlike pairs (A_i, B_{i mod |B|}), A the larger group: one thread per
 // column j of B takes i = j, j + |B|, ... in order, which is the order of the
-// rounds; columns share no particle.
+// rounds; columns share no particle.  Columns of one collision come first,
+// then the longer ones.
 template <class R>
 __global__ void __launch_bounds__(256) k_coll_unlike(Ctx<R> X, CollWork<R> W, CollConst K) {
   const Dev<R> &D = X.d;
-  const int nitems = W.n[2];
+  const int n1 = W.n[2], nitems = n1 + W.n[5];
   const uint32_t step = (uint32_t)*D.step;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x) {
-    const unsigned long long it = W.unl[t];
+    const unsigned long long it = W.unl[t < n1 ? t : W.lcap - 1 - (t - n1)];
     const int cidx = (int)(unsigned)it, j = (int)(it >> 34) & 0xFFFF;
     const CollParam<R> P = W.par[cidx];
     const int A = P.nE >= P.nH ? 0 : 1;
