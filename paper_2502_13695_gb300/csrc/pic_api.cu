@@ -544,7 +544,9 @@ int enqueue(pic_ctx *h, int mask) {
     k_coll_cells<<<grid_blocks((P.ncell + kCellsPerThread - 1) / kCellsPerThread), kThreads, 0, s>>>(
         cend, P.ncell, clist, W.n);
     const double dtc = P.dt * P.g.coll_every;
-    k_coll_prep_small<R><<<kPersistentBlocks, 128, 0, s>>>(X, cend, W, dtc);
+    // twice the resident warps of one pass: the thread-per-cell preparation
+    // waits on its scattered particle loads
+    k_coll_prep_small<R><<<kPersistentBlocks * 2, 128, 0, s>>>(X, cend, W, dtc);
     k_coll_prep<R><<<h->coll_blocks, 32 * kCollWarps, 0, s>>>(X, cend, W, dtc);
     k_coll_like<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
     k_coll_unlike<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, W, K);
