@@ -57,6 +57,7 @@ struct Plan {
   size_t off_work, off_work_n, off_leave16;
   size_t off_imax, off_prof;
   size_t off_clist, off_cn;  // collision cell list and its counters
+  size_t off_hot;            // hot-plane stamps (n_mplanes + 1)
   size_t off_cpar, off_cord, off_clike, off_cunl;  // collision work (coll_every > 0)
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
@@ -186,6 +187,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   const bool coll = g.coll_every > 0;
   P.off_clist = take(coll ? P.ncell * 2 * 4 : 4);
   P.off_cn = take(32);
+  P.off_hot = take((size_t)(P.n_mplanes + 1) * sizeof(uint32_t));
   P.off_cpar = take((size_t)(coll ? P.ncell : 1) *
                     std::max(sizeof(CollParam<double>), sizeof(CollParam<float>)));
   P.off_cord = take(coll ? P.cap * 4 : 4);
@@ -392,6 +394,7 @@ void bind(pic_ctx *h) {
   }
   D.J4 = (R *)(A + P.off_J4);
   D.layer_of_plane = (const int *)(A + P.off_lop);
+  D.hot = (uint32_t *)(A + P.off_hot);
   D.mplane = (const int *)(A + P.off_mplane);
   D.kplane = (const int *)(A + P.off_kplane);
   D.layers = (const LayerK *)(A + P.off_lk);
@@ -1421,6 +1424,10 @@ int set_material_t(pic_ctx *h, const uint32_t *alive, const double *win) {
   const Plan &P = h->P;
   if (!P.nmat) return PIC_OK;
   int rc;
+  // k_ionize skips no plane until the next window pass stamps them again
+  const uint32_t all = 0xFFFFFFFFu;
+  if ((rc = copy_in(h, P.off_hot + (size_t)P.n_mplanes * sizeof(uint32_t), &all, sizeof(all))))
+    return rc;
   if (alive && (rc = copy_in(h, P.off_alive, alive, P.nmat * 4))) return rc;
   if (win) {
     const int NW = P.NW;

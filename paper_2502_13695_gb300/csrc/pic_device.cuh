@@ -72,6 +72,11 @@ struct Dev {
   unsigned long long *T;
   uint32_t *alive;
   uint32_t *leave_step;           // first step index at which a neutral may have left its cell
+  // per material plane the stamp (step + 1) of the last window pass that
+  // found a cell at or above its layer's skip amplitude (only such cells
+  // can have a nonzero threshold); [n_mplanes] that pass's stamp, all ones
+  // when the host has written the material since
+  uint32_t *hot;
   // charged particles (SoA)
   int32_t *pcell;
   R *po[3], *pu[3];

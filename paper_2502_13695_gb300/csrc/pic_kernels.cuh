@@ -679,6 +679,7 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
   const int mp = blockIdx.y;
   const long long m = (long long)mp * nxy + r;
   uint32_t miss = 0;  // cells whose threshold k_keldysh must recompute
+  bool hot = false;   // a cell at or above the skip amplitude
   if (r < nxy) {
     const int j = r / nx, i = r - j * nx;
     const int k = D.kplane[mp];
@@ -750,6 +751,7 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
     const R e_skip = X.lr[D.layer_of_plane[k]].e_skip;
 #pragma unroll
     for (int l = 0; l < V; ++l) {
+      hot |= amp[l] >= e_skip;
       if (key[l] == amp[l]) continue;  // threshold cached for this exact amplitude
       if (!(amp[l] >= e_skip)) {
         D.T[m + l] = 0ull;
@@ -759,6 +761,9 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
       }
     }
   }
+  // stamp the plane for k_ionize, which skips planes without such cells
+  if (__syncthreads_or(hot) && threadIdx.x == 0) D.hot[mp] = (uint32_t)*D.step + 1u;
+  if (threadIdx.x == 0 && blockIdx.x == 0 && mp == 0) D.hot[gridDim.y] = (uint32_t)*D.step + 1u;
   // warp-aggregated append of the misses to k_keldysh's work list
   const int cnt = __popc(miss);
   int incl = cnt;
@@ -917,6 +922,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 3) k_ionize(Ctx<R> X
   const Dev<R> &D = X.d;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;  // cell in material plane blockIdx.y
   const int mp = blockIdx.y;
+  {
+    // only cells at or above the skip amplitude can have a nonzero
+    // threshold; a neutral may sit in the plane above or below its birth
+    // plane, so a plane is skipped when neither it nor those hold one
+    const uint32_t stamp = D.hot[gridDim.y];
+    if (stamp != 0xFFFFFFFFu && D.hot[mp] != stamp && (mp == 0 || D.hot[mp - 1] != stamp) &&
+        (mp + 1 == (int)gridDim.y || D.hot[mp + 1] != stamp))
+      return;
+  }
   const long long m = (long long)mp * D.nxy + r;
   const bool active = r < D.nxy;
   const long long step = *D.step;
