@@ -1657,16 +1657,6 @@ __device__ __noinline__ void collide_pool(const Dev<R> &D, const LayerR<R> *__re
 
 constexpr int kCollSmall = 8;  // cells up to this size are prepared by one thread
 
-__device__ __forceinline__ void append_cell(int *list, int *count, bool have, int c) {
-  const unsigned act = __ballot_sync(0xffffffffu, have);
-  if (!act) return;
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == __ffs(act) - 1) base = atomicAdd(count, __popc(act));
-  base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
-  if (have) list[base + __popc(act & ((1u << lane) - 1u))] = c;
-}
-
 // Cells that hold two or more charged particles after the sort: those of at
 // most kCollSmall in list (count n[0]), larger ones in list + ncell (n[4]).
 // Each thread classifies kCellsPerThread consecutive cells and each block
