@@ -274,3 +274,26 @@ def test_config1_full_run_fp64_and_fp32(pic, oracle_mod):
     assert d32["frac_absorbed"] == pytest.approx(do["frac_absorbed"], rel=0.02)
     assert d32["n_e_peak"] == pytest.approx(do["n_e_peak"], rel=0.02)
     assert do["N_pairs"] > 0 and do["frac_absorbed"] > 0.01
+
+
+def test_anisotropic_cells_y_polarisation_and_phase(pic, oracle_mod):
+    """The paper's anisotropic cells (40 x 40 x 5 nm), the laser polarised
+    along y with a carrier-envelope phase of 1 rad, FP64 full run: every
+    20 steps E, B, P, Q to rel-L2 1e-12, identical decisions and particles."""
+    cfg = wl.grid(8, 8, 64, 40e-9, [wl.layer(10, 44, wl.SILICA, 2, 0.025)],
+                  wl.pulse(5e-15, 3.0, 1e-15, cep=1.0, pol=1), seed=13, precision="fp64",
+                  dz=5e-9)
+    g, o = _pair(pic, oracle_mod, cfg)
+    for block in range(3):
+        g.step(20)
+        o.step(20)
+        Fg, Fo = g.fields(), o.fields()
+        for name, sl in (("E", slice(0, 3)), ("B", slice(3, 6)), ("P", slice(9, 12)),
+                         ("Q", slice(12, 15))):
+            err = rel_l2(Fg[sl], Fo[sl])
+            assert err <= TOL64, (block, name, err, field_errors(Fg, Fo))
+        assert np.array_equal(g.material()["alive"], o.material()["alive"]), block
+        assert_particles_close(g.particles(), o.particles(), cfg, 1e-11, 1e-11, f"block {block}")
+    assert np.abs(Fo[1]).max() > 10 * np.abs(Fo[0]).max()  # polarised along y
+    assert len(o.particles()["id"]) > 100
+    g.close()
