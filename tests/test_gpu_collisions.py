@@ -24,11 +24,16 @@ def pic():
     return picmod
 
 
-def _box(counts, seed, precision="fp64"):
+def _box(counts, seed, precision="fp64", mixed=False):
     """Electrons and holes at rest-frame temperatures of 50-200 eV in a few
-    cells of a 4x4x8 grid; counts = [(n_electrons, n_holes) per cell]."""
-    cfg = wl.grid(4, 4, 8, 25e-9, [wl.layer(2, 6, wl.SILICA, 2, 0.0)],
-                  wl.pulse(5e-15, 0.0, 1.0), seed=seed, precision=precision)
+    cells of a 4x4x8 grid; counts = [(n_electrons, n_holes) per cell].
+    mixed: two layers of different materials and ppc (so different masses
+    and weights), each particle's birth layer drawn at random."""
+    mats = [wl.SILICA, wl.HIGH_INDEX] if mixed else [wl.SILICA]
+    layers = ([wl.layer(2, 4, wl.SILICA, 2, 0.0), wl.layer(4, 6, wl.HIGH_INDEX, 3, 0.0)]
+              if mixed else [wl.layer(2, 6, wl.SILICA, 2, 0.0)])
+    cfg = wl.grid(4, 4, 8, 25e-9, layers, wl.pulse(5e-15, 0.0, 1.0), seed=seed,
+                  precision=precision)
     cfg["coll_every"] = 1
     rng = np.random.default_rng(seed)
     cells = [(3 * 4 + 1) * 4 + 1, (3 * 4 + 2) * 4 + 2, (4 * 4 + 0) * 4 + 3, (4 * 4 + 3) * 4 + 0,
@@ -37,25 +42,26 @@ def _box(counts, seed, precision="fp64"):
     nid = 0
     for c, (ne, nh) in zip(cells, counts):
         for sp, m in ((0, ne), (1, nh)):
-            mass = (wl.SILICA["me_star"] if sp == 0 else wl.SILICA["mh_star"]) * ME
-            sig = np.array([math.sqrt(200 * QE / mass), math.sqrt(50 * QE / mass),
-                            math.sqrt(80 * QE / mass)])
             for _ in range(m):
+                L = int(rng.integers(len(mats)))
+                mass = (mats[L]["me_star"] if sp == 0 else mats[L]["mh_star"]) * ME
+                sig = np.array([math.sqrt(200 * QE / mass), math.sqrt(50 * QE / mass),
+                                math.sqrt(80 * QE / mass)])
                 v = rng.normal(size=3) * sig + (0.02 * C if sp == 0 else 0.0)
                 g = 1 / math.sqrt(1 - v @ v / C ** 2)
                 ids.append(2 * nid + sp)
                 nid += 1
                 cell.append(c)
                 u.append(g * v)
-                tag.append(sp)
+                tag.append((L << 1) | sp)
     n = len(ids)
     P = dict(id=np.array(ids, np.uint64), cell=np.array(cell, np.int32),
              off=rng.uniform(size=(n, 3)), u=np.array(u), tag=np.array(tag, np.uint32))
     return cfg, P
 
 
-def _run_box(pic, oracle_mod, counts, seed, steps, precision="fp64"):
-    cfg, P = _box(counts, seed)
+def _run_box(pic, oracle_mod, counts, seed, steps, precision="fp64", mixed=False):
+    cfg, P = _box(counts, seed, mixed=mixed)
     o = oracle_mod.Sim(cfg)
     g = pic.Simulation(dict(cfg, precision=precision))
     for sim in (o, g):
@@ -77,6 +83,20 @@ def test_collision_box_matches_oracle_fp64(pic, oracle_mod, counts):
     po, pg = o.particles(), g.particles()
     assert np.array_equal(po["id"], pg["id"])
     assert not np.allclose(po["u"], P["u"][np.argsort(P["id"])])  # they did collide
+    np.testing.assert_allclose(pg["u"], po["u"], rtol=1e-11,
+                               atol=1e-11 * np.abs(po["u"]).max())
+
+
+def test_collision_box_two_birth_layers_fp64(pic, oracle_mod):
+    """Groups that mix particles born in two materials: each keeps its
+    layer's mass and weight, so pairs of unequal weight take the weighted
+    acceptance on one side."""
+    cfg, P, o, g = _run_box(pic, oracle_mod, [(9, 4), (6, 6), (3, 7), (12, 1)], seed=43,
+                            steps=10, mixed=True)
+    po, pg = o.particles(), g.particles()
+    assert np.array_equal(po["id"], pg["id"])
+    assert len(set((po["tag"] >> 1).tolist())) == 2
+    assert not np.allclose(po["u"], P["u"][np.argsort(P["id"])])
     np.testing.assert_allclose(pg["u"], po["u"], rtol=1e-11,
                                atol=1e-11 * np.abs(po["u"]).max())
 
