@@ -58,6 +58,7 @@ struct Plan {
   size_t off_imax, off_prof;
   size_t off_clist, off_cn;  // collision cell list and its counters
   size_t off_hot;            // hot-plane stamps (n_mplanes + 1)
+  size_t off_jtouch;         // deposit-plane marks (nz + 2)
   size_t off_cpar, off_cord, off_clike, off_cunl;  // collision work (coll_every > 0)
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
@@ -188,6 +189,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_clist = take(coll ? P.ncell * 2 * 4 : 4);
   P.off_cn = take(32);
   P.off_hot = take((size_t)(P.n_mplanes + 1) * sizeof(uint32_t));
+  P.off_jtouch = take((size_t)(g.nz + 2) * sizeof(uint32_t));
   P.off_cpar = take((size_t)(coll ? P.ncell : 1) *
                     std::max(sizeof(CollParam<double>), sizeof(CollParam<float>)));
   P.off_cord = take(coll ? P.cap * 4 : 4);
@@ -395,6 +397,7 @@ void bind(pic_ctx *h) {
   D.J4 = (R *)(A + P.off_J4);
   D.layer_of_plane = (const int *)(A + P.off_lop);
   D.hot = (uint32_t *)(A + P.off_hot);
+  D.jtouch = (uint32_t *)(A + P.off_jtouch);
   D.mplane = (const int *)(A + P.off_mplane);
   D.kplane = (const int *)(A + P.off_kplane);
   D.layers = (const LayerK *)(A + P.off_lk);
@@ -1293,6 +1296,10 @@ int set_fields_t(pic_ctx *h, const double *src) {
       for (long long o = 0; o < P.nfield; ++o) j4[4 * o + d] = src[(size_t)(6 + d) * P.nfield + o];
     from_double<R>(j4.data(), j4.size(), raw);
     int rc = copy_in(h, off_of(h, X.d.J4), raw.data(), raw.size());
+    if (rc) return rc;
+    // the next E step reads the current on every plane
+    const uint32_t all = 1u;
+    rc = copy_in(h, P.off_jtouch + (size_t)P.g.nz * sizeof(uint32_t), &all, sizeof(all));
     if (rc) return rc;
   }
   std::vector<double> tmp(P.nmat);

@@ -77,6 +77,11 @@ struct Dev {
   // can have a nonzero threshold); [n_mplanes] that pass's stamp, all ones
   // when the host has written the material since
   uint32_t *hot;
+  // per cell plane the number of the field pass that must read the current
+  // a push deposited from a particle in it (completed passes + 1); [nz]
+  // nonzero when the host wrote the current (the next E step reads every
+  // plane); [nz + 1] the number of completed field passes
+  uint32_t *jtouch;
   // charged particles (SoA)
   int32_t *pcell;
   R *po[3], *pu[3];

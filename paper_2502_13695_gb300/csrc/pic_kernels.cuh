@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
   const R dl_inv[3] = {D.idx, D.idy, D.idz};
   const R c2inv = R(1.0 / (kC * kC));
   double pushed = 0.0;
+  const uint32_t jstamp = D.jtouch[D.nz + 1] + 1u;  // the next field pass
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   // each thread loads its next particle's state one iteration ahead, so that
@@ -309,6 +310,8 @@ __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
       cn[d] = cc;
       on[d] = nd;
     }
+    // the frame reaches node planes ck - 2 .. ck + 3: mark ck for k_efull
+    if (D.jtouch[ck] != jstamp) D.jtouch[ck] = jstamp;
     esirkepov(D, L.jpref[sp], co, off, cn, on);
     if (cn[2] < 2 || cn[2] >= nz - 2) {
       D.pcell[p] = -1;  // outflow through a z face
@@ -432,6 +435,12 @@ __device__ __forceinline__ void b_out(const Dev<R> &D, int d, long long o, const
 template <int V, int kMode, class R>
 __global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
+  // the E step of this pass has read the current: count the pass and clear
+  // the host-write flag
+  if (kMode != kPrime && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    D.jtouch[D.nz + 1] += 1u;
+    D.jtouch[D.nz] = 0u;
+  }
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (r >= nxy) return;
   const int k = blockIdx.y;
@@ -528,6 +537,14 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
   const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   const int k = blockIdx.y;
+  // the current is nonzero only on node planes within reach of a particle
+  // deposited since the last field pass (cell planes k - 3 .. k + 2) or
+  // after a host write
+  bool jt = D.jtouch[nz] != 0u;
+  {
+    const uint32_t jstamp = D.jtouch[nz + 1] + 1u;  // this pass
+    for (int q = max(0, k - 3); q <= min(nz - 1, k + 2); ++q) jt |= D.jtouch[q] == jstamp;
+  }
   R joule = R(0);
   if (r < nxy) {
     const int j = r / nx, i = r - j * nx;
@@ -543,8 +560,13 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
     ldv<V>(bx, D.Bh[0] + o);
     ldv<V>(by, D.Bh[1] + o);
     R jx[V], jy[V], jz[V];
+    if (jt) {
 #pragma unroll
-    for (int l = 0; l < V; ++l) load_j3(D.J4 + 4 * (o + l), jx[l], jy[l], jz[l]);
+      for (int l = 0; l < V; ++l) load_j3(D.J4 + 4 * (o + l), jx[l], jy[l], jz[l]);
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l) jx[l] = jy[l] = jz[l] = R(0);
+    }
     R ex0[V], ey0[V], ex1[V], ey1[V], dBz_dy[V], dBz_dx[V];
     ldv<V>(ex0, D.E[0] + o);
     ldv<V>(ey0, D.E[1] + o);
@@ -633,7 +655,7 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
 #pragma unroll
     for (int l = 0; l < V; ++l) {
       joule += jx[l] * R(0.5) * (ex0[l] + ex1[l]) + jy[l] * R(0.5) * (ey0[l] + ey1[l]);
-      clear_j3(D.J4 + 4 * (o + l));
+      if (jt) clear_j3(D.J4 + 4 * (o + l));
     }
     stv<V>(D.E[0] + o, ex1);
     stv<V>(D.E[1] + o, ey1);
