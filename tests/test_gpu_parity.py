@@ -297,3 +297,26 @@ def test_anisotropic_cells_y_polarisation_and_phase(pic, oracle_mod):
     assert np.abs(Fo[1]).max() > 10 * np.abs(Fo[0]).max()  # polarised along y
     assert len(o.particles()["id"]) > 100
     g.close()
+
+
+def test_particles_then_advance_then_fields_fp64(pic, oracle_mod):
+    """Phases in a split order: the push, the step advance, and only then the
+    field pass.  The E step must still read the current that push deposited
+    (it skips only planes no particle could reach since the last field pass)."""
+    cfg = wl.small_slab(precision="fp64")
+    o = oracle_mod.Sim(cfg)
+    o.step(45)
+    st = oracle_state_for_gpu(o)
+    g = pic.Simulation(cfg)
+    g.load_state(st)
+    g.step(1)                      # a whole step, so the host-write flags are spent
+    o2 = _oracle_clone_step(oracle_mod, cfg, st)
+    for sim in (g, o2):
+        sim.phases(pic.PHASE_PARTICLES | pic.PHASE_ADVANCE)
+        sim.phases(pic.PHASE_FIELDS)
+    Fg, Fo = g.fields(), o2.fields()
+    assert np.abs(Fo[6:9]).max() == 0.0 and len(o2.particles()["id"]) > 0
+    assert not np.any(Fg[6:9]), "the E step left current behind"
+    nz_comps = [c for c in range(15) if np.linalg.norm(Fo[c]) > 0]
+    assert_fields_close(Fg, Fo, TOL64, comps=nz_comps, what="split phases")
+    g.close()
