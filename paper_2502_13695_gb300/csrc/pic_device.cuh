@@ -235,19 +235,29 @@ __host__ __device__ __forceinline__ float dawson_w<float>(float z) {
   return dawson<float>(z);
 }
 
-// Square root of a Dawson argument y > 0: in FP32 on the device y rsqrt(y)
-// (within a few ulp; the FP32 Dawson table is good to 1.3e-7 anyway), the
-// correctly rounded root elsewhere.
+// Dawson's F at z = sqrt(y), y > 0, for the Keldysh series (which has y).
+// FP32 on the device: r = rsqrt(y); below z = 5 the table at z = y r (the
+// rsqrt is within a few ulp; the table is good to 1.3e-7); from z = 5 the
+// asymptotic series with 1/(2 z^2) = r^2 / 2 and 1/(2 z) = r / 2, so with no
+// division.  Elsewhere the correctly rounded root and dawson_w.
 template <class R>
-__host__ __device__ __forceinline__ R dawson_arg_sqrt(R y) {
-  return sqrt(y);
+__host__ __device__ __forceinline__ R dawson_of_square(R y) {
+  return dawson_w<R>(sqrt(y));
 }
 template <>
-__host__ __device__ __forceinline__ float dawson_arg_sqrt<float>(float y) {
+__host__ __device__ __forceinline__ float dawson_of_square<float>(float y) {
 #ifdef __CUDA_ARCH__
-  return y * rsqrtf(y);
+  const float r = rsqrtf(y);
+  if (y >= 25.0f) {
+    const float inv = 0.5f * r * r;
+    float s = 1.0f;
+#pragma unroll
+    for (int k = DawsonCfg<float>::asym; k >= 1; --k) s = fmaf(float(2 * k - 1) * inv, s, 1.0f);
+    return s * (0.5f * r);
+  }
+  return dawson_w<float>(y * r);
 #else
-  return sqrtf(y);
+  return dawson_w<float>(sqrtf(y));
 #endif
 }
 
@@ -285,10 +295,10 @@ __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterm
   R sum = R(0), rn = R(1);
   int n = 0;
   for (; n < nterms; ++n) {
-    const R z = dawson_arg_sqrt<R>(cd * (base + R(n)));
-    const R term = rn * dawson_w<R>(z);
+    const R y = cd * (base + R(n));  // the Dawson argument squared
+    const R term = rn * dawson_of_square<R>(y);
     sum += term;
-    if (z > R(0.9242) && term * tail <= R(0.5) * Eps<R>::v() * sum) {
+    if (y > R(0.85414564) && term * tail <= R(0.5) * Eps<R>::v() * sum) {  // z > 0.9242
       ++n;
       break;
     }
