@@ -1,15 +1,19 @@
 // Kernels of one PIC step on sm_103a.  Every step of the hot path runs here:
-//   k_push      gather (TSC) + relativistic Boris + move + Esirkepov deposit
+//   k_push      gather (TSC) + relativistic Boris + move + Esirkepov deposit;
+//               marks the cell planes it deposits from
 //   k_bstep     B half steps (Faraday): B and Bh around the particle phase
 //   k_efull     E step with the Lorentz polarisation current (trapezoidal
 //               oscillator), Silver-Mueller z faces with the laser source,
-//               Joule work, J cleared
+//               Joule work, J read and cleared near the marked planes
 //   k_window    cell-centred |E|, exact sliding maximum over one optical
-//               cycle (van Herk / Gil-Werman blocks), Keldysh threshold with
-//               a per-cell cache and an exact low-field skip
+//               cycle (van Herk / Gil-Werman blocks), the per-cell threshold
+//               cache with an exact low-field skip, the work list for
+//   k_keldysh   Keldysh thresholds of the cells whose amplitude changed
 //   k_ionize    Philox draws per alive neutral, electron + hole appends
+//               (planes with no cell above the skip amplitude return at once)
 //   k_hist / k_scan* / k_scatter   counting sort of the pool by cell
-//   k_diag_*    FP64 diagnostics
+//   k_coll_*    binary collisions (cell lists, per-cell preparation, pairs)
+//   k_diag_*    FP64 diagnostics and damage metrics
 #pragma once
 #include "pic_device.cuh"
 
