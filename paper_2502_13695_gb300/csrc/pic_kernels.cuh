@@ -1449,6 +1449,31 @@ struct CollConst {
 // e^2 / (eps0 m_e c^2) = 4 pi r_e [m]: the Debye sum in normalised units.
 constexpr double K_KD = kQe * kQe / (kEps0 * kMe * kC * kC);
 
+// Arithmetic of the collision pass in the working precision.  FP32, whose
+// results are held to 1e-5 of the FP64 oracle, takes the hardware's
+// approximate division, reciprocal square root, exponential and logarithm
+// (each within a few ulp over the ranges met here); FP64 the correctly
+// rounded operations.
+template <class R>
+struct CollMath {
+  __device__ static R div(R a, R b) { return a / b; }
+  __device__ static R rcp(R x) { return R(1) / x; }
+  __device__ static R sqrt_(R x) { return sqrt(x); }
+  __device__ static R exp_(R x) { return exp(x); }
+  __device__ static R log_(R x) { return log(x); }
+  __device__ static R one_minus_exp_m2(R A) { return -expm1(R(-2) * A); }  // 1 - exp(-2A)
+};
+template <>
+struct CollMath<float> {
+  __device__ static float div(float a, float b) { return __fdividef(a, b); }
+  __device__ static float rcp(float x) { return __fdividef(1.0f, x); }
+  __device__ static float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+  __device__ static float exp_(float x) { return __expf(x); }
+  __device__ static float log_(float x) { return __logf(x); }
+  // only for A >= 0.5, where 1 - exp(-2A) >= 0.63 does not cancel
+  __device__ static float one_minus_exp_m2(float A) { return 1.0f - __expf(-2.0f * A); }
+};
+
 template <class R> struct CollTol;
 template <> struct CollTol<double> { static constexpr double v = 4e-16, small = 1e-4; };
 template <> struct CollTol<float> { static constexpr float v = 4e-7f, small = 0.5f; };
@@ -1489,7 +1514,8 @@ __device__ __forceinline__ void langevin_both(R A, R &L, R &Ld) {
     Ld = langevin_d(A);
     return;
   }
-  const R d = -expm1(R(-2) * A), id = R(1) / d, iA = R(1) / A;
+  using M = CollMath<R>;
+  const R d = M::one_minus_exp_m2(A), id = M::rcp(d), iA = M::rcp(A);
   L = smallL ? langevin(A) : (R(2) - d) * id - iA;
   Ld = smallD ? langevin_d(A) : iA * iA - R(4) * (R(1) - d) * id * id;
 }
@@ -1502,12 +1528,13 @@ __device__ __forceinline__ void langevin_both(R A, R &L, R &Ld) {
 // two steps reach FP32 precision; at most 40 steps.
 template <class R>
 __device__ R nanbu_A(R s) {
-  const R t = exp(-s);
-  R A = R(0.95) * t * (R(3) - t * t) / (R(1) - t * t);
+  using M = CollMath<R>;
+  const R t = M::exp_(-s);
+  R A = R(0.95) * t * M::div(R(3) - t * t, R(1) - t * t);
   for (int it = 0; it < 40; ++it) {
     R L, Ld;
     langevin_both(A, L, Ld);
-    const R dA = (t - L) / Ld;
+    const R dA = M::div(t - L, Ld);
     A += dA;
     if (!(fabs(dA) > CollTol<R>::v * A)) break;
   }
@@ -1518,12 +1545,13 @@ __device__ R nanbu_A(R s) {
 // for s >= 6, otherwise the inverse of A exp(A cos chi) / (2 sinh A).
 template <class R>
 __device__ R nanbu_cos(R s, R U) {
+  using M = CollMath<R>;
   R c;
   if (s < R(0.1)) {
-    c = R(1) + s * log(U);
+    c = R(1) + s * M::log_(U);
   } else if (s < R(6)) {
     const R A = nanbu_A(s);
-    c = log(exp(-A) + R(2) * U * sinh(A)) / A;
+    c = M::log_(M::exp_(-A) + R(2) * U * sinh(A)) * M::rcp(A);
   } else {
     c = R(2) * U - R(1);
   }
@@ -1540,10 +1568,11 @@ __device__ R nanbu_cos(R s, R U) {
 template <class R>
 __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R na23, R nb23, R lD,
                              const CollConst &K, const R U[4]) {
-  const R ga = sqrt(R(1) + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]));
-  const R gb = sqrt(R(1) + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]));
+  using M = CollMath<R>;
+  const R ga = M::sqrt_(R(1) + (ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]));
+  const R gb = M::sqrt_(R(1) + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]));
   const R Et = ma * ga + mb * gb;
-  const R iga = R(1) / ga, igb = R(1) / gb, iEt = R(1) / Et;
+  const R iga = M::rcp(ga), igb = M::rcp(gb), iEt = M::rcp(Et);
   R vc[3], va[3], vb[3], pa[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -1553,8 +1582,8 @@ __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R n
     vc[d] = (pa[d] + mb * ub[d]) * iEt;
   }
   const R vc2 = vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2];
-  const R gc = R(1) / sqrt(R(1) - vc2);
-  const R kc = gc * gc / (gc + R(1));  // (gamma_c - 1) / v_c^2
+  const R gc = M::rcp(M::sqrt_(R(1) - vc2));
+  const R kc = M::div(gc * gc, gc + R(1));  // (gamma_c - 1) / v_c^2
   const R vcva = vc[0] * va[0] + vc[1] * va[1] + vc[2] * va[2];
   const R vcvb = vc[0] * vb[0] + vc[1] * vb[1] + vc[2] * vb[2];
   R ps[3];
@@ -1562,32 +1591,32 @@ __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R n
   for (int d = 0; d < 3; ++d) ps[d] = pa[d] + (kc * vcva - gc) * ma * ga * vc[d];
   const R gsa = (R(1) - vcva) * gc * ga, gsb = (R(1) - vcvb) * gc * gb;
   const R p2 = ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2];
-  const R pm = sqrt(p2);
+  const R pm = M::sqrt_(p2);
   if (!(pm > R(0))) return;
-  const R ipm = R(1) / pm;
+  const R ipm = M::rcp(pm);
   const R mab = ma * gsa * mb * gsb;
-  const R mm = mab / p2 + R(1);
+  const R mm = M::div(mab, p2) + R(1);
   const R b0 = R(K.re) * gc * iEt * mm;
   const R bmin = fmax(R(K.lc) * R(0.5) * ipm, b0);
-  const R lnL = fmax(R(1), R(0.5) * log(R(1) + lD * lD / (bmin * bmin)));
-  const R sv = nd * R(K.K1) * lnL * gc * pm / (ma * ga * mb * gb * Et) * mm * mm;
-  const R vrel = Et * pm / (mab * gc);
+  const R lnL = fmax(R(1), R(0.5) * M::log_(R(1) + M::div(lD * lD, bmin * bmin)));
+  const R sv = M::div(nd * R(K.K1) * lnL * gc * pm, ma * ga * mb * gb * Et) * mm * mm;
+  const R vrel = M::div(Et * pm, mab * gc);
   const R dens = fmax(ma * na23, mb * nb23);
-  const R scap = nd * R(K.capc) * (ma + mb) / dens * vrel;
+  const R scap = M::div(nd * R(K.capc) * (ma + mb), dens) * vrel;
   const R s = fmin(sv, scap);
   const R cx = nanbu_cos(s, U[0]);
-  const R sx = sqrt(fmax(R(0), R(1) - cx * cx));
+  const R sx = M::sqrt_(fmax(R(0), R(1) - cx * cx));
   R sp, cp;
   sincospi(R(2) * U[1], &sp, &cp);  // phi = 2 pi U
   const R u[3] = {ps[0] * ipm, ps[1] * ipm, ps[2] * ipm};
   R e1[3], e2v[3];
   if (fabs(u[2]) < R(0.9)) {
-    const R in = R(1) / sqrt(u[0] * u[0] + u[1] * u[1]);
+    const R in = M::rcp(M::sqrt_(u[0] * u[0] + u[1] * u[1]));
     e1[0] = u[1] * in;
     e1[1] = -u[0] * in;
     e1[2] = R(0);
   } else {
-    const R in = R(1) / sqrt(u[1] * u[1] + u[2] * u[2]);
+    const R in = M::rcp(M::sqrt_(u[1] * u[1] + u[2] * u[2]));
     e1[0] = R(0);
     e1[1] = u[2] * in;
     e1[2] = -u[1] * in;
@@ -1603,12 +1632,12 @@ __device__ void collide_pair(R ua[3], R ub[3], R ma, R mb, R wa, R wb, R nd, R n
   // as U w_max < w_other for every U < 1, and safe when a float U rounds to 1)
   const R wmax = fmax(wa, wb);
   if (wb >= wmax || U[2] * wmax < wb) {
-    const R ima = R(1) / ma;
+    const R ima = M::rcp(ma);
 #pragma unroll
     for (int d = 0; d < 3; ++d) ua[d] = (pn[d] + (kc * vpa + ma * gsa * gc) * vc[d]) * ima;
   }
   if (wa >= wmax || U[3] * wmax < wa) {
-    const R imb = R(1) / mb;
+    const R imb = M::rcp(mb);
 #pragma unroll
     for (int d = 0; d < 3; ++d) ub[d] = (-pn[d] + (-kc * vpa + mb * gsb * gc) * vc[d]) * imb;
   }
