@@ -239,6 +239,7 @@ LIMITER = {
     "push": "issue rate of the deposit's ~26 global vector reductions per particle",
     "keldysh": "FP32 issue (series of Dawson terms)",
     "ionize": "load latency and integer issue (Philox draws)",
+    "collide": "issue rate and lane divergence of the per-pair arithmetic",
 }
 
 
