@@ -56,6 +56,8 @@ extern "C" {
 #define PIC_ESTATE (-6)   /* call not valid in the handle's current state */
 #define PIC_ECOLL (-7)    /* a cell held more charged particles than a collision
                              pass handles (128) */
+#define PIC_EIO (-8)      /* a checkpoint file could not be opened, written or
+                             read, or does not match this library's layout */
 
 #define PIC_FP64 0
 #define PIC_FP32 1
@@ -299,6 +301,35 @@ int pic_set_material(pic_handle h, const uint32_t *alive, const double *win);
 /* Accumulators: [U_joule, N_pairs, U_ionization, events]. */
 int pic_get_scalars(pic_handle h, long long *step, double out[4]);
 int pic_set_scalars(pic_handle h, long long step, const double in[4]);
+
+/* ---- checkpoints ---------------------------------------------------------
+ * The paper has no counterpart (its runs are single jobs); this is the
+ * resume path of long runs and of a serving loop that parks simulations.
+ * pic_save writes the handle's configuration, step state and every
+ * device-side quantity to the file at path (host path, created or
+ * replaced; written to path.tmp first and renamed, so a failed save leaves
+ * no partial file under path).  The particle pool is stored up to its live
+ * slot count, so the file holds roughly the state, not the pool capacity.
+ * Synchronous on the handle's stream; a handle holding a latched device
+ * error (PIC_EPOOL, PIC_ECOLL) is not saved.
+ * pic_load creates a handle from such a file, as pic_create would from the
+ * stored configuration (same stream / d_arena / arena_bytes rules; the
+ * arena size is pic_query's for the configuration that
+ * pic_checkpoint_config returns), and restores the state: stepping it gives
+ * the results the saved handle would have given.  Files are read by the
+ * library build and machine family that wrote them.
+ * pic_checkpoint_config reads only the stored configuration: grid, pulse,
+ * layers (the caller provides PIC_MAX_LAYERS entries), layer count, seed
+ * and the step the file was written at (step may be NULL).
+ * Errors: PIC_EINVAL for null pointers; PIC_EIO for a file that cannot be
+ * opened, written or read, is not a checkpoint, or does not match this
+ * library's state layout; otherwise as pic_create. */
+int pic_save(pic_handle h, const char *path);
+int pic_checkpoint_config(const char *path, pic_grid *grid, pic_pulse *pulse,
+                          pic_layer *layers, int *n_layers, uint64_t *seed,
+                          long long *step);
+int pic_load(const char *path, void *stream, void *d_arena, size_t arena_bytes,
+             pic_handle *out);
 
 /* ---- batches: many simulations advanced by one CUDA graph ----------------
  * Advances uneven simulations together (the batched fluence scan): the

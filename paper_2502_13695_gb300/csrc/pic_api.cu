@@ -1531,3 +1531,234 @@ int pic_set_scalars(pic_handle h, long long step, const double in[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the configuration, the host-side step state and the arena.
+// Every device-side quantity of a simulation lives in its arena, so writing
+// the arena back into a simulation created from the same configuration
+// resumes it exactly.  The two pool halves are the exception: only the live
+// half holds state, and only its first nslots entries (slots at or past
+// nslots are written before they are read, and the other half is written by
+// the sort before it becomes live), so those are all that is stored.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kStageBytes = size_t(64) << 20;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, n_layers;
+  pic_grid grid;
+  pic_pulse pulse;
+  uint64_t seed;
+  int64_t step;
+  int32_t since_sort, bh_valid;
+  uint64_t arena_bytes;  // layout check: the plan's total size
+  uint64_t pool_lo, pool_hi;  // arena span of the two pool halves
+  uint64_t nslots;       // live slots stored
+};
+
+struct Span {
+  size_t off, elem;
+};
+
+// arrays of pool half b with their element sizes
+std::vector<Span> pool_arrays(const Plan &P, int b) {
+  std::vector<Span> a{{P.off_pc[b], 4}};
+  for (int d = 0; d < 3; ++d) a.push_back({P.off_po[b][d], (size_t)P.rsz});
+  for (int d = 0; d < 3; ++d) a.push_back({P.off_pu[b][d], (size_t)P.rsz});
+  a.push_back({P.off_pt[b], 4});
+  a.push_back({P.off_pid[b], 8});
+  return a;
+}
+
+size_t pool_hi(const Plan &P) { return align_up(P.off_pid[1] + std::max<size_t>(P.cap * 8, 1)); }
+
+// pinned host buffer through which the arena streams to or from a file
+struct Stage {
+  char *buf = nullptr;
+  ~Stage() {
+    if (buf) cudaFreeHost(buf);
+  }
+};
+
+struct File {
+  FILE *f = nullptr;
+  ~File() {
+    if (f) std::fclose(f);
+  }
+};
+
+int write_span(pic_ctx *h, FILE *f, char *st, size_t off, size_t bytes) {
+  while (bytes) {
+    const size_t n = std::min(bytes, kStageBytes);
+    PIC_CUDA(cudaMemcpyAsync(st, h->arena + off, n, cudaMemcpyDeviceToHost, h->stream));
+    PIC_CUDA(cudaStreamSynchronize(h->stream));
+    h->d2h_bytes += (long long)n;
+    if (std::fwrite(st, 1, n, f) != n) return fail(PIC_EIO, "checkpoint write failed");
+    off += n;
+    bytes -= n;
+  }
+  return PIC_OK;
+}
+
+int read_span(pic_ctx *h, FILE *f, char *st, size_t off, size_t bytes) {
+  while (bytes) {
+    const size_t n = std::min(bytes, kStageBytes);
+    if (std::fread(st, 1, n, f) != n) return fail(PIC_EIO, "checkpoint file is truncated");
+    PIC_CUDA(cudaMemcpyAsync(h->arena + off, st, n, cudaMemcpyHostToDevice, h->stream));
+    PIC_CUDA(cudaStreamSynchronize(h->stream));
+    h->h2d_bytes += (long long)n;
+    off += n;
+    bytes -= n;
+  }
+  return PIC_OK;
+}
+
+// header and layers of a checkpoint file, checked for magic, version and
+// layer count
+int read_head(FILE *f, CkptHeader &hd, std::vector<pic_layer> &layers) {
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1) return fail(PIC_EIO, "not a checkpoint (short header)");
+  if (std::memcmp(hd.magic, kCkptMagic, sizeof(kCkptMagic)) != 0)
+    return fail(PIC_EIO, "not a checkpoint (bad magic)");
+  if (hd.version != kCkptVersion) return fail(PIC_EIO, "unsupported checkpoint version");
+  if (hd.n_layers > PIC_MAX_LAYERS) return fail(PIC_EIO, "checkpoint has a bad layer count");
+  layers.resize(hd.n_layers);
+  if (hd.n_layers && std::fread(layers.data(), sizeof(pic_layer), hd.n_layers, f) != hd.n_layers)
+    return fail(PIC_EIO, "checkpoint file is truncated");
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_save(pic_handle h, const char *path) {
+  if (!h || !path) return fail(PIC_EINVAL, "null pointer");
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  int rc = check_sticky(h);
+  if (rc) return rc;
+  const Plan &P = h->P;
+  unsigned long long ns = 0;
+  rc = copy_out(h, P.off_nslots, &ns, 8);
+  if (rc) return rc;
+  ns = std::min<unsigned long long>(ns, (unsigned long long)P.cap);
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, sizeof(kCkptMagic));
+  hd.version = kCkptVersion;
+  hd.n_layers = (uint32_t)P.layers.size();
+  hd.grid = P.g;
+  hd.pulse = P.pulse;
+  hd.seed = h->seed;
+  hd.step = h->step;
+  hd.since_sort = h->since_sort;
+  hd.bh_valid = h->bh_valid ? 1 : 0;
+  hd.arena_bytes = P.total;
+  hd.pool_lo = P.off_pc[0];
+  hd.pool_hi = pool_hi(P);
+  hd.nslots = ns;
+  // the live pool half: the one the particle pointers address
+  const int32_t *pcell = h->fp64 ? h->c64.d.pcell : h->c32.d.pcell;
+  const int live = (const char *)pcell == h->arena + P.off_pc[1] ? 1 : 0;
+  // written to path.tmp and renamed, so that a failed save leaves no
+  // partial file under the final name
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    Stage st;
+    PIC_CUDA(cudaMallocHost((void **)&st.buf, kStageBytes));
+    File f;
+    f.f = std::fopen(tmp.c_str(), "wb");
+    if (!f.f) return fail(PIC_EIO, "cannot open " + tmp + " for writing");
+    if (std::fwrite(&hd, sizeof(hd), 1, f.f) != 1 ||
+        (hd.n_layers &&
+         std::fwrite(P.layers.data(), sizeof(pic_layer), hd.n_layers, f.f) != hd.n_layers))
+      rc = fail(PIC_EIO, "checkpoint write failed");
+    if (!rc) rc = write_span(h, f.f, st.buf, 0, hd.pool_lo);
+    if (!rc) rc = write_span(h, f.f, st.buf, hd.pool_hi, P.total - hd.pool_hi);
+    for (const Span &a : pool_arrays(P, live))
+      if (!rc) rc = write_span(h, f.f, st.buf, a.off, ns * a.elem);
+    if (!rc && std::fflush(f.f) != 0) rc = fail(PIC_EIO, "checkpoint write failed");
+    const int closed = std::fclose(f.f);
+    f.f = nullptr;
+    if (!rc && closed != 0) rc = fail(PIC_EIO, "checkpoint write failed");
+  }
+  if (rc) {
+    std::remove(tmp.c_str());
+    return rc;
+  }
+  if (std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(PIC_EIO, std::string("cannot rename the checkpoint to ") + path);
+  }
+  return PIC_OK;
+}
+
+int pic_checkpoint_config(const char *path, pic_grid *grid, pic_pulse *pulse, pic_layer *layers,
+                          int *n_layers, uint64_t *seed, long long *step) {
+  if (!path || !grid || !pulse || !layers || !n_layers || !seed)
+    return fail(PIC_EINVAL, "null pointer");
+  File f;
+  f.f = std::fopen(path, "rb");
+  if (!f.f) return fail(PIC_EIO, std::string("cannot open ") + path);
+  CkptHeader hd;
+  std::vector<pic_layer> ly;
+  const int rc = read_head(f.f, hd, ly);
+  if (rc) return rc;
+  *grid = hd.grid;
+  *pulse = hd.pulse;
+  std::copy(ly.begin(), ly.end(), layers);
+  *n_layers = (int)hd.n_layers;
+  *seed = hd.seed;
+  if (step) *step = hd.step;
+  return PIC_OK;
+}
+
+int pic_load(const char *path, void *stream, void *d_arena, size_t arena_bytes, pic_handle *out) {
+  if (!path || !out) return fail(PIC_EINVAL, "null pointer");
+  *out = nullptr;
+  File f;
+  f.f = std::fopen(path, "rb");
+  if (!f.f) return fail(PIC_EIO, std::string("cannot open ") + path);
+  CkptHeader hd;
+  std::vector<pic_layer> ly;
+  int rc = read_head(f.f, hd, ly);
+  if (rc) return rc;
+  pic_material m;
+  std::memset(&m, 0, sizeof(m));
+  m.n_layers = (int)hd.n_layers;
+  m.layers = ly.data();
+  pic_handle h = nullptr;
+  rc = pic_create(&hd.grid, &m, &hd.pulse, hd.seed, stream, d_arena, arena_bytes, &h);
+  if (rc) return rc;
+  const Plan &P = h->P;
+  if (hd.arena_bytes != P.total || hd.pool_lo != P.off_pc[0] || hd.pool_hi != pool_hi(P) ||
+      hd.nslots > (uint64_t)P.cap || hd.step < 0) {
+    pic_destroy(h);
+    return fail(PIC_EIO, "checkpoint layout does not match this library's");
+  }
+  {
+    Stage st;
+    cudaError_t e = cudaMallocHost((void **)&st.buf, kStageBytes);
+    if (e != cudaSuccess) rc = fail(PIC_ECUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    // pic_create's initialisation is on the same stream, before these copies
+    if (!rc) rc = read_span(h, f.f, st.buf, 0, hd.pool_lo);
+    if (!rc) rc = read_span(h, f.f, st.buf, hd.pool_hi, P.total - hd.pool_hi);
+    for (const Span &a : pool_arrays(P, 0))
+      if (!rc) rc = read_span(h, f.f, st.buf, a.off, hd.nslots * a.elem);
+    if (!rc && std::fgetc(f.f) != EOF) rc = fail(PIC_EIO, "checkpoint file has trailing data");
+  }
+  if (rc) {
+    pic_destroy(h);
+    return rc;
+  }
+  h->step = hd.step;
+  h->since_sort = hd.since_sort;
+  h->bh_valid = hd.bh_valid != 0;
+  *out = h;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,8 @@ from . import build as _build
 
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_EPOOL, PIC_ETIMEOUT, PIC_ECUDA, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PIC_ECOLL = -7
+PIC_EIO = -8
+PIC_MAX_LAYERS = 128
 PIC_FP64, PIC_FP32 = 0, 1
 PHASE_PARTICLES, PHASE_FIELDS, PHASE_WINDOW, PHASE_IONIZE, PHASE_ADVANCE = 1, 2, 4, 8, 16
 PHASE_COLLIDE = 32
@@ -28,7 +30,8 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
            "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
-           "pic_damage", "pic_get_intensity_max"]
+           "pic_damage", "pic_get_intensity_max", "pic_save", "pic_load",
+           "pic_checkpoint_config"]
 PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other", "collide"]
 
 
@@ -132,6 +135,10 @@ def lib():
         L.pic_batch_sync.argtypes = [vp]
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_profile_read.argtypes = [vp, vp, vp]
+        L.pic_save.argtypes = [vp, ctypes.c_char_p]
+        L.pic_load.argtypes = [ctypes.c_char_p, vp, vp, ctypes.c_size_t, P(vp)]
+        L.pic_checkpoint_config.argtypes = [ctypes.c_char_p, P(Grid), P(Pulse), P(Layer),
+                                            P(i), P(ctypes.c_uint64), P(ll)]
         _lib = L
     return _lib
 
@@ -181,6 +188,31 @@ def c_structs(cfg: dict):
     return g, m, p, layers
 
 
+def checkpoint_config(path: str) -> dict:
+    """The workload dictionary a checkpoint file was written from (the
+    inverse of c_structs), plus the step it was written at."""
+    g, p = Grid(), Pulse()
+    layers = (Layer * PIC_MAX_LAYERS)()
+    n, seed, step = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_longlong()
+    _check(lib().pic_checkpoint_config(os.fsencode(path), ctypes.byref(g), ctypes.byref(p),
+                                       layers, ctypes.byref(n), ctypes.byref(seed),
+                                       ctypes.byref(step)))
+    cfg = dict(nx=g.nx, ny=g.ny, nz=g.nz, dx=g.dx, dy=g.dy, dz=g.dz, cfl=g.cfl,
+               precision="fp64" if g.precision == PIC_FP64 else "fp32",
+               pool_factor=g.pool_factor, keldysh_terms=g.keldysh_terms,
+               sort_interval=g.sort_interval, imax_every=g.imax_every,
+               coll_every=g.coll_every, seed=int(seed.value), step=int(step.value))
+    cfg["layers"] = [
+        {f: getattr(layers[q], f) for f in (
+            "z0", "z1", "ppc", "n_index", "gap_eV", "me_star", "mh_star", "n_mol",
+            "omega0_eV", "damping", "temp_eV", "mol_mass_amu", "e_melt", "e_boil",
+            "e_dissoc")} for q in range(n.value)]
+    cfg["pulse"] = {"lambda": p.lam, "fwhm": p.fwhm, "fluence": p.fluence, "cep": p.cep,
+                    "t_peak": p.t_peak, "pol": p.pol,
+                    "shape": "sin2" if p.shape == 1 else "gauss", "w0": p.w0}
+    return cfg
+
+
 def _info_dict(info: Info) -> dict:
     return {f: getattr(info, f) for f, _ in Info._fields_}
 
@@ -195,7 +227,7 @@ def query(cfg: dict) -> dict:
 class Simulation:
     """One simulation resident on the current CUDA device."""
 
-    def __init__(self, cfg: dict, stream=None, arena="torch"):
+    def __init__(self, cfg: dict, stream=None, arena="torch", _checkpoint=None):
         import torch
         self.cfg = cfg
         g, m, p, keep = c_structs(cfg)
@@ -211,14 +243,29 @@ class Simulation:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        _check(lib().pic_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
-                                int(cfg["seed"]), ctypes.c_void_p(stream.cuda_stream),
-                                ctypes.c_void_p(ptr) if ptr else None, nbytes, ctypes.byref(h)))
+        if _checkpoint is not None:
+            _check(lib().pic_load(os.fsencode(_checkpoint), ctypes.c_void_p(stream.cuda_stream),
+                                  ctypes.c_void_p(ptr) if ptr else None, nbytes,
+                                  ctypes.byref(h)))
+        else:
+            _check(lib().pic_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                                    int(cfg["seed"]), ctypes.c_void_p(stream.cuda_stream),
+                                    ctypes.c_void_p(ptr) if ptr else None, nbytes,
+                                    ctypes.byref(h)))
         self._h = h
         self.static = _info_dict(info)
         self.dt, self.NW, self.nmat = info.dt, info.NW, info.nmat
         self.nfield = info.nfield
         self.fp64 = g.precision == PIC_FP64
+
+    @classmethod
+    def load(cls, path: str, stream=None, arena="torch") -> "Simulation":
+        """Resume a simulation from a file written by save()."""
+        return cls(checkpoint_config(path), stream=stream, arena=arena, _checkpoint=path)
+
+    def save(self, path: str):
+        """Write a checkpoint (configuration, step state, device state)."""
+        _check(lib().pic_save(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
