@@ -352,6 +352,50 @@ int pic_batch_step(pic_batch b, int n_steps);
 int pic_batch_sync(pic_batch b);
 int pic_batch_destroy(pic_batch b);
 
+/* ---- serving: continuous batching of submitted simulations ---------------
+ * The paper runs one simulation per job; this is the request loop of a
+ * fluence or stack sweep served on one GPU.  A server owns a host worker
+ * thread on the device current at pic_serve_create.  Submitted requests
+ * wait in submission order; the head of the queue is admitted as soon as
+ * its state (pic_query's arena_bytes) fits budget_bytes next to the running
+ * simulations, whose state stays resident on the device until they finish.
+ * The running simulations with at least `quantum` steps left advance
+ * together from one CUDA graph (pic_batch_*, rebuilt when that set
+ * changes); one with fewer steps left takes them alone.  A finished
+ * request's FP64 diagnostics are kept until its ticket is polled, and its
+ * device memory is released at once.
+ *   pic_serve_create  : budget_bytes >= 1, quantum >= 1 steps.
+ *   pic_serve_submit  : copies the configuration (as pic_create takes it)
+ *                       and returns a ticket.  n_bins, e_min_eV, e_max_eV
+ *                       ask for the spectrum of pic_diagnostics (n_bins 0:
+ *                       none); fields_out, if not NULL, is a host array of
+ *                       15 * nfield doubles (layout of pic_get_fields) that
+ *                       receives the final fields and must stay valid until
+ *                       the ticket is polled done.  PIC_EINVAL for a bad
+ *                       configuration or request, PIC_ENOMEM for one whose
+ *                       state alone exceeds the budget.
+ *   pic_serve_poll    : waits up to wait_ms for the ticket; *done = 1 once it
+ *                       has finished, then fills diag (its spectrum pointer
+ *                       must hold the submitted n_bins) and times =
+ *                       {submitted, admitted, finished} in seconds since
+ *                       pic_serve_create, releases the ticket and returns
+ *                       the request's own status (PIC_OK, or the error that
+ *                       ended it: PIC_EPOOL, PIC_ECOLL, PIC_ENOMEM, PIC_ECUDA).
+ *                       *done = 0 with PIC_OK while it runs or waits;
+ *                       PIC_EINVAL for an unknown ticket.
+ *   pic_serve_destroy : stops the worker after its current quantum; requests
+ *                       not yet finished are dropped with their state.
+ * The server is thread-safe: submit and poll may come from any thread. */
+typedef struct pic_server_ctx *pic_server;
+int pic_serve_create(double budget_bytes, int quantum, pic_server *out);
+int pic_serve_submit(pic_server s, const pic_grid *grid, const pic_material *mat,
+                     const pic_pulse *pulse, uint64_t seed, long long n_steps,
+                     int n_bins, double e_min_eV, double e_max_eV,
+                     double *fields_out, long long *ticket);
+int pic_serve_poll(pic_server s, long long ticket, int wait_ms, int *done,
+                   pic_diag *diag, double times[3]);
+int pic_serve_destroy(pic_server s);
+
 /* ---- allocation-free field energy -------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory, such as code that runs while a stream is being

@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpicgb300.so")
-SOURCES = [os.path.join(CSRC, "pic_api.cu"), os.path.join(CSRC, "pic_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, "pic_api.cu"), os.path.join(CSRC, "pic_noalloc.cu"),
+           os.path.join(CSRC, "pic_serve.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("pic_device.cuh", "pic_kernels.cuh",
                                                   "dawson_f32_table.inc")] + [
     os.path.join(os.path.dirname(HERE), "include", "pic.h")]

@@ -31,7 +31,8 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
            "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
            "pic_damage", "pic_get_intensity_max", "pic_save", "pic_load",
-           "pic_checkpoint_config"]
+           "pic_checkpoint_config", "pic_serve_create", "pic_serve_submit",
+           "pic_serve_poll", "pic_serve_destroy"]
 PROF_NAMES = ["push", "fields", "keldysh", "window", "ionize", "sort", "other", "collide"]
 
 

@@ -1,20 +1,24 @@
 """Request loop with continuous batching over simulations resident on one GPU.
 
-Requests (a workload configuration and a step count) arrive over time.  A
-request is admitted as soon as its state fits the device-memory budget next
-to the running ones (the arena size comes from pic_query); every admitted
-simulation keeps its fields, particles and RNG state on the device until it
-finishes.  Running simulations advance together in quanta of 32 steps from
-one CUDA graph (pic_batch_*, rebuilt when the running set changes), so the
-work of requests that arrived at different times overlaps on the GPU; a
-request whose remaining steps are fewer than a quantum finishes alone.  A
-finished request returns its FP64 diagnostics and is released.
+The loop itself is native (pic_serve_* in csrc/pic_serve.cpp): a host
+worker thread admits submitted requests in submission order as soon as
+their state fits the device-memory budget next to the running ones (the
+arena size comes from pic_query), keeps every admitted simulation's fields,
+particles and RNG state on the device until it finishes, advances the
+running ones together in quanta of 32 steps from one CUDA graph
+(pic_batch_*, rebuilt when the running set changes), lets a request with
+fewer steps left than a quantum finish alone, and returns a finished
+request's FP64 diagnostics.  This module submits requests at their arrival
+times and collects the results (argument marshalling only).
 """
 from __future__ import annotations
 
 import collections
+import ctypes
 import time
 from dataclasses import dataclass, field
+
+import numpy as np
 
 from . import pic
 
@@ -42,85 +46,78 @@ class Result:
         return self.done_s - self.arrival_s
 
 
+def _bind(L):
+    if getattr(L, "_serve_bound", False):
+        return L
+    vp, P = ctypes.c_void_p, ctypes.POINTER
+    L.pic_serve_create.argtypes = [ctypes.c_double, ctypes.c_int, P(vp)]
+    L.pic_serve_submit.argtypes = [vp, P(pic.Grid), P(pic.Material), P(pic.Pulse),
+                                   ctypes.c_uint64, ctypes.c_longlong, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double, vp,
+                                   P(ctypes.c_longlong)]
+    L.pic_serve_poll.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, P(ctypes.c_int),
+                                 P(pic.Diag), P(ctypes.c_double)]
+    L.pic_serve_destroy.argtypes = [vp]
+    L._serve_bound = True
+    return L
+
+
 class Server:
     def __init__(self, budget_bytes: float, quantum: int = QUANTUM, keep_state=False):
         self.budget = float(budget_bytes)
         self.quantum = int(quantum)
         self.keep_state = keep_state
-        self.used = 0.0
-        self.active = collections.OrderedDict()  # rid -> [req, sim, remaining, admit_s, bytes]
-        self._batch = None
-        self._batch_ids = ()
 
-    # -- internals -----------------------------------------------------------
-    def _rebatch(self):
-        ids = tuple(rid for rid, a in self.active.items() if a[2] >= self.quantum)
-        if ids == self._batch_ids:
-            return
-        if self._batch is not None:
-            self._batch.close()
-            self._batch = None
-        self._batch_ids = ids
-        if ids:
-            self._batch = pic.Batch([self.active[r][1] for r in ids])
-
-    def _admit(self, req: Request, now: float) -> bool:
-        import torch
-        need = float(pic.query(req.cfg)["arena_bytes"])
-        if need > self.budget:
-            raise ValueError(f"request {req.rid} needs {need:.3g} B, above the whole budget")
-        if self.used + need > self.budget:
-            return False
-        sim = pic.Simulation(req.cfg, stream=torch.cuda.Stream())
-        self.active[req.rid] = [req, sim, req.steps, now, need]
-        self.used += need
-        return True
-
-    def _retire(self, rid, now, results):
-        req, sim, _, admit_s, need = self.active.pop(rid)
-        sim.sync()
-        d = sim.diagnostics()
-        if self.keep_state:
-            d["fields"] = sim.fields()
-        results.append(Result(rid, req.arrival_s, admit_s, now, d))
-        sim.close()
-        self.used -= need
-
-    # -- public ------------------------------------------------------------------
     def run(self, requests, clock=None):
         """Serve `requests` (arrival_s relative to the start) in real time;
-        returns the results in completion order."""
+        returns the results in completion order.  Times are seconds from the
+        start on the server's steady clock."""
         clock = clock or time.perf_counter
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
-        waiting = collections.deque()
-        results = []
+        L = _bind(pic.lib())
+        srv = ctypes.c_void_p()
+        pic._check(L.pic_serve_create(self.budget, self.quantum, ctypes.byref(srv)))
         t0 = clock()
-        while pending or waiting or self.active:
+        try:
+            return self._loop(L, srv, requests, clock, t0)
+        finally:
+            L.pic_serve_destroy(srv)
+
+    def _loop(self, L, srv, requests, clock, t0):
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        out = {}  # ticket -> (request, structs kept alive, fields buffer)
+        results = []
+        while pending or out:
             now = clock() - t0
             while pending and pending[0].arrival_s <= now:
-                waiting.append(pending.popleft())
-            while waiting and self._admit(waiting[0], now):
-                waiting.popleft()
-            if not self.active:
-                if pending:
-                    time.sleep(max(0.0, min(0.05, pending[0].arrival_s - now)))
-                continue
-            self._rebatch()
-            if self._batch is not None:
-                self._batch.step(self.quantum)
-                for rid in self._batch_ids:
-                    self.active[rid][2] -= self.quantum
-            for rid, a in self.active.items():
-                if rid not in self._batch_ids and 0 < a[2] < self.quantum:
-                    a[1].step(a[2])
-                    a[2] = 0
-            if self._batch is not None:
-                self._batch.sync()
-            now = clock() - t0
-            for rid in [r for r, a in self.active.items() if a[2] <= 0]:
-                self._retire(rid, now, results)
-        if self._batch is not None:
-            self._batch.close()
-            self._batch = None
-            self._batch_ids = ()
+                req = pending.popleft()
+                g, m, p, keep = pic.c_structs(req.cfg)
+                F = None
+                if self.keep_state:
+                    F = np.zeros((15, req.cfg["nz"] + 1, req.cfg["ny"], req.cfg["nx"]))
+                t = ctypes.c_longlong()
+                pic._check(L.pic_serve_submit(srv, ctypes.byref(g), ctypes.byref(m),
+                                              ctypes.byref(p), int(req.cfg["seed"]),
+                                              int(req.steps), 0, 0.0, 1.0, pic._ptr(F),
+                                              ctypes.byref(t)))
+                out[t.value] = (req, (g, m, p, keep), F)
+            for t in list(out):
+                done, d = ctypes.c_int(), pic.Diag()
+                times = (ctypes.c_double * 3)()
+                rc = L.pic_serve_poll(srv, t, 0, ctypes.byref(done), ctypes.byref(d), times)
+                if not done.value:
+                    pic._check(rc)
+                    continue
+                req, _, F = out.pop(t)
+                pic._check(rc)
+                diag = {f: getattr(d, f) for f, _ in pic.Diag._fields_
+                        if f not in ("reserved", "reserved2", "region", "spectrum")}
+                diag["spectrum"] = np.zeros(0)
+                if F is not None:
+                    diag["fields"] = F
+                results.append(Result(req.rid, req.arrival_s, times[1], times[2], diag))
+            wait = 1e-3
+            if pending:
+                wait = min(wait, max(0.0, pending[0].arrival_s - (clock() - t0)))
+            time.sleep(wait)
+        results.sort(key=lambda r: r.done_s)
         return results

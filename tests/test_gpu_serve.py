@@ -59,3 +59,80 @@ def test_admission_waits_for_memory(mods):
     res = {r.rid: r for r in serve.Server(budget_bytes=budget).run(reqs)}
     assert res[2].admit_s >= min(res[0].done_s, res[1].done_s) - 1e-6
     assert res[0].admit_s <= res[2].admit_s
+
+
+def _submit(pic, L, srv, cfg, steps, n_bins=0, e_max=1.0):
+    import ctypes
+    g, m, p, keep = pic.c_structs(cfg)
+    t = ctypes.c_longlong()
+    rc = L.pic_serve_submit(srv, ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                            int(cfg["seed"]), steps, n_bins, 0.0, e_max, None, ctypes.byref(t))
+    return rc, t.value
+
+
+def _wait(pic, L, srv, ticket, n_bins=0):
+    import ctypes
+    spec = np.zeros(max(1, n_bins))
+    d = pic.Diag()
+    d.n_bins = n_bins
+    d.spectrum = spec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    done, times = ctypes.c_int(), (ctypes.c_double * 3)()
+    for _ in range(600):  # at most ten minutes
+        rc = L.pic_serve_poll(srv, ticket, 1000, ctypes.byref(done), ctypes.byref(d), times)
+        if done.value:
+            return rc, d, spec[:n_bins], list(times)
+        assert rc == pic.PIC_OK
+    pytest.fail("request did not finish")
+
+
+def test_native_server_statuses_and_spectrum(mods):
+    import ctypes
+    import time
+    pic, serve = mods
+    L = serve._bind(pic.lib())
+    ok = wl.small_slab(precision="fp64", seed=31)
+    over = wl.small_slab(precision="fp32", fluence=20.0, seed=32)
+    over["pool_factor"] = 0.0  # 1024 spare slots: ionisation outgrows the pool
+    srv = ctypes.c_void_p()
+    assert L.pic_serve_create(1e12, 32, ctypes.byref(srv)) == pic.PIC_OK
+    try:
+        rc1, t1 = _submit(pic, L, srv, ok, 45, n_bins=16, e_max=50.0)
+        rc2, t2 = _submit(pic, L, srv, over, 100)
+        assert rc1 == pic.PIC_OK and rc2 == pic.PIC_OK and t1 != t2
+        rc, d, spec, times = _wait(pic, L, srv, t1, 16)
+        assert rc == pic.PIC_OK and d.step == 45
+        assert 0.0 <= times[0] <= times[1] <= times[2]
+        rc, _, _, _ = _wait(pic, L, srv, t2)
+        assert rc == pic.PIC_EPOOL
+        assert b"pool" in pic.lib().pic_last_error()
+        # a collected ticket is released
+        done = ctypes.c_int()
+        assert L.pic_serve_poll(srv, t1, 0, ctypes.byref(done), None, None) == pic.PIC_EINVAL
+    finally:
+        L.pic_serve_destroy(srv)
+    sim = pic.Simulation(ok)
+    sim.step(45)
+    alone = sim.diagnostics(n_bins=16, e_min_eV=0.0, e_max_eV=50.0)
+    sim.close()
+    assert d.N_pairs == pytest.approx(alone["N_pairs"], rel=1e-10)
+    assert d.U_kinetic == pytest.approx(alone["U_kinetic"], rel=1e-10)
+    assert spec.sum() > 0 and np.allclose(spec, alone["spectrum"], rtol=1e-10, atol=0.0)
+
+    # a request whose state alone exceeds the budget is refused at submit
+    srv = ctypes.c_void_p()
+    assert L.pic_serve_create(1e6, 32, ctypes.byref(srv)) == pic.PIC_OK
+    try:
+        rc, _ = _submit(pic, L, srv, ok, 10)
+        assert rc == pic.PIC_ENOMEM
+    finally:
+        L.pic_serve_destroy(srv)
+
+    # destroying a server with work in flight drops it after the current quantum
+    srv = ctypes.c_void_p()
+    assert L.pic_serve_create(1e12, 32, ctypes.byref(srv)) == pic.PIC_OK
+    rc, t = _submit(pic, L, srv, wl.small_slab(precision="fp32", seed=33), 100000)
+    assert rc == pic.PIC_OK
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    L.pic_serve_destroy(srv)
+    assert time.perf_counter() - t0 < 30.0
