@@ -1,6 +1,7 @@
 // C ABI of the GB300 PIC library (declared in include/pic.h): validation,
 // device memory layout, step scheduling, diagnostics and state access.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -335,6 +336,10 @@ struct pic_ctx {
   std::vector<Rec> recs;
   size_t used = 0;
   int open_cls = -1;
+  // NVTX range per kernel class, for timeline tools (ids, not the thread's
+  // push/pop stack, so a range an error path leaves open unbalances nothing)
+  nvtxRangeId_t nvtx[4] = {};
+  int nvtx_n = 0;
 };
 
 namespace {
@@ -439,8 +444,14 @@ void bind(pic_ctx *h) {
 int grid_blocks(long long n) { return (int)std::max<long long>(1, (n + kThreads - 1) / kThreads); }
 constexpr int kPersistentBlocks = 152 * 8;
 
-// Event pair around a group of launches of one class (no-op unless profiling).
+const char *const kProfNames[PIC_PROF_N] = {"pic push",   "pic fields", "pic keldysh",
+                                             "pic window", "pic ionize", "pic sort",
+                                             "pic other",  "pic collide"};
+
+// Event pair around a group of launches of one class (no-op unless
+// profiling), inside an NVTX range named for the class.
 void prof_begin(pic_ctx *h, int cls) {
+  if (h->nvtx_n < 4) h->nvtx[h->nvtx_n++] = nvtxRangeStartA(kProfNames[cls]);
   if (!h->profiling) return;
   if (h->used == h->recs.size()) {
     pic_ctx::Rec r{cls, nullptr, nullptr};
@@ -454,6 +465,7 @@ void prof_begin(pic_ctx *h, int cls) {
 }
 
 void prof_end(pic_ctx *h) {
+  if (h->nvtx_n > 0) nvtxRangeEnd(h->nvtx[--h->nvtx_n]);
   if (!h->profiling || h->open_cls < 0) return;
   cudaEventRecord(h->recs[h->used].b, h->stream);
   h->used++;
