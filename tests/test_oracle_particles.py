@@ -9,6 +9,8 @@ Gather     : a field linear along any axis is gathered exactly at the particle
 Esirkepov  : discrete continuity (rho^{n+1} - rho^n)/dt + div J = 0 at every
              node to roundoff, for random moves that cross cells and the
              periodic seam.
+Outflow    : the two-cell z band at both faces, and the current moment
+             sum J dV = q w displacement / dt of particles that leave.
 """
 import math
 
@@ -233,3 +235,46 @@ def test_esirkepov_discrete_continuity(oracle_mod):
     p = s.particles()
     moved = np.sum(p["cell"] != P["cell"][np.argsort(P["id"])])
     assert moved > 300
+
+
+def test_z_outflow_band_and_current_moment(oracle_mod):
+    """A particle whose cell after the move lies within two cells of a z face
+    (k < 2 or k >= nz - 2) is deleted after it deposits its current; others
+    stay.  With no field the momentum is unchanged, so the moves follow by
+    hand.  Each particle's deposited current, summed over the grid times the
+    cell volume, equals its charge times its displacement over dt: the first
+    moment of a charge-conserving deposit, whether or not the particle
+    leaves."""
+    nx, ny, nz = 8, 8, 32
+    layers = [wl.layer(10, 20, wl.SILICA, 1, 0.0)]
+    u = np.array([2e7, -3e7, 2.5e8])
+    cases = [  # (k, z offset, sign of u_z, kept)
+        (nz - 3, 0.9, +1, False),  # moves into plane nz - 2
+        (nz - 3, 0.3, +1, True),
+        (2, 0.1, -1, False),       # moves into plane 1
+        (2, 0.5, -1, True),
+    ]
+    for q, (k, oz, sgn, kept) in enumerate(cases):
+        cfg, s = _sim(oracle_mod, nx=nx, ny=ny, nz=nz, layers=layers)
+        uu = u * np.array([1.0, 1.0, sgn])
+        cell = (k * ny + 3) * nx + 4
+        off = np.array([0.4, 0.6, oz])
+        s.set_particles(dict(id=np.array([2 * q + 1], np.uint64), cell=np.array([cell], np.int32),
+                             off=off[None, :], u=uu[None, :], tag=np.array([1], np.uint32)))
+        g = math.sqrt(1 + (uu * uu).sum() / C ** 2)
+        disp = s.dt * uu / g  # metres
+        new_z = oz + disp[2] / cfg["dz"]
+        k_new = k + math.floor(new_z)
+        assert (k_new < 2 or k_new >= nz - 2) != kept  # the cases straddle the band
+        s.phases(1)
+        assert s.np == (1 if kept else 0), (q, s.np)
+        if kept:
+            p = s.particles()
+            assert p["cell"][0] // (nx * ny) == k_new
+            assert p["off"][0][2] == pytest.approx(new_z - math.floor(new_z), abs=1e-12)
+        G = s.fields()
+        V = cfg["dx"] * cfg["dy"] * cfg["dz"]
+        w = wl.SILICA["n_mol"] * V
+        for d in range(3):
+            moment = G[6 + d].sum() * V
+            assert moment == pytest.approx(QE * w * disp[d] / s.dt, rel=1e-12), (q, d)
