@@ -202,7 +202,7 @@ def oracle_sample(prerun, steps):
     return psteps / dt, ncell * steps / dt, dict(
         sample=f"4x4x512 column of the 128x128x512 silica workload (same z profile), "
                f"steps {prerun}..{prerun + steps}, {n0} charged macroparticles at start",
-        seconds=dt, cores=1)
+        seconds=dt, cores=1, workload=cfg["name"], grid=[cfg["nx"], cfg["ny"], cfg["nz"]])
 
 
 def run_reference(args, rank, world, dist):
@@ -214,8 +214,9 @@ def run_reference(args, rank, world, dist):
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * info["seconds"] / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "silica-128x128x512-fp32 (oracle on a 4x4 column)",
-                       "cell_updates_per_s": cu},
+            "config": {"workload": info["workload"], "grid": info["grid"], "ppc": 8,
+                       "prerun_steps": args.prerun, "parallelism": "FP64 oracle, one host core"},
+            "cell_updates_per_s": cu,
             "cpu_baseline": {"value": ps, "unit": UNIT, "cores": info["cores"],
                              "kind": "oracle", "sample": info["sample"]},
             "e2e": {"value": ps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
