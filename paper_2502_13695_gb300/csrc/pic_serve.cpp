@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -88,6 +89,7 @@ struct pic_server_ctx {
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
   void run();
+  void loop();
   void finish(Running &r, int status, const std::string &msg);
   void admit();
   void rebatch();
@@ -175,7 +177,34 @@ void pic_server_ctx::rebatch() {
   }
 }
 
+// The worker: the loop, and if host memory runs out inside it (the only
+// exception it can meet), every request still held fails with PIC_ENOMEM.
 void pic_server_ctx::run() {
+  try {
+    loop();
+  } catch (const std::exception &e) {
+    const std::string m = std::string("server worker stopped: ") + e.what();
+    if (batch) pic_batch_destroy(batch);
+    batch = nullptr;
+    for (Running &r : running) {
+      if (r.h) pic_destroy(r.h);
+      if (r.stream) cudaStreamDestroy(r.stream);
+    }
+    running.clear();
+    std::lock_guard<std::mutex> lk(mu);
+    stop = true;  // later submits are refused
+    for (auto &kv : all)
+      if (!kv.second->done) {
+        kv.second->status = PIC_ENOMEM;
+        kv.second->message = m;
+        kv.second->done = true;
+      }
+    waiting.clear();
+    cv_done.notify_all();
+  }
+}
+
+void pic_server_ctx::loop() {
   cudaSetDevice(device);
   for (;;) {
     {
@@ -264,15 +293,21 @@ int pic_serve_create(double budget_bytes, int quantum, pic_server *out) {
   *out = nullptr;
   if (!(budget_bytes >= 1.0 && budget_bytes < 1.8e19) || quantum < 1)
     return serve_fail(PIC_EINVAL, "budget must be >= 1 byte and quantum >= 1");
-  auto *s = new pic_server_ctx();
-  s->budget = (unsigned long long)budget_bytes;
-  s->quantum = quantum;
-  s->t0 = Clock::now();
-  if (cudaGetDevice(&s->device) != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return serve_fail(PIC_ECUDA, "no CUDA device");
+  // no C++ exception may cross the C ABI
+  pic_server_ctx *s = nullptr;
+  try {
+    s = new pic_server_ctx();
+    s->budget = (unsigned long long)budget_bytes;
+    s->quantum = quantum;
+    s->device = dev;
+    s->t0 = Clock::now();
+    s->worker = std::thread([s] { s->run(); });
+  } catch (const std::exception &e) {
     delete s;
-    return serve_fail(PIC_ECUDA, "no CUDA device");
+    return serve_fail(PIC_ENOMEM, std::string("cannot start the server: ") + e.what());
   }
-  s->worker = std::thread([s] { s->run(); });
   *out = s;
   return PIC_OK;
 }
@@ -289,24 +324,31 @@ int pic_serve_submit(pic_server s, const pic_grid *grid, const pic_material *mat
   if (rc != PIC_OK) return serve_fail(rc, pic_last_error());
   if ((unsigned long long)info.arena_bytes > s->budget)
     return serve_fail(PIC_ENOMEM, "the request alone needs more than the server's budget");
-  auto q = std::make_shared<Request>();
-  q->grid = *grid;
-  q->layers.assign(mat->layers, mat->layers + mat->n_layers);
-  q->pulse = *pulse;
-  q->seed = seed;
-  q->steps = n_steps;
-  q->n_bins = n_bins;
-  q->e_min = e_min_eV;
-  q->e_max = e_max_eV;
-  q->fields_out = fields_out;
-  q->need = (unsigned long long)info.arena_bytes;
-  {
+  std::shared_ptr<Request> q;
+  try {
+    q = std::make_shared<Request>();
+    q->grid = *grid;
+    q->layers.assign(mat->layers, mat->layers + mat->n_layers);
+    q->pulse = *pulse;
+    q->seed = seed;
+    q->steps = n_steps;
+    q->n_bins = n_bins;
+    q->e_min = e_min_eV;
+    q->e_max = e_max_eV;
+    q->fields_out = fields_out;
+    q->need = (unsigned long long)info.arena_bytes;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return serve_fail(PIC_ESTATE, "server is stopping");
     q->ticket = s->next_ticket++;
     q->t_submit = s->now();
-    s->waiting.push_back(q);
     s->all[q->ticket] = q;
+    s->waiting.push_back(q);
+  } catch (const std::exception &e) {
+    if (q && q->ticket) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->all.erase(q->ticket);
+    }
+    return serve_fail(PIC_ENOMEM, std::string("cannot queue the request: ") + e.what());
   }
   s->cv_work.notify_one();
   *ticket = q->ticket;
