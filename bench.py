@@ -226,6 +226,17 @@ def run_reference(args, rank, world, dist):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+# Whole step (per cell, per material cell extra, per charged particle, per
+# ionisation event), FP32 and FP64 (8-byte reals, integer words unchanged).
+STEP_BYTES = {"fp32": (72.0, 65.0, 60.0, 64.0), "fp64": (144.0, 129.0, 108.0, 112.0)}
+ALG_BYTES_F64 = {  # as ALG_BYTES below, with 8-byte reals
+    "push": ("particle", 108.0),       # (cell 4 + offset 24 + u 24) x 2 + tag 4
+    "fields": ("field point", 144.0),  # + 96 per material point below
+    "window": ("material cell", 88.0),  # the 40 B of reals doubled, threshold 8
+    "ionize": ("material cell", 16.0),
+    "sort": ("particle", 128.0),
+    "collide": ("particle", 60.0),
+}
 ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
     "push": ("particle", 60.0),
     "fields": ("field point", 72.0),  # whole field update; + 48 per material point below
@@ -250,6 +261,9 @@ def run_native(args, rank, local, world, dist):
     build.build()
     torch.cuda.set_device(local)
     cfg = wl.config2()
+    if args.precision == "fp64":
+        cfg["precision"] = "fp64"
+        cfg["name"] = cfg["name"].replace("fp32", "fp64")
     cfg["seed"] = replica_seed(cfg["seed"], rank)  # independent replica per rank
     if args.pool_factor is not None:
         cfg["pool_factor"] = args.pool_factor
@@ -288,12 +302,20 @@ def run_native(args, rank, local, world, dist):
     t = ms_max / 1e3
     ncell = cfg["nx"] * cfg["ny"] * cfg["nz"]
     cells_all = ncell * args.steps * world
-    alg = (72.0 * ncell + 65.0 * st["nmat"]) * args.steps * world + 60.0 * psteps_all + 64.0 * events_all
+    b_cell, b_mat, b_part, b_ev = STEP_BYTES[args.precision]
+    alg = (b_cell * ncell + b_mat * st["nmat"]) * args.steps * world + b_part * psteps_all \
+        + b_ev * events_all
     peak, peak_kind = measured_peaks()
     # dominant kernel roofline
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
-    unit_name, per_unit = ALG_BYTES.get(dom, ("step", 0.0))
+    table = ALG_BYTES_F64 if args.precision == "fp64" else ALG_BYTES
+    limiter = LIMITER.get(dom, "DRAM bandwidth")
+    if args.precision == "fp64" and dom == "push":
+        limiter = "the deposit's FP64 atomic additions (up to three per node)"
+    elif args.precision == "fp64" and dom == "keldysh":
+        limiter = "FP64 issue (series of Dawson terms)"
+    unit_name, per_unit = table.get(dom, ("step", 0.0))
     if dom == "push":
         units = psteps / max(dom_n, 1)
     elif dom in ("sort", "collide"):
@@ -304,7 +326,7 @@ def run_native(args, rank, local, world, dist):
         units = st["nmat"]
     bytes_launch = per_unit * units
     if dom == "fields":
-        bytes_launch += 48.0 * st["nmat"]
+        bytes_launch += (96.0 if args.precision == "fp64" else 48.0) * st["nmat"]
     achieved = bytes_launch / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else 0.0
     # end to end: one whole job of the workload through the public API
     sim.close()
@@ -325,7 +347,8 @@ def run_native(args, rank, local, world, dist):
     line = {
         "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
                    "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
@@ -339,12 +362,17 @@ def run_native(args, rank, local, world, dist):
         "charged_particles": [i0["n_particles"], i1["n_particles"]],
         "ionisation_events": events,
         "per_kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-        "roofline": {"kernel": dom, "bound": "hbm", "limiter": LIMITER.get(dom, "DRAM bandwidth"),
-                     "achieved": achieved, "peak": peak,
+        # a class with no algorithmic bytes (Keldysh) is bound by arithmetic:
+        # no HBM fraction is claimed for it
+        "roofline": {"kernel": dom, "bound": "hbm" if per_unit else "alu", "limiter": limiter,
+                     "achieved": achieved if per_unit else None,
+                     "peak": peak if per_unit else None,
                      "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "bytes_per_launch": bytes_launch,
+                     "frac": achieved / peak if per_unit else None,
+                     "bytes_per_launch": bytes_launch,
                      "unit_of_work": unit_name, "per_unit_bytes": per_unit,
-                     "traffic": ncu_traffic(dom, units)},
+                     # the committed ncu capture is of the FP32 kernels
+                     "traffic": ncu_traffic(dom, units) if args.precision == "fp32" else None},
         "e2e": {"value": e2e_ps, "unit": UNIT, "job_steps": job_steps, "job_s": e2e_t,
                 "h2d_bytes_per_step": ji["h2d_bytes"] / job_steps,
                 "d2h_bytes_per_step": ji["d2h_bytes"] / job_steps},
@@ -578,6 +606,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--ref-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="working precision of the bench workload (silica run)")
     ap.add_argument("--sort-interval", type=int, default=0,
                     help="steps between pool sorts (0: the library default)")
     ap.add_argument("--coll-every", type=int, default=0,
