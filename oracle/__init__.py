@@ -23,7 +23,13 @@ Parity status of each function (pins are in ``tests/test_oracle_*.py``):
   window          pinned: brute-force sliding maximum
   ionisation      pinned: frozen-field survival fraction 1 - exp(-n w dt),
                   one event per molecule, charge neutrality of pairs
-  diagnostics     pinned: partition of unity (n_e integral), energy sums
+  diagnostics     pinned: closed forms for one carrier (kinetic energy, its
+                  spectrum bin and region test, n_e and energy density on a
+                  node), uniform fields (field energy), a linear field and a
+                  planted charge (Gauss residual and its plane range), the
+                  absorbed fraction; Poynting split against pure +z / -z
+                  packets, a vacuum pulse and the discrete Fresnel reflection
+                  of a thick slab (tests/test_oracle_diagnostics.py)
 """
 from __future__ import annotations
 
@@ -92,7 +98,9 @@ class Diag(ctypes.Structure):
         "U_incident", "U_kinetic", "U_ionization", "U_absorbed",
         "frac_absorbed", "U_joule", "U_field", "N_pairs", "n_e_peak",
         "energy_density_peak", "gauss_residual_max", "rho_max",
-        "n_electrons_macro", "n_holes_macro", "step")]
+        "n_electrons_macro", "n_holes_macro", "step",
+        "flux_front", "flux_back", "U_fwd_front", "U_bwd_front", "U_fwd_back",
+        "U_bwd_back", "frac_reflected", "frac_transmitted", "frac_absorbed_flux")]
 
 
 def _P(t):
@@ -119,6 +127,8 @@ def lib():
             L.or_get_material.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_set_material.argtypes = [vp, vp, vp]
             L.or_get_scalars.argtypes = [vp, vp]
+            L.or_get_flux.argtypes = [vp, vp]
+            L.or_set_flux.argtypes = [vp, vp]
             L.or_set_scalars.argtypes = [vp, l_, vp]
             L.or_diagnostics.argtypes = [vp, _P(Diag), i, d, d, vp, vp]
             L.or_rho.argtypes = [vp, vp]
@@ -363,6 +373,16 @@ class Sim:
         lib().or_set_scalars(self._h, int(step), _ptr(v))
         self._refresh()
 
+    def flux(self) -> np.ndarray:
+        """Poynting time integrals [fwd front, bwd front, fwd back, bwd back]."""
+        out = np.zeros(4)
+        lib().or_get_flux(self._h, _ptr(out))
+        return out
+
+    def set_flux(self, v):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        lib().or_set_flux(self._h, _ptr(a))
+
     def state(self) -> dict:
         """Everything the per-step parity tests compare or reload."""
         return dict(fields=self.fields(), particles=self.particles(),
@@ -384,6 +404,7 @@ class Sim:
                              float(e_min_eV), float(e_max_eV), _ptr(reg),
                              _ptr(spec))
         out = {f: getattr(dg, f) for f, _ in Diag._fields_}
+        out["flux_front"], out["flux_back"] = int(dg.flux_front), int(dg.flux_back)
         out["spectrum"] = spec[:n_bins]
         return out
 

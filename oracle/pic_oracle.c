@@ -18,6 +18,9 @@
  *   Keldysh rate   : Sec. 2.1, Eqs. for x, W and Q, first 500 terms of Q
  *   ionisation     : one event per molecule (Sec. 2.1), electron + hole with
  *                    the Table 1 effective masses (Sec. 3.2)
+ *   diagnostics    : energies, TSC number and energy density (Sec. 4.1-4.2),
+ *                    spectra (Sec. 4.3), Gauss residual, and the Poynting
+ *                    split into +z and -z waves at two planes
  * Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) supplies
  * every random number, keyed by (seed) with counter (step, cell, slot, stream).
  * A neutral's 64-bit ionisation uniform takes its top 16 bits from the block
@@ -87,6 +90,11 @@ typedef struct {
   double U_joule, U_field, N_pairs, n_e_peak, energy_density_peak;
   double gauss_residual_max, rho_max;
   double n_electrons_macro, n_holes_macro, step;
+  /* Poynting split (reading K17): node planes, time integrals of the +z and
+   * -z wave power through each, and the balance they give */
+  double flux_front, flux_back;
+  double U_fwd_front, U_bwd_front, U_fwd_back, U_bwd_back;
+  double frac_reflected, frac_transmitted, frac_absorbed_flux;
 } or_diag;
 
 /* ------------------------------------------------------------------------ */
@@ -362,6 +370,10 @@ typedef struct {
   double *imax;
   int imax_every;
   double Tsin2; /* full duration of the sine-squared field envelope */
+  /* Poynting split: node planes (front, back) and the time integrals of
+   * the +z (fwd) and -z (bwd) wave power through them */
+  int flux_plane[2];
+  double U_fwd[2], U_bwd[2];
 } or_sim;
 
 static long fidx(const or_sim *s, int i, int j, int k) {
@@ -472,6 +484,22 @@ or_sim *or_create(const or_config *cfg) {
   int nm = 0;
   for (int k = 0; k < nz; k++)
     s->mplane[k] = s->layer_of_plane[k] >= 0 ? nm++ : -1;
+  /* Poynting planes: halfway between the entrance face and the first
+   * material plane, and halfway between the last one and the far face
+   * (a quarter and three quarters of the box without material), inside
+   * 1 .. nz - 1 so that the B planes on both sides exist */
+  {
+    int zlo = -1, zhi = -1;
+    for (int k = 0; k < nz; k++)
+      if (s->layer_of_plane[k] >= 0) {
+        if (zlo < 0) zlo = k;
+        zhi = k + 1;
+      }
+    int f = zlo < 0 ? nz / 4 : zlo / 2;
+    int b = zlo < 0 ? (3 * nz) / 4 : (zhi + nz) / 2;
+    s->flux_plane[0] = f < 1 ? 1 : (f > nz - 1 ? nz - 1 : f);
+    s->flux_plane[1] = b < 1 ? 1 : (b > nz - 1 ? nz - 1 : b);
+  }
   s->nmat = (long)nm * s->nxy;
   s->win = calloc((size_t)s->NW * (s->nmat ? s->nmat : 1), sizeof(double));
   s->eamp = calloc(s->nmat ? s->nmat : 1, sizeof(double));
@@ -1165,13 +1193,50 @@ void or_collide_pass(or_sim *s) {
 
 /* Phases of one step: 1 particle, 32 collisions, 2 field, 4 window + Keldysh,
  * 8 ionisation, 16 advance the step counter.  A full step is 63. */
+/* Poynting split (reading K17: the reflected and transmitted energy from
+ * the waves going along -z and +z).  At node plane k the transverse E of
+ * the plane (Ex at (i + 1/2, j, k), Ey at (i, j + 1/2, k)) is paired with B
+ * averaged over the two half-integer planes k - 1/2 and k + 1/2 (By and Bx
+ * share those transverse positions).  A wave along +z has Ex = c By and
+ * Ey = -c Bx, one along -z the opposite signs, so
+ *   fwd = ((Ex + c By) / 2, (Ey - c Bx) / 2),
+ *   bwd = ((Ex - c By) / 2, (Ey + c Bx) / 2),
+ * and c eps0 (|fwd|^2 - |bwd|^2) is the Poynting flux (E x B)_z / mu0.
+ * Called once per step at the end of the step (E^{n+1}, B^{n+1}); each
+ * plane's sum of c eps0 |fwd|^2 dx dy and c eps0 |bwd|^2 dx dy, times dt, is
+ * added to the time integrals. */
+static void poynting_split(or_sim *s) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny;
+  const double *Ex = s->F[FEX], *Ey = s->F[FEY], *Bx = s->F[FBX], *By = s->F[FBY];
+  for (int q = 0; q < 2; q++) {
+    int k = s->flux_plane[q];
+    double f = 0.0, b = 0.0;
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        long o = fidx(s, i, j, k), om = fidx(s, i, j, k - 1);
+        double cby = OR_C * 0.5 * (By[om] + By[o]);
+        double cbx = OR_C * 0.5 * (Bx[om] + Bx[o]);
+        double fx = 0.5 * (Ex[o] + cby), fy = 0.5 * (Ey[o] - cbx);
+        double bx = 0.5 * (Ex[o] - cby), by = 0.5 * (Ey[o] + cbx);
+        f += fx * fx + fy * fy;
+        b += bx * bx + by * by;
+      }
+    double scale = OR_C * OR_EPS0 * s->cfg.dx * s->cfg.dy * s->dt;
+    s->U_fwd[q] += f * scale;
+    s->U_bwd[q] += b * scale;
+  }
+}
+
 void or_step_phases(or_sim *s, int mask) {
   if (mask & 1) or_particle_pass(s);
   if (mask & 32) or_collide_pass(s);
   if (mask & 2) or_field_pass(s);
   if (mask & 4) or_window_keldysh_pass(s);
   if (mask & 8) or_ionize_pass(s);
-  if (mask & 16) s->step++;
+  if (mask & 16) {
+    poynting_split(s);
+    s->step++;
+  }
 }
 
 void or_step(or_sim *s, int n) {
@@ -1371,6 +1436,21 @@ void or_diagnostics(const or_sim *s, or_diag *dg, int n_bins, double e_min_eV,
   dg->U_joule = s->U_joule;
   dg->N_pairs = s->N_pairs;
   dg->step = (double)s->step;
+  /* Poynting balance: reflected and transmitted fractions of the energy
+   * that came in through the front plane, and the net energy that stayed
+   * between the planes (1 - R - T when nothing enters through the back) */
+  dg->flux_front = s->flux_plane[0];
+  dg->flux_back = s->flux_plane[1];
+  dg->U_fwd_front = s->U_fwd[0];
+  dg->U_bwd_front = s->U_bwd[0];
+  dg->U_fwd_back = s->U_fwd[1];
+  dg->U_bwd_back = s->U_bwd[1];
+  if (s->U_fwd[0] > 0.0) {
+    dg->frac_reflected = s->U_bwd[0] / s->U_fwd[0];
+    dg->frac_transmitted = s->U_fwd[1] / s->U_fwd[0];
+    dg->frac_absorbed_flux =
+        ((s->U_fwd[0] - s->U_bwd[0]) - (s->U_fwd[1] - s->U_bwd[1])) / s->U_fwd[0];
+  }
   free(ne);
   free(ed);
   free(rho);
@@ -1466,6 +1546,21 @@ void or_set_scalars(or_sim *s, long step, const double in[4]) {
   s->N_pairs = in[1];
   s->U_ion = in[2];
   s->n_events = in[3];
+}
+
+/* Poynting time integrals [fwd front, bwd front, fwd back, bwd back]. */
+void or_get_flux(const or_sim *s, double out[4]) {
+  out[0] = s->U_fwd[0];
+  out[1] = s->U_bwd[0];
+  out[2] = s->U_fwd[1];
+  out[3] = s->U_bwd[1];
+}
+
+void or_set_flux(or_sim *s, const double in[4]) {
+  s->U_fwd[0] = in[0];
+  s->U_bwd[0] = in[1];
+  s->U_fwd[1] = in[2];
+  s->U_bwd[1] = in[3];
 }
 
 /* Incident field value, for the boundary tests. */
