@@ -45,8 +45,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 MAX_LAYERS = 128
 NCOMP = 15
@@ -54,18 +56,21 @@ COMP_NAMES = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz",
               "Px", "Py", "Pz", "Qx", "Qy", "Qz"]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE double, no contraction)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no contraction); openmp
+    builds the OpenMP variant used to time the oracle on all host cores."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    path = _LIB_OMP_PATH if openmp else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared"] + (["-fopenmp"] if openmp else []) + [
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class Layer(ctypes.Structure):
@@ -107,11 +112,12 @@ def _P(t):
     return ctypes.POINTER(t)
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
+    """The serial oracle library, or (openmp) its OpenMP build."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            L = ctypes.CDLL(build(openmp=openmp))
             d, i, l_, vp = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
             L.or_create.restype = vp
             L.or_create.argtypes = [_P(Config)]
@@ -158,8 +164,18 @@ def lib():
             L.or_keldysh_parts.argtypes = [d, d, d, d, i, _P(i), vp]
             L.or_keldysh_parts.restype = d
             L.or_boris.argtypes = [d, d, vp, vp, vp]
-            _lib = L
-        return _lib
+            L.or_threads.restype = i
+            L.or_threads.argtypes = []
+            if openmp:
+                _lib_omp = L
+            else:
+                _lib = L
+        return _lib_omp if openmp else _lib
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads the oracle's parallel loops use (1 for the serial build)."""
+    return int(lib(openmp).or_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -273,10 +289,12 @@ def make_config(cfg: dict) -> Config:
 class Sim:
     """One oracle simulation (FP64, single-threaded)."""
 
-    def __init__(self, cfg: dict):
+    def __init__(self, cfg: dict, openmp: bool = False):
+        """openmp: run on the OpenMP build (for timing on all host cores)."""
         self.cfg = cfg
+        self._L = lib(openmp)
         self._c = make_config(cfg)
-        self._h = lib().or_create(ctypes.byref(self._c))
+        self._h = self._L.or_create(ctypes.byref(self._c))
         if not self._h:
             raise ValueError("oracle rejected the configuration")
         self._refresh()
@@ -285,7 +303,7 @@ class Sim:
         dt, nw = ctypes.c_double(), ctypes.c_int()
         nf, nm, npart, st = (ctypes.c_long() for _ in range(4))
         e0 = ctypes.c_double()
-        lib().or_info(self._h, ctypes.byref(dt), ctypes.byref(nw),
+        self._L.or_info(self._h, ctypes.byref(dt), ctypes.byref(nw),
                       ctypes.byref(nf), ctypes.byref(nm), ctypes.byref(npart),
                       ctypes.byref(st), ctypes.byref(e0))
         self.dt, self.NW, self.nfield, self.nmat = dt.value, nw.value, nf.value, nm.value
@@ -293,7 +311,7 @@ class Sim:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -301,11 +319,11 @@ class Sim:
 
     # stepping -------------------------------------------------------------
     def step(self, n: int = 1):
-        lib().or_step(self._h, int(n))
+        self._L.or_step(self._h, int(n))
         self._refresh()
 
     def phases(self, mask: int):
-        lib().or_step_phases(self._h, int(mask))
+        self._L.or_step_phases(self._h, int(mask))
         self._refresh()
 
     # state ------------------------------------------------------------------
@@ -316,20 +334,20 @@ class Sim:
 
     def fields(self) -> np.ndarray:
         out = np.zeros((NCOMP,) + self.shape, dtype=np.float64)
-        lib().or_get_fields(self._h, _ptr(out))
+        self._L.or_get_fields(self._h, _ptr(out))
         return out
 
     def set_fields(self, F: np.ndarray):
         F = np.ascontiguousarray(F, dtype=np.float64)
         assert F.shape == (NCOMP,) + self.shape
-        lib().or_set_fields(self._h, _ptr(F))
+        self._L.or_set_fields(self._h, _ptr(F))
 
     def particles(self) -> dict:
         n = self.np
         d = dict(id=np.zeros(n, np.uint64), cell=np.zeros(n, np.int32),
                  off=np.zeros((n, 3)), u=np.zeros((n, 3)),
                  tag=np.zeros(n, np.uint32))
-        lib().or_get_particles(self._h, _ptr(d["id"]), _ptr(d["cell"]),
+        self._L.or_get_particles(self._h, _ptr(d["id"]), _ptr(d["cell"]),
                                _ptr(d["off"]), _ptr(d["u"]), _ptr(d["tag"]))
         return d
 
@@ -340,7 +358,7 @@ class Sim:
                 np.ascontiguousarray(d["off"], np.float64).reshape(n, 3),
                 np.ascontiguousarray(d["u"], np.float64).reshape(n, 3),
                 np.ascontiguousarray(d["tag"], np.uint32)]
-        lib().or_set_particles(self._h, n, *[_ptr(a) for a in arrs])
+        self._L.or_set_particles(self._h, n, *[_ptr(a) for a in arrs])
         self._refresh()
 
     def material(self) -> dict:
@@ -348,7 +366,7 @@ class Sim:
         d = dict(alive=np.zeros(nm, np.uint32),
                  win=np.zeros((self.NW, nm)), eamp=np.zeros(nm),
                  T=np.zeros(nm, np.uint64), Talways=np.zeros(nm, np.uint8))
-        lib().or_get_material(self._h, _ptr(d["alive"]), _ptr(d["win"]),
+        self._L.or_get_material(self._h, _ptr(d["alive"]), _ptr(d["win"]),
                               _ptr(d["eamp"]), _ptr(d["T"]),
                               _ptr(d["Talways"]))
         if self.nmat == 0:
@@ -358,30 +376,30 @@ class Sim:
     def set_material(self, alive=None, win=None):
         a = None if alive is None else np.ascontiguousarray(alive, np.uint32)
         w = None if win is None else np.ascontiguousarray(win, np.float64)
-        lib().or_set_material(self._h, None if a is None else _ptr(a),
+        self._L.or_set_material(self._h, None if a is None else _ptr(a),
                               None if w is None else _ptr(w))
 
     def scalars(self) -> dict:
         out = np.zeros(4)
-        lib().or_get_scalars(self._h, _ptr(out))
+        self._L.or_get_scalars(self._h, _ptr(out))
         return dict(U_joule=out[0], N_pairs=out[1], U_ion=out[2],
                     n_events=out[3], step=self.step_index)
 
     def set_scalars(self, step: int, U_joule=0.0, N_pairs=0.0, U_ion=0.0,
                     n_events=0.0):
         v = np.array([U_joule, N_pairs, U_ion, n_events], dtype=np.float64)
-        lib().or_set_scalars(self._h, int(step), _ptr(v))
+        self._L.or_set_scalars(self._h, int(step), _ptr(v))
         self._refresh()
 
     def flux(self) -> np.ndarray:
         """Poynting time integrals [fwd front, bwd front, fwd back, bwd back]."""
         out = np.zeros(4)
-        lib().or_get_flux(self._h, _ptr(out))
+        self._L.or_get_flux(self._h, _ptr(out))
         return out
 
     def set_flux(self, v):
         a = np.ascontiguousarray(v, dtype=np.float64)
-        lib().or_set_flux(self._h, _ptr(a))
+        self._L.or_set_flux(self._h, _ptr(a))
 
     def state(self) -> dict:
         """Everything the per-step parity tests compare or reload."""
@@ -390,7 +408,7 @@ class Sim:
 
     def rho(self) -> np.ndarray:
         out = np.zeros(self.shape)
-        lib().or_rho(self._h, _ptr(out))
+        self._L.or_rho(self._h, _ptr(out))
         return out
 
     def diagnostics(self, n_bins=0, e_min_eV=0.0, e_max_eV=1.0, region=None):
@@ -400,7 +418,7 @@ class Sim:
             [0, self.cfg["nx"], 0, self.cfg["ny"], 0, self.cfg["nz"]],
             dtype=np.int32)
         spec = np.zeros(max(n_bins, 1))
-        lib().or_diagnostics(self._h, ctypes.byref(dg), int(n_bins),
+        self._L.or_diagnostics(self._h, ctypes.byref(dg), int(n_bins),
                              float(e_min_eV), float(e_max_eV), _ptr(reg),
                              _ptr(spec))
         out = {f: getattr(dg, f) for f, _ in Diag._fields_}
@@ -409,24 +427,24 @@ class Sim:
         return out
 
     def incident(self, t: float) -> float:
-        return lib().or_incident(self._h, float(t))
+        return self._L.or_incident(self._h, float(t))
 
     def threshold(self, layer: int, E: float) -> int:
         """Ionisation threshold T = floor(p 2^64) of a cell of this layer at
         window amplitude E (2^64 - 1 when p reaches 1)."""
         T = np.zeros(1, dtype=np.uint64)
         a = np.zeros(1, dtype=np.int32)
-        lib().or_cell_threshold(self._h, int(layer), float(E), _ptr(T), _ptr(a))
+        self._L.or_cell_threshold(self._h, int(layer), float(E), _ptr(T), _ptr(a))
         return (1 << 64) - 1 if a[0] else int(T[0])
 
     def spot(self, x: float, y: float) -> float:
-        return lib().or_spot(self._h, float(x), float(y))
+        return self._L.or_spot(self._h, float(x), float(y))
 
     def intensity_max(self) -> np.ndarray:
         """Recorded maximum of |E|^2 / E0^2 per cell, shape (nz, ny, nx)."""
         c = self.cfg
         out = np.zeros((c["nz"], c["ny"], c["nx"]))
-        lib().or_get_imax(self._h, _ptr(out))
+        self._L.or_get_imax(self._h, _ptr(out))
         return out
 
     def damage(self, region=None) -> dict:
@@ -439,7 +457,7 @@ class Sim:
         ne_z, ed_z = np.zeros(c["nz"] + 1), np.zeros(c["nz"] + 1)
         lay = np.zeros(max(1, 4 * nl))
         flags = np.zeros(max(1, nl), dtype=np.int32)
-        ncrit = lib().or_damage(self._h, _ptr(reg), _ptr(ne_z), _ptr(ed_z), _ptr(lay),
+        ncrit = self._L.or_damage(self._h, _ptr(reg), _ptr(ne_z), _ptr(ed_z), _ptr(lay),
                                 _ptr(flags))
         layers = [dict(ne_peak=lay[4 * L], ed_peak=lay[4 * L + 1], imax_peak=lay[4 * L + 2],
                        n_inst=lay[4 * L + 3], flags=int(flags[L])) for L in range(nl)]

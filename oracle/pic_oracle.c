@@ -28,11 +28,21 @@
  * the block (step, cell, slot, 4) (or_ion_uniform).
  *
  * Parity pins for every function here live in tests/test_oracle_*.py.
+ *
+ * The same source also builds with OpenMP (liboracle_omp.so), used only to
+ * time the oracle on all host cores: the loops whose iterations write
+ * disjoint data (the field updates and the intensity record over z planes,
+ * the window and Keldysh pass over material planes) then run in parallel;
+ * the particle and ionisation passes stay serial.  Only the summation order
+ * of the Joule work differs from the serial build.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_C 299792458.0
 #define OR_EPS0 8.8541878128e-12
@@ -671,6 +681,7 @@ static void b_half(or_sim *s) {
                dz = s->cfg.dz;
   double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
   double *Bx = s->F[FBX], *By = s->F[FBY], *Bz = s->F[FBZ];
+#pragma omp parallel for schedule(static)
   for (int k = 0; k <= nz; k++)
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) {
@@ -723,6 +734,7 @@ static void e_full(or_sim *s) {
   double einc = e_inc(s, (s->step + 0.5) * dt);
   double exi = s->cfg.pol == 0 ? einc : 0.0, eyi = s->cfg.pol == 0 ? 0.0 : einc;
   double joule = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : joule)
   for (int k = 0; k <= nz; k++) {
     int L = k < nz ? s->layer_of_plane[k] : -1;
     for (int j = 0; j < ny; j++)
@@ -783,6 +795,7 @@ static void record_intensity(or_sim *s) {
   const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
   const double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
   const double norm = s->E0 > 0.0 ? 1.0 / (s->E0 * s->E0) : 1.0;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; k++)
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) {
@@ -816,6 +829,7 @@ void or_window_keldysh_pass(or_sim *s) {
   const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz, NW = s->NW;
   double *Ex = s->F[FEX], *Ey = s->F[FEY], *Ez = s->F[FEZ];
   int slot = (int)(s->step % NW);
+#pragma omp parallel for schedule(dynamic)
   for (int k = 0; k < nz; k++) {
     int L = s->layer_of_plane[k];
     if (L < 0) continue;
@@ -1561,6 +1575,15 @@ void or_set_flux(or_sim *s, const double in[4]) {
   s->U_bwd[0] = in[1];
   s->U_fwd[1] = in[2];
   s->U_bwd[1] = in[3];
+}
+
+/* Threads the parallel loops use: 1 in the serial build. */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* Incident field value, for the boundary tests. */
