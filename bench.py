@@ -5,10 +5,18 @@ Workload: bulk fused silica, 128 x 128 x 512 cells at lambda/40, slab z
 fields, push and deposit (the 2000-step bulk-silica configuration).  A step
 is one full PIC step (gather, Boris, deposit, Yee + polarisation, window,
 Keldysh, ionisation, pool maintenance).  The run first advances `--prerun`
-untimed steps so that the pulse is inside the slab and ionising, then
-`--warmup` steps, then times `--steps` steps with CUDA events on the
-simulation's stream.  The state (13.6 GB) is far larger than L2, so no
+untimed steps (default 1700: the pulse has ionised the slab, every material
+cell is drawn each step and the pool holds its late-job particle count),
+then `--warmup` steps, then times `--steps` steps with CUDA events on the
+simulation's stream.  The state (13.9 GB) is far larger than L2, so no
 flush is needed between steps.
+
+At one GPU the line also carries, measured the same way:
+  mirror  the 20-pair quarter-wave mirror, 256 x 256 x 1024, 3000 steps
+          (window after `--mirror-prerun` steps, whole job as e2e, its own
+          roofline and oracle baseline);
+  scan    the 64-instance fluence scan (batched graph vs one at a time) and
+          its time-to-result p50 / p99 (also at the top level).
 
 value   = charged-particle pushes per second (all ranks)
 e2e     = the same metric for one whole job through the public API: from the
@@ -181,41 +189,95 @@ def emit(line, rank):
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(prerun, steps):
-    """Time the FP64 oracle on a 4 x 4 transverse column of the workload,
-    prerun to the same step; returns (particle-steps/s, cell-updates/s, info)."""
-    import oracle
+def _oracle_column(workload):
     from paper_2502_13695_gb300 import workloads as wl
-    oracle.build()
-    cfg = wl.config2()
-    col = dict(cfg, nx=4, ny=4)
-    s = oracle.Sim(col)
-    s.step(prerun)
-    n0 = s.np
-    t0 = time.perf_counter()
+    cfg = wl.config2() if workload == "silica" else wl.config3()
+    return cfg, dict(cfg, nx=4, ny=4, precision="fp64")
+
+
+def _time_oracle(s, steps):
     psteps = 0
+    t0 = time.perf_counter()
     for _ in range(steps):
         psteps += s.np
         s.step(1)
-    dt = time.perf_counter() - t0
+    return psteps, time.perf_counter() - t0
+
+
+def oracle_sample(prerun, steps, workload="silica", openmp=False):
+    """Time the FP64 oracle on a 4 x 4 transverse column of the workload
+    (silica: 128x128x512; mirror: 256x256x1024), prerun to the same step;
+    returns (particle-steps/s, cell-updates/s, info, state), state being
+    what oracle_sample_from_state needs to time the same steps again."""
+    import oracle
+    oracle.build(openmp=openmp)
+    cfg, col = _oracle_column(workload)
+    s = oracle.Sim(col, openmp=openmp)
+    s.step(prerun)
+    n0 = s.np
+    state = dict(s.state(), flux=s.flux())
+    psteps, dt = _time_oracle(s, steps)
     ncell = col["nx"] * col["ny"] * col["nz"]
     return psteps / dt, ncell * steps / dt, dict(
-        sample=f"4x4x512 column of the 128x128x512 silica workload (same z profile), "
+        sample=f"4x4x{cfg['nz']} column of the {cfg['nx']}x{cfg['ny']}x{cfg['nz']} "
+               f"{workload} workload (same z profile), "
                f"steps {prerun}..{prerun + steps}, {n0} charged macroparticles at start",
-        seconds=dt, cores=1, workload=cfg["name"], grid=[cfg["nx"], cfg["ny"], cfg["nz"]])
+        seconds=dt, cores=oracle.threads(openmp), workload=cfg["name"],
+        grid=[cfg["nx"], cfg["ny"], cfg["nz"]]), state
+
+
+def oracle_sample_from_state(state, steps, workload="silica"):
+    """Time the same sample on the OpenMP build (all host cores) from the
+    state oracle_sample started its timed steps from."""
+    import oracle
+    oracle.build(openmp=True)
+    cfg, col = _oracle_column(workload)
+    s = oracle.Sim(col, openmp=True)
+    sc = state["scalars"]
+    s.set_scalars(sc["step"], sc["U_joule"], sc["N_pairs"], sc["U_ion"], sc["n_events"])
+    s.set_fields(state["fields"])
+    s.set_particles(state["particles"])
+    s.set_material(state["material"]["alive"], state["material"]["win"])
+    s.set_flux(state["flux"])
+    psteps, dt = _time_oracle(s, steps)
+    ncell = col["nx"] * col["ny"] * col["nz"]
+    return psteps / dt, ncell * steps / dt, oracle.threads(True)
+
+
+def oracle_samples_async(jobs):
+    """Start oracle_sample(prerun, steps, workload) for each job in its own
+    spawned process (started before any GPU call), so that the oracle's long
+    preruns overlap the GPU measurements; returns (executor, futures)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    ex = ProcessPoolExecutor(max_workers=max(1, len(jobs)), mp_context=mp.get_context("spawn"))
+    return ex, [ex.submit(oracle_sample, *j) for j in jobs]
+
+
+def cpu_baseline_entry(res, steps, workload):
+    """cpu_baseline object: the OpenMP build on all host cores, with the
+    single-core serial build beside it, over the same sample."""
+    ps1, cu1, info, state = res
+    psm, cum, cores = oracle_sample_from_state(state, steps, workload)
+    return {"value": psm, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": info["sample"] + "; OpenMP build (field, window and Keldysh loops "
+                      "parallel; particle and ionisation passes serial)",
+            "cell_updates_per_s": cum,
+            "single_core": {"value": ps1, "cores": 1, "cell_updates_per_s": cu1}}
 
 
 def run_reference(args, rank, world, dist):
     if rank != 0:
         return
     steps = max(1, args.steps if args.ref_steps is None else args.ref_steps)
-    ps, cu, info = oracle_sample(args.prerun + args.warmup, steps)
+    ps, cu, info, _ = oracle_sample(args.prerun + args.warmup, steps, openmp=True)
     line = {"metric": METRIC, "value": ps, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * info["seconds"] / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": info["workload"], "grid": info["grid"], "ppc": 8,
-                       "prerun_steps": args.prerun, "parallelism": "FP64 oracle, one host core"},
+                       "prerun_steps": args.prerun,
+                       "parallelism": f"FP64 oracle, OpenMP build, {info['cores']} host threads"},
             "cell_updates_per_s": cu,
             "cpu_baseline": {"value": ps, "unit": UNIT, "cores": info["cores"],
                              "kind": "oracle", "sample": info["sample"]},
@@ -255,25 +317,17 @@ LIMITER = {
 }
 
 
-def run_native(args, rank, local, world, dist):
+def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup):
+    """Time `steps` full steps of cfg after `prerun + warmup` untimed ones
+    (CUDA events on the simulation's stream, clocks sampled meanwhile), then
+    one whole job of cfg["steps"] steps through the public API (e2e).
+    Returns the fields of a bench line for this workload."""
     import torch
-    from paper_2502_13695_gb300 import build, pic, workloads as wl
-    build.build()
-    torch.cuda.set_device(local)
-    cfg = wl.config2()
-    if args.precision == "fp64":
-        cfg["precision"] = "fp64"
-        cfg["name"] = cfg["name"].replace("fp32", "fp64")
-    cfg["seed"] = replica_seed(cfg["seed"], rank)  # independent replica per rank
-    if args.pool_factor is not None:
-        cfg["pool_factor"] = args.pool_factor
-    if args.coll_every:
-        cfg["coll_every"] = args.coll_every
-    if args.sort_interval:
-        cfg["sort_interval"] = args.sort_interval
+    from paper_2502_13695_gb300 import pic
+    precision = cfg.get("precision", "fp32")
     sim = pic.Simulation(cfg)
     st = sim.static
-    sim.step(args.prerun + args.warmup)
+    sim.step(prerun + warmup)
     sim.sync()
     stream = sim.stream
     i0, s0 = sim.info(), sim.scalars()
@@ -286,7 +340,7 @@ def run_native(args, rank, local, world, dist):
         if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
     with Clocks(gpu_index if gpu_index.isdigit() else local) as clk:
         ev0.record(stream)
-        sim.step(args.steps)
+        sim.step(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -301,19 +355,19 @@ def run_native(args, rank, local, world, dist):
     ms_max, psteps_all, events_all = agg["ms_max"], agg["psteps_all"], agg["events_all"]
     t = ms_max / 1e3
     ncell = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    cells_all = ncell * args.steps * world
-    b_cell, b_mat, b_part, b_ev = STEP_BYTES[args.precision]
-    alg = (b_cell * ncell + b_mat * st["nmat"]) * args.steps * world + b_part * psteps_all \
+    cells_all = ncell * steps * world
+    b_cell, b_mat, b_part, b_ev = STEP_BYTES[precision]
+    alg = (b_cell * ncell + b_mat * st["nmat"]) * steps * world + b_part * psteps_all \
         + b_ev * events_all
     peak, peak_kind = measured_peaks()
     # dominant kernel roofline
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
-    table = ALG_BYTES_F64 if args.precision == "fp64" else ALG_BYTES
+    table = ALG_BYTES_F64 if precision == "fp64" else ALG_BYTES
     limiter = LIMITER.get(dom, "DRAM bandwidth")
-    if args.precision == "fp64" and dom == "push":
+    if precision == "fp64" and dom == "push":
         limiter = "the deposit's FP64 atomic additions (up to three per node)"
-    elif args.precision == "fp64" and dom == "keldysh":
+    elif precision == "fp64" and dom == "keldysh":
         limiter = "FP64 issue (series of Dawson terms)"
     unit_name, per_unit = table.get(dom, ("step", 0.0))
     if dom == "push":
@@ -326,7 +380,7 @@ def run_native(args, rank, local, world, dist):
         units = st["nmat"]
     bytes_launch = per_unit * units
     if dom == "fields":
-        bytes_launch += (96.0 if args.precision == "fp64" else 48.0) * st["nmat"]
+        bytes_launch += (96.0 if precision == "fp64" else 48.0) * st["nmat"]
     achieved = bytes_launch / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else 0.0
     # end to end: one whole job of the workload through the public API
     sim.close()
@@ -336,32 +390,23 @@ def run_native(args, rank, local, world, dist):
     t0 = time.perf_counter()
     job = pic.Simulation(cfg)
     job.step(job_steps)
-    job.diagnostics(n_bins=64, e_min_eV=0.0, e_max_eV=100.0)
+    jd = job.diagnostics(n_bins=64, e_min_eV=0.0, e_max_eV=100.0)
     e2e_t = time.perf_counter() - t0
     ji = job.info()
     job.close()
+    del job
+    torch.cuda.empty_cache()
     e2e_t = allreduce(dist, e2e_t, _op(dist, "max"))
     e2e_ps = allreduce(dist, ji["particle_steps"], _op(dist, "sum")) / e2e_t
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32",
-        "data": "synthetic",
-        "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
-                   "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
-                   "collisions_every": args.coll_every,
-                   "sort_interval": args.sort_interval or 16,
-                   "l2": "state larger than L2 (%.1f GB), no flush" % (st["arena_bytes"] / 1e9),
-                   "parallelism": f"replicas x{world}"},
+    return {
+        "value": agg["value"], "ms_per_step": ms_max / steps,
         "cell_updates_per_s": cells_all / t,
         "hbm_roofline_frac": alg / t / (peak * 1e9),
-        "hbm_alg_bytes_per_step": alg / args.steps / world,
+        "hbm_alg_bytes_per_step": alg / steps / world,
+        "timed_steps": [prerun + warmup, prerun + warmup + steps],
         "charged_particles": [i0["n_particles"], i1["n_particles"]],
         "ionisation_events": events,
-        "per_kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "per_kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
         # a class with no algorithmic bytes (Keldysh) is bound by arithmetic:
         # no HBM fraction is claimed for it
         "roofline": {"kernel": dom, "bound": "hbm" if per_unit else "alu", "limiter": limiter,
@@ -372,22 +417,94 @@ def run_native(args, rank, local, world, dist):
                      "bytes_per_launch": bytes_launch,
                      "unit_of_work": unit_name, "per_unit_bytes": per_unit,
                      # the committed ncu capture is of the FP32 kernels
-                     "traffic": ncu_traffic(dom, units) if args.precision == "fp32" else None},
+                     "traffic": ncu_traffic(dom, units) if precision == "fp32" else None},
         "e2e": {"value": e2e_ps, "unit": UNIT, "job_steps": job_steps, "job_s": e2e_t,
                 "h2d_bytes_per_step": ji["h2d_bytes"] / job_steps,
-                "d2h_bytes_per_step": ji["d2h_bytes"] / job_steps},
+                "d2h_bytes_per_step": ji["d2h_bytes"] / job_steps,
+                "frac_absorbed": jd["frac_absorbed"],
+                "frac_reflected": jd["frac_reflected"],
+                "frac_absorbed_flux": jd["frac_absorbed_flux"],
+                "n_e_peak_m3": jd["n_e_peak"]},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "arena_gb": st["arena_bytes"] / 1e9,
     }
+
+
+def run_native(args, rank, local, world, dist):
+    import torch
+    from paper_2502_13695_gb300 import build, workloads as wl
+    full = world == 1 and not args.silica_only and args.precision == "fp32"
+    # the oracle's CPU baselines run in spawned processes beside the GPU work
+    cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        ps, cu, info = oracle_sample(args.prerun, args.cpu_steps)
-        line["cpu_baseline"] = {"value": ps, "unit": UNIT, "cores": info["cores"],
-                                "kind": "oracle", "sample": info["sample"],
-                                "cell_updates_per_s": cu}
+        jobs = [(args.prerun, args.cpu_steps, "silica")]
+        if full:
+            jobs.append((args.mirror_prerun, args.cpu_steps, "mirror"))
+        cpu = oracle_samples_async(jobs)
+    build.build()
+    torch.cuda.set_device(local)
+    cfg = wl.config2()
+    if args.precision == "fp64":
+        cfg["precision"] = "fp64"
+        cfg["name"] = cfg["name"].replace("fp32", "fp64")
+    cfg["seed"] = replica_seed(cfg["seed"], rank)  # independent replica per rank
+    if args.pool_factor is not None:
+        cfg["pool_factor"] = args.pool_factor
+    if args.coll_every:
+        cfg["coll_every"] = args.coll_every
+    if args.sort_interval:
+        cfg["sort_interval"] = args.sort_interval
+    m = measure_workload(cfg, args, rank, local, world, dist, args.prerun, args.steps, args.warmup)
+    mirror = scan = None
+    if full:
+        # the 20-pair multilayer mirror (256 x 256 x 1024, 3000 steps)
+        mcfg = wl.config3()
+        mm = measure_workload(mcfg, args, rank, local, world, dist, args.mirror_prerun,
+                              args.steps, args.warmup)
+        mirror = {"workload": mcfg["name"], "grid": [mcfg["nx"], mcfg["ny"], mcfg["nz"]],
+                  "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+                  "prerun_steps": args.mirror_prerun,
+                  "l2": "state larger than L2 (%.1f GB), no flush" % mm["arena_gb"]}
+        mirror.update({k: v for k, v in mm.items() if k != "arena_gb"})
+        torch.cuda.empty_cache()
+        scan = run_scan(args, emit_line=False)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]],
+                   "ppc": 8, "prerun_steps": args.prerun, "pool_factor": cfg["pool_factor"],
+                   "collisions_every": args.coll_every,
+                   "sort_interval": args.sort_interval or 16,
+                   "l2": "state larger than L2 (%.1f GB), no flush" % m["arena_gb"],
+                   "parallelism": f"replicas x{world}"},
+    }
+    line.update({k: v for k, v in m.items() if k not in ("value", "ms_per_step", "arena_gb")})
+    if mirror is not None:
+        line["mirror"] = mirror
+    if scan is not None:
+        line["scan"] = {k: scan[k] for k in ("config", "scan_time_to_result_s", "value",
+                                             "cell_updates_per_s", "one_at_a_time",
+                                             "batched_total_s", "damage_threshold_fluence_J_cm2",
+                                             "gpu_launches_per_step")}
+        line["scan"]["unit"] = UNIT
+        line["scan_time_to_result_s"] = scan["scan_time_to_result_s"]
+    if cpu is not None:
+        ex, futs = cpu
+        res = [f.result() for f in futs]
+        ex.shutdown()
+        line["cpu_baseline"] = cpu_baseline_entry(res[0], args.cpu_steps, "silica")
+        if mirror is not None and len(res) > 1:
+            mirror["cpu_baseline"] = cpu_baseline_entry(res[1], args.cpu_steps, "mirror")
     emit(line, rank)
 
 
-def run_scan(args):
+def run_scan(args, emit_line=True):
     """Batched fluence scan: 64 instances 64x64x{128..512}, fluence 0.1-3
     J cm^-2 log-spaced, FP32, advanced together from one CUDA graph, against
     the same instances run one at a time on the same GPU.  An instance's
@@ -406,6 +523,7 @@ def run_scan(args):
     batch.step(32)  # capture + warm-up
     batch.sync()
     p0 = sum(s.info()["particle_steps"] for s in sims)
+    l0 = sum(s.info()["launches"] for s in sims)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     batch.step(steps)
@@ -413,6 +531,7 @@ def run_scan(args):
     results = [s_.damage() for s_ in sims]
     t_batch = time.perf_counter() - t0
     p_batch = sum(s.info()["particle_steps"] for s in sims) - p0
+    launches = sum(s.info()["launches"] for s in sims) - l0
     cells = sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs) * steps
     batch.close()
     for s_ in sims:
@@ -461,10 +580,13 @@ def run_scan(args):
             "one_at_a_time": {"particle_steps_per_s": p_seq / t_seq,
                               "cell_updates_per_s": cells / t_seq, "total_s": t_seq},
             "batched_total_s": t_batch,
+            "gpu_launches_per_step": launches / steps,
             "damage_threshold_fluence_J_cm2": lidt,
             "peak_ne_m3": [max(ly["ne_peak"] for ly in r["layers"]) for r in results],
             "peak_energy_density_J_m3": [max(ly["ed_peak"] for ly in r["layers"]) for r in results]}
-    print(json.dumps(line), flush=True)
+    if emit_line:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_paper(args):
@@ -599,7 +721,12 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--prerun", type=int, default=700)
+    ap.add_argument("--prerun", type=int, default=1700,
+                    help="untimed steps before the silica window (the job has 2000)")
+    ap.add_argument("--mirror-prerun", type=int, default=2500,
+                    help="untimed steps before the mirror window (the job has 3000)")
+    ap.add_argument("--silica-only", action="store_true",
+                    help="skip the mirror workload and the fluence scan of the default line")
     ap.add_argument("--pool-factor", type=float, default=None,
                     help="charged-slot capacity / neutrals (default: the workload's 3.0)")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")

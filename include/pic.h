@@ -68,7 +68,8 @@ extern "C" {
 #define PIC_PHASE_FIELDS 2    /* B half step, E (+ polarisation), B half */
 #define PIC_PHASE_WINDOW 4    /* |E| window and Keldysh threshold per cell */
 #define PIC_PHASE_IONIZE 8    /* ionisation draws and pair creation */
-#define PIC_PHASE_ADVANCE 16  /* step counter += 1 */
+#define PIC_PHASE_ADVANCE 16  /* Poynting split of the step's end fields, step
+                                 counter += 1 */
 #define PIC_PHASE_COLLIDE 32  /* binary collisions (when coll_every divides step + 1);
                                  runs after the particles, before the fields */
 #define PIC_PHASE_ALL 63
@@ -196,6 +197,26 @@ typedef struct {
   int reserved2[2];
   double *spectrum;          /* caller-owned host array of n_bins: real
                                 electrons per bin (electron kinetic energy) */
+  /* Poynting split (the reflected and transmitted energy behind the absorbed
+   * fraction, Sec. 4.2 and Sec. 5): at a node plane k the transverse E of the
+   * plane is paired with B averaged over the planes k - 1/2 and k + 1/2, and
+   * split into the wave going along +z, ((Ex + c By) / 2, (Ey - c Bx) / 2),
+   * and the one going along -z, ((Ex - c By) / 2, (Ey + c Bx) / 2); c eps0
+   * |.|^2 of each, summed over the plane times dx dy, is its power.  The
+   * split is taken once per step, at the end of the step (the advance
+   * phase), and its powers are summed times dt from step 0.  The planes are
+   * halfway between the entrance face and the first material plane and
+   * halfway between the last material plane and the far face (nz / 4 and
+   * 3 nz / 4 without material), clamped to 1 .. nz - 1. */
+  int flux_plane[2];         /* out: node planes of the split (front, back) */
+  double U_fwd[2];           /* out: energy carried along +z through each [J] */
+  double U_bwd[2];           /* out: energy carried along -z through each [J] */
+  double frac_reflected;     /* out: U_bwd[0] / U_fwd[0] (0 while U_fwd[0] = 0) */
+  double frac_transmitted;   /* out: U_fwd[1] / U_fwd[0] */
+  double frac_absorbed_flux; /* out: (U_fwd[0] - U_bwd[0] - U_fwd[1] + U_bwd[1]) /
+                                U_fwd[0], the energy that stayed between the
+                                planes (1 - R - T when nothing enters through
+                                the back plane) */
 } pic_diag;
 
 /* Sizes of a configuration without creating it.  Returns PIC_EINVAL for an

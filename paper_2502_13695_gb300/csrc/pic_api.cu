@@ -64,6 +64,8 @@ struct Plan {
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
+  size_t off_flux_part, off_flux_cnt;
+  int flux_plane[2];  // node planes of the Poynting split (front, back)
   size_t total;
 };
 
@@ -139,6 +141,16 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
       P.kplane.push_back(k);
     }
   P.n_mplanes = (int)P.kplane.size();
+  // Poynting planes: halfway between the entrance face and the first
+  // material plane, and between the last one and the far face (a quarter
+  // and three quarters of the box without material), within 1 .. nz - 1
+  {
+    const int nz = g.nz;
+    const int f = P.kplane.empty() ? nz / 4 : P.kplane.front() / 2;
+    const int b = P.kplane.empty() ? (3 * nz) / 4 : (P.kplane.back() + 1 + nz) / 2;
+    P.flux_plane[0] = std::min(std::max(f, 1), nz - 1);
+    P.flux_plane[1] = std::min(std::max(b, 1), nz - 1);
+  }
   P.nmat = (long long)P.n_mplanes * P.nxy;
   P.cap = (long long)std::ceil(g.pool_factor * (double)P.n_neutrals) + 1024;
   if (P.cap >= (1ll << 31)) return fail(PIC_EINVAL, "particle pool of >= 2^31 slots");
@@ -203,7 +215,9 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_total = take(8);
   P.off_nslots = take(8);
   P.off_step = take(8);
-  P.off_acc = take(8 * 8);
+  P.off_acc = take(16 * 8);
+  P.off_flux_part = take(2 * kFluxBlocks * 2 * 8);
+  P.off_flux_cnt = take(16);
   P.off_err = take(16);
   P.off_ne = take(P.nfield * 8);
   P.off_ed = take(P.nfield * 8);
@@ -432,6 +446,11 @@ void bind(pic_ctx *h) {
   D.imax_every = P.imax_every;
   D.inv_e0sq = R(P.E0 > 0.0 ? 1.0 / (P.E0 * P.E0) : 1.0);
   D.acc = (double *)(A + P.off_acc);
+  D.flux_k[0] = P.flux_plane[0];
+  D.flux_k[1] = P.flux_plane[1];
+  D.flux_scale = kC * kEps0 * P.g.dx * P.g.dy * P.dt;
+  D.flux_part = (double *)(A + P.off_flux_part);
+  D.flux_cnt = (unsigned int *)(A + P.off_flux_cnt);
   D.err = (int *)(A + P.off_err);
   D.seed = h->seed;
   X.lr = (const LayerR<R> *)(A + P.off_lr);
@@ -472,8 +491,11 @@ void prof_end(pic_ctx *h) {
   h->open_cls = -1;
 }
 
+// Counting sort of the pool: by cell (by_frame false: the collision pass
+// needs each cell's particles in one range, with cnt holding the cell ends)
+// or by deposit-frame base node (the periodic sort, for the push).
 template <class R>
-int sort_pool(pic_ctx *h) {
+int sort_pool(pic_ctx *h, bool by_frame) {
   Ctx<R> &X = ctx_of<R>(h);
   const Plan &P = h->P;
   cudaStream_t s = h->stream;
@@ -482,11 +504,17 @@ int sort_pool(pic_ctx *h) {
   unsigned long long *total = (unsigned long long *)(h->arena + P.off_total);
   prof_begin(h, PIC_PROF_SORT);
   PIC_CUDA(cudaMemsetAsync(cnt, 0, P.ncell * 4, s));
-  k_hist<<<kPersistentBlocks, kThreads, 0, s>>>(X.d.pcell, X.d.nslots, X.d.cap, cnt);
+  if (by_frame)
+    k_hist<true, R><<<kPersistentBlocks, kThreads, 0, s>>>(X.d, cnt);
+  else
+    k_hist<false, R><<<kPersistentBlocks, kThreads, 0, s>>>(X.d, cnt);
   k_scan_reduce<<<P.nb_scan, kScanThreads, 0, s>>>(cnt, P.ncell, bsum);
   k_scan_blocks<<<1, kScanThreads, 0, s>>>(bsum, P.nb_scan, total);
   k_scan_final<<<P.nb_scan, kScanThreads, 0, s>>>(cnt, P.ncell, bsum);
-  k_scatter<R><<<kPersistentBlocks, kThreads, 0, s>>>(X, cnt);
+  if (by_frame)
+    k_scatter<true, R><<<kPersistentBlocks, kThreads, 0, s>>>(X, cnt);
+  else
+    k_scatter<false, R><<<kPersistentBlocks, kThreads, 0, s>>>(X, cnt);
   k_set_slots<<<1, 1, 0, s>>>(X.d.nslots, total);
   prof_end(h);
   h->launches += 6;
@@ -538,7 +566,7 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if ((mask & PIC_PHASE_COLLIDE) && P.g.coll_every > 0 && (h->step + 1) % P.g.coll_every == 0) {
     // pairs are formed per cell: the pool is sorted first (cell ends in cnt)
-    const int rc = sort_pool<R>(h);
+    const int rc = sort_pool<R>(h, false);
     if (rc) return rc;
     prof_begin(h, PIC_PROF_COLLIDE);
     CollConst K;
@@ -614,13 +642,13 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (mask & PIC_PHASE_ADVANCE) {
     prof_begin(h, PIC_PROF_OTHER);
-    k_advance<<<1, 1, 0, s>>>(X.d.step);
+    k_flux_advance<R><<<dim3(kFluxBlocks, 2), kThreads, 0, s>>>(X.d);
     prof_end(h);
     h->launches += 1;
     h->step++;
     if (++h->since_sort >= P.g.sort_interval) {
       h->since_sort = 0;
-      const int rc = sort_pool<R>(h);
+      const int rc = sort_pool<R>(h, true);
       if (rc) return rc;
     }
   }
@@ -1196,12 +1224,12 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
     k_diag_grid<float><<<P.diag_blocks_g, kThreads, 0, s>>>(h->c32, ne, ed, rho, part);
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaMemcpyAsync(pg5.data(), part, pg5.size() * 8, cudaMemcpyDeviceToHost, s));
-  double acc[4];
-  PIC_CUDA(cudaMemcpyAsync(acc, A + P.off_acc, 32, cudaMemcpyDeviceToHost, s));
+  double acc[12];
+  PIC_CUDA(cudaMemcpyAsync(acc, A + P.off_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
   if (dg->n_bins > 0)
     PIC_CUDA(cudaMemcpyAsync(dg->spectrum, spec, dg->n_bins * 8, cudaMemcpyDeviceToHost, s));
   PIC_CUDA(cudaStreamSynchronize(s));
-  h->d2h_bytes += (long long)((pp.size() + pg5.size() + 4 + std::max(dg->n_bins, 0)) * 8);
+  h->d2h_bytes += (long long)((pp.size() + pg5.size() + 12 + std::max(dg->n_bins, 0)) * 8);
   double kin = 0, nel = 0, nho = 0;
   for (int b = 0; b < P.diag_blocks_p; ++b) {
     kin += pp[3 * b];
@@ -1245,6 +1273,18 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
   dg->n_electrons_macro = nel;
   dg->n_holes_macro = nho;
   dg->step = h->step;
+  dg->flux_plane[0] = P.flux_plane[0];
+  dg->flux_plane[1] = P.flux_plane[1];
+  dg->U_fwd[0] = acc[8];
+  dg->U_bwd[0] = acc[9];
+  dg->U_fwd[1] = acc[10];
+  dg->U_bwd[1] = acc[11];
+  dg->frac_reflected = dg->frac_transmitted = dg->frac_absorbed_flux = 0.0;
+  if (acc[8] > 0.0) {
+    dg->frac_reflected = acc[9] / acc[8];
+    dg->frac_transmitted = acc[10] / acc[8];
+    dg->frac_absorbed_flux = ((acc[8] - acc[9]) - (acc[10] - acc[11])) / acc[8];
+  }
   return PIC_OK;
 }
 
@@ -1556,7 +1596,7 @@ int pic_set_scalars(pic_handle h, long long step, const double in[4]) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 constexpr size_t kStageBytes = size_t(64) << 20;
 
 struct CkptHeader {

@@ -96,6 +96,13 @@ struct Dev {
   int imax_every;
   R inv_e0sq;
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
+                                  // [4] pushes [8..11] Poynting fwd/bwd front, back
+  // Poynting split: node planes (front, back), c eps0 dx dy dt, per-block
+  // partials (2 planes x kFluxBlocks x {fwd, bwd}) and the finished-block count
+  int flux_k[2];
+  double flux_scale;
+  double *flux_part;
+  unsigned int *flux_cnt;
   int *err;
   unsigned long long seed;
 };

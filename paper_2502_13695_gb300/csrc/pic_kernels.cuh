@@ -1136,18 +1136,89 @@ __global__ void k_init_material(Ctx<R> X) {
   (void)nx;
 }
 
-__global__ void k_advance(long long *step) { *step += 1; }
+// End of a step: the Poynting split at the two flux planes (blockIdx.y = 0
+// front, 1 back; kFluxBlocks blocks per plane over a fixed partition of its
+// points) and the step counter.  At node plane k the transverse E (Ex and
+// Ey of the plane) is paired with B averaged over planes k - 1 and k (By and
+// Bx at k - 1/2 and k + 1/2, the same transverse positions) and split into
+// the waves going along +z, ((Ex + c By) / 2, (Ey - c Bx) / 2), and along -z,
+// ((Ex - c By) / 2, (Ey + c Bx) / 2).  Each block writes its FP64 sums of
+// |fwd|^2 and |bwd|^2; the last block to finish (counted with one atomic,
+// nothing waits) adds them in block order times c eps0 dx dy dt to the time
+// integrals, advances the step and resets the count.
+constexpr int kFluxBlocks = 16;
+
+template <class R>
+__global__ void __launch_bounds__(256) k_flux_advance(Dev<R> D) {
+  const int q = blockIdx.y;
+  const long long base = (long long)D.flux_k[q] * D.nxy, basem = base - D.nxy;
+  double f = 0.0, b = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < D.nxy; r += gridDim.x * blockDim.x) {
+    const double cby = kC * 0.5 * ((double)D.B[1][basem + r] + (double)D.B[1][base + r]);
+    const double cbx = kC * 0.5 * ((double)D.B[0][basem + r] + (double)D.B[0][base + r]);
+    const double ex = (double)D.E[0][base + r], ey = (double)D.E[1][base + r];
+    const double fx = 0.5 * (ex + cby), fy = 0.5 * (ey - cbx);
+    const double bx = 0.5 * (ex - cby), by = 0.5 * (ey + cbx);
+    f += fx * fx + fy * fy;
+    b += bx * bx + by * by;
+  }
+  const double fs = block_sum<R>(f);
+  __syncthreads();
+  const double bs = block_sum<R>(b);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    double *p = D.flux_part + 2 * (q * gridDim.x + blockIdx.x);
+    p[0] = fs;
+    p[1] = bs;
+    __threadfence();
+    last = atomicAdd(D.flux_cnt, 1u) == 2u * gridDim.x - 1u;
+    if (last) {
+      __threadfence();
+      for (int qq = 0; qq < 2; ++qq) {
+        double F = 0.0, B = 0.0;
+        for (unsigned x = 0; x < gridDim.x; ++x) {
+          F += __ldcg(D.flux_part + 2 * (qq * gridDim.x + x));
+          B += __ldcg(D.flux_part + 2 * (qq * gridDim.x + x) + 1);
+        }
+        D.acc[8 + 2 * qq] += F * D.flux_scale;
+        D.acc[9 + 2 * qq] += B * D.flux_scale;
+      }
+      *D.flux_cnt = 0u;
+      *D.step += 1;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
-// Counting sort of the pool by cell (dead slots dropped)
+// Counting sort of the pool (dead slots dropped).  The key is the cell (the
+// collision pass forms its pairs per cell), or (kByFrame) the lowest node of
+// the particle's 3 x 3 x 3 deposit frame: its nearest integer node minus one
+// on each axis, x and y wrapped.  Sorted by frame, the particles a warp
+// pushes together share frame rows, so each of the deposit's vector
+// reductions touches a few consecutive nodes of one grid row instead of up
+// to four rows per cell.  Both keys lie in [0, ncell).
 // ---------------------------------------------------------------------------
-__global__ void k_hist(const int32_t *__restrict__ cell, const unsigned long long *nslots,
-                       unsigned long long cap, unsigned int *cnt) {
-  const unsigned long long n = min(*nslots, cap);
+template <bool kByFrame, class R>
+__device__ __forceinline__ int sort_key(const Dev<R> &D, int c, unsigned long long p) {
+  if constexpr (!kByFrame) {
+    return c;
+  } else {
+    const int nx = D.nx, ny = D.ny;
+    const int ci = c % nx, t = c / nx, cj = t % ny, ck = t / ny;
+    const int i0 = wrap(ci + (D.po[0][p] >= R(0.5) ? 0 : -1), nx);
+    const int j0 = wrap(cj + (D.po[1][p] >= R(0.5) ? 0 : -1), ny);
+    const int k0 = ck + (D.po[2][p] >= R(0.5) ? 0 : -1);
+    return (k0 * ny + j0) * nx + i0;
+  }
+}
+
+template <bool kByFrame, class R>
+__global__ void k_hist(Dev<R> D, unsigned int *cnt) {
+  const unsigned long long n = min(*D.nslots, D.cap);
   for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
        p += (unsigned long long)gridDim.x * blockDim.x) {
-    const int c = cell[p];
-    if (c >= 0) atomicAdd(cnt + c, 1u);
+    const int c = D.pcell[p];
+    if (c >= 0) atomicAdd(cnt + sort_key<kByFrame>(D, c, p), 1u);
   }
 }
 
@@ -1255,7 +1326,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, 
   }
 }
 
-template <class R>
+template <bool kByFrame, class R>
 __global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor) {
   const Dev<R> &D = X.d;
   const unsigned long long n = min(*D.nslots, D.cap);
@@ -1263,7 +1334,7 @@ __global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor)
        p += (unsigned long long)gridDim.x * blockDim.x) {
     const int c = D.pcell[p];
     if (c < 0) continue;
-    const unsigned int q = atomicAdd(cursor + c, 1u);
+    const unsigned int q = atomicAdd(cursor + sort_key<kByFrame>(D, c, p), 1u);
     X.acell[q] = c;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -89,7 +89,21 @@ class Diag(ctypes.Structure):
         ("step", ctypes.c_longlong), ("n_bins", ctypes.c_int), ("reserved", ctypes.c_int),
         ("e_min_eV", ctypes.c_double), ("e_max_eV", ctypes.c_double),
         ("region", ctypes.c_int * 6), ("reserved2", ctypes.c_int * 2),
-        ("spectrum", ctypes.POINTER(ctypes.c_double))]
+        ("spectrum", ctypes.POINTER(ctypes.c_double)),
+        ("flux_plane", ctypes.c_int * 2), ("U_fwd", ctypes.c_double * 2),
+        ("U_bwd", ctypes.c_double * 2), ("frac_reflected", ctypes.c_double),
+        ("frac_transmitted", ctypes.c_double), ("frac_absorbed_flux", ctypes.c_double)]
+
+_DIAG_ARRAYS = ("reserved", "reserved2", "region", "spectrum", "flux_plane", "U_fwd", "U_bwd")
+
+
+def diag_dict(dg: Diag) -> dict:
+    """The scalar outputs of a pic_diag, with the Poynting pairs named by plane."""
+    out = {f: getattr(dg, f) for f, _ in Diag._fields_ if f not in _DIAG_ARRAYS}
+    out.update(flux_front=dg.flux_plane[0], flux_back=dg.flux_plane[1],
+               U_fwd_front=dg.U_fwd[0], U_bwd_front=dg.U_bwd[0],
+               U_fwd_back=dg.U_fwd[1], U_bwd_back=dg.U_bwd[1])
+    return out
 
 
 _lib = None
@@ -315,8 +329,7 @@ class Simulation:
         spec = np.zeros(max(1, n_bins))
         dg.spectrum = spec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(lib().pic_diagnostics(self._h, ctypes.byref(dg)))
-        out = {f: getattr(dg, f) for f, _ in Diag._fields_
-               if f not in ("reserved", "reserved2", "region", "spectrum")}
+        out = diag_dict(dg)
         out["spectrum"] = spec[:n_bins]
         return out
 

@@ -109,8 +109,7 @@ class Server:
                     continue
                 req, _, F = out.pop(t)
                 pic._check(rc)
-                diag = {f: getattr(d, f) for f, _ in pic.Diag._fields_
-                        if f not in ("reserved", "reserved2", "region", "spectrum")}
+                diag = pic.diag_dict(d)
                 diag["spectrum"] = np.zeros(0)
                 if F is not None:
                     diag["fields"] = F
