@@ -1,0 +1,37 @@
+"""One rank of the two-rank z decomposition test (run as a subprocess by
+tests/test_decomp.py with the torchrun environment variables set): the slab
+of the shared test state advanced by an FP64 oracle engine, exchanging over
+gloo; writes its owned fields and particles to <out>/rank<r>.npz."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+import torch.distributed as dist  # noqa: E402
+
+import oracle  # noqa: E402
+from decomp_case import case  # noqa: E402
+from paper_2502_13695_gb300 import decomp  # noqa: E402
+
+
+def main():
+    out, steps = sys.argv[1], int(sys.argv[2])
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    dist.init_process_group("gloo")
+    cfg, F, P = case()
+    slab = decomp.ZSlab(cfg, rank, world, oracle.Sim, dist)
+    slab.set_state(F, P)
+    slab.step(steps)
+    k0, Fo = slab.owned_fields()
+    p = slab.owned_particles()
+    np.savez(os.path.join(out, f"rank{rank}.npz"), k0=k0, F=Fo, **p)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
