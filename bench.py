@@ -665,20 +665,22 @@ def run_serve(args):
     build.build()
     trace = wl.config5(args.serve_requests)
     reqs = [serve.Request(q, t["cfg"], t["cfg"]["steps"], t["arrival_s"]) for q, t in enumerate(trace)]
-    # one at a time: service time of every request alone, then FIFO in time
+    # one at a time: service time of every request alone (create, steps,
+    # diagnostics: the whole life of a request, as the server's
+    # time-to-result counts it), then FIFO in time
     service = []
     psteps_alone = 0.0
+    torch.cuda.synchronize()
     for r in reqs:
-        sim = pic.Simulation(r.cfg)
-        torch.cuda.synchronize()
         t0 = time.perf_counter()
+        sim = pic.Simulation(r.cfg)
         sim.step(r.steps)
-        sim.sync()
+        sim.diagnostics()
         service.append(time.perf_counter() - t0)
         psteps_alone += sim.info()["particle_steps"]
         sim.close()
         del sim
-        torch.cuda.empty_cache()
+    torch.cuda.empty_cache()
     free_at, fifo = 0.0, []
     for r, sv in zip(reqs, service):
         start = max(r.arrival_s, free_at)
@@ -691,6 +693,15 @@ def run_serve(args):
     wall = time.perf_counter() - t0
     lat = sorted(r.time_to_result_s for r in res)
     fifo = sorted(fifo)
+    # how many requests were resident at once (from admit / done times)
+    ev = sorted([(r.admit_s, 1) for r in res] + [(r.done_s, -1) for r in res])
+    live, peak_live, area = 0, 0, 0.0
+    for q, (t, dv) in enumerate(ev):
+        if q:
+            area += live * (t - ev[q - 1][0])
+        live += dv
+        peak_live = max(peak_live, live)
+    waits = sorted(r.admit_s - r.arrival_s for r in res)
 
     def pct(v, q):
         return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
@@ -706,7 +717,10 @@ def run_serve(args):
                                        "one_at_a_time_p50": pct(fifo, 0.5),
                                        "one_at_a_time_p99": pct(fifo, 0.99)},
             "serve_wall_s": wall, "one_at_a_time_busy_s": sum(service),
-            "last_arrival_s": reqs[-1].arrival_s}
+            "last_arrival_s": reqs[-1].arrival_s,
+            "resident": {"peak": peak_live, "mean": area / max(ev[-1][0] - ev[0][0], 1e-9)},
+            "admission_wait_s": {"p50": pct(waits, 0.5), "p99": pct(waits, 0.99)},
+            "one_at_a_time_particle_steps_per_s": psteps_alone / sum(service)}
     print(json.dumps(line), flush=True)
 
 
@@ -743,7 +757,7 @@ def main():
                     default="silica")
     ap.add_argument("--fluence", type=float, default=None,
                     help="peak fluence (J cm^-2) of the paper-geometry workloads")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--scan-instances", type=int, default=64)
     ap.add_argument("--scan-steps", type=int, default=1000)
     args = ap.parse_args()

@@ -377,9 +377,16 @@ int pic_batch_destroy(pic_batch b);
  * The paper runs one simulation per job; this is the request loop of a
  * fluence or stack sweep served on one GPU.  A server owns a host worker
  * thread on the device current at pic_serve_create.  Submitted requests
- * wait in submission order; the head of the queue is admitted as soon as
- * its state (pic_query's arena_bytes) fits budget_bytes next to the running
+ * wait in submission order and are admitted as soon as their state
+ * (pic_query's arena_bytes) fits budget_bytes next to the running
  * simulations, whose state stays resident on the device until they finish.
+ * A request that fits may be admitted before earlier ones that do not,
+ * unless the oldest waiting request has waited 1 s or more: then nothing
+ * passes it and memory frees up for it.  The state lives in the server's
+ * own device memory: chunks of 16 GiB (or one request's size) reserved with
+ * cudaMalloc when no free range fits, never more than budget_bytes in all,
+ * kept until pic_serve_destroy and handed out first-fit, so that admitting
+ * and finishing requests allocates and frees no device memory.
  * The running simulations with at least `quantum` steps left advance
  * together from one CUDA graph (pic_batch_*, rebuilt when that set
  * changes); one with fewer steps left takes them alone.  A finished
@@ -387,7 +394,9 @@ int pic_batch_destroy(pic_batch b);
  * device memory is released at once.
  *   pic_serve_create  : budget_bytes >= 1, quantum >= 1 steps.
  *   pic_serve_submit  : copies the configuration (as pic_create takes it)
- *                       and returns a ticket.  n_bins, e_min_eV, e_max_eV
+ *                       and returns a ticket (a request that cannot get
+ *                       device memory even with nothing running ends with
+ *                       PIC_ENOMEM).  n_bins, e_min_eV, e_max_eV
  *                       ask for the spectrum of pic_diagnostics (n_bins 0:
  *                       none); fields_out, if not NULL, is a host array of
  *                       15 * nfield doubles (layout of pic_get_fields) that

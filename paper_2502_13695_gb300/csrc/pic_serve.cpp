@@ -1,10 +1,16 @@
 // Serving: continuous batching of submitted simulations on one GPU.
 //
 // A host worker thread owns every running simulation.  Submitted requests
-// wait in submission order; the head of the queue is admitted as soon as its
-// state (pic_query's arena size) fits the budget next to the running ones,
-// and an admitted simulation keeps all of its state on the device until it
-// finishes.  The running simulations with at least a quantum of steps left
+// wait in submission order and are admitted as soon as their state
+// (pic_query's arena size) fits the budget next to the running ones; a
+// request that fits may go ahead of earlier ones that do not, unless the
+// oldest waiting request has waited longer than kHeadWait, in which case
+// memory is left to free up for it.  Each admitted simulation keeps all of
+// its state on the device until it finishes, in a range of the server's
+// own device memory (DeviceArena): chunks reserved with cudaMalloc as
+// requests need them, up to the budget, and kept until the server is
+// destroyed, so admitting and finishing requests neither allocates nor
+// frees device memory (cudaFree would wait for the whole device).  The running simulations with at least a quantum of steps left
 // advance together from one CUDA graph (pic_batch_*), rebuilt only when that
 // set changes; one with fewer steps left takes them alone.  A finished
 // request's FP64 diagnostics (and, if asked, its final fields) are kept until
@@ -13,6 +19,7 @@
 // Built only on the public C ABI of the simulation (include/pic.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -64,7 +71,90 @@ struct Running {
   std::shared_ptr<Request> req;
   pic_handle h = nullptr;
   cudaStream_t stream = nullptr;
+  char *arena = nullptr;  // the request's range of the server's device memory
   long long left = 0;
+};
+
+// A waiting request older than this blocks the admission of later ones.
+constexpr double kHeadWait = 1.0;  // seconds
+
+// Device memory of a server: chunks of at least kChunk bytes (or one
+// request's arena) reserved with cudaMalloc when no free range fits, never
+// more than the budget in total, carved first-fit into 256-byte aligned
+// ranges and coalesced when released.
+class DeviceArena {
+ public:
+  static constexpr size_t kAlign = 256;
+  static constexpr size_t kChunk = size_t(16) << 30;
+
+  explicit DeviceArena(unsigned long long budget) : budget_(budget) {}
+  ~DeviceArena() {
+    for (Chunk &c : chunks_) cudaFree(c.base);
+  }
+
+  // A range of n bytes, or nullptr when none is free now (and no chunk may
+  // or can be reserved).
+  char *alloc(size_t n) {
+    n = (n + kAlign - 1) / kAlign * kAlign;
+    for (Chunk &c : chunks_)
+      for (auto it = c.free.begin(); it != c.free.end(); ++it)
+        if (it->second >= n) {
+          const size_t off = it->first, len = it->second;
+          c.free.erase(it);
+          if (len > n) c.free[off + n] = len - n;
+          return c.base + off;
+        }
+    if (reserved_ + n > budget_) return nullptr;
+    size_t size = std::max(n, std::min<size_t>(kChunk, (size_t)(budget_ - reserved_)));
+    char *base = nullptr;
+    if (cudaMalloc((void **)&base, size) != cudaSuccess) {
+      (void)cudaGetLastError();
+      size = n;
+      if (cudaMalloc((void **)&base, size) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+      }
+    }
+    Chunk c;
+    c.base = base;
+    c.size = size;
+    if (size > n) c.free[n] = size - n;
+    chunks_.push_back(std::move(c));
+    reserved_ += size;
+    return base;
+  }
+
+  void release(char *p, size_t n) {
+    n = (n + kAlign - 1) / kAlign * kAlign;
+    for (Chunk &c : chunks_) {
+      if (p < c.base || p >= c.base + c.size) continue;
+      size_t off = (size_t)(p - c.base);
+      auto next = c.free.lower_bound(off);
+      if (next != c.free.end() && off + n == next->first) {
+        n += next->second;
+        next = c.free.erase(next);
+      }
+      if (next != c.free.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+          prev->second += n;
+          return;
+        }
+      }
+      c.free[off] = n;
+      return;
+    }
+  }
+
+ private:
+  struct Chunk {
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free;  // offset -> length
+  };
+  std::vector<Chunk> chunks_;
+  unsigned long long budget_;
+  unsigned long long reserved_ = 0;
 };
 
 }  // namespace
@@ -84,6 +174,7 @@ struct pic_server_ctx {
   // worker-only state
   std::vector<Running> running;
   unsigned long long used = 0;
+  std::unique_ptr<DeviceArena> mem;
   pic_batch batch = nullptr;
   std::vector<pic_handle> batch_members;
 
@@ -111,9 +202,13 @@ void pic_server_ctx::finish(Running &r, int status, const std::string &msg) {
   }
   const std::string m = status == PIC_OK ? std::string() : (msg.empty() ? pic_last_error() : msg);
   if (r.h) pic_destroy(r.h);
+  // the handle's stream has no work left (every finish follows a sync or a
+  // failed create), so the range is free for the next request
   if (r.stream) cudaStreamDestroy(r.stream);
+  if (r.arena) mem->release(r.arena, q.need);
   r.h = nullptr;
   r.stream = nullptr;
+  r.arena = nullptr;
   used -= q.need;
   std::lock_guard<std::mutex> lk(mu);
   q.status = status;
@@ -123,19 +218,40 @@ void pic_server_ctx::finish(Running &r, int status, const std::string &msg) {
   cv_done.notify_all();
 }
 
-// Admit from the head of the queue while the next request fits.
+// Admit waiting requests in submission order while they fit the budget and
+// a free range of the server's memory; later requests may pass one that does
+// not fit, unless the oldest waiting request has waited kHeadWait or longer.
 void pic_server_ctx::admit() {
-  for (;;) {
+  for (size_t idx = 0;;) {
     std::shared_ptr<Request> q;
+    char *arena = nullptr;
     {
       std::lock_guard<std::mutex> lk(mu);
-      if (waiting.empty() || used + waiting.front()->need > budget) return;
-      q = waiting.front();
-      waiting.pop_front();
+      if (idx >= waiting.size()) return;
+      if (idx > 0 && now() - waiting.front()->t_submit >= kHeadWait) return;
+      q = waiting[idx];
+      if (used + q->need <= budget) arena = mem->alloc(q->need);
+      if (!arena) {
+        if (running.empty() && used == 0) {
+          // nothing holds memory and the range still cannot be had: the
+          // device itself is out of memory for this request
+          waiting.erase(waiting.begin() + (long)idx);
+          q->status = PIC_ENOMEM;
+          q->message = "no device memory for the request's state";
+          q->t_admit = q->t_done = now();
+          q->done = true;
+          cv_done.notify_all();
+          continue;
+        }
+        ++idx;
+        continue;
+      }
+      waiting.erase(waiting.begin() + (long)idx);
     }
     Running r;
     r.req = q;
     r.left = q->steps;
+    r.arena = arena;
     used += q->need;
     q->t_admit = now();
     int rc = PIC_OK;
@@ -150,7 +266,7 @@ void pic_server_ctx::admit() {
       std::memset(&m, 0, sizeof(m));
       m.n_layers = (int)q->layers.size();
       m.layers = q->layers.data();
-      rc = pic_create(&q->grid, &m, &q->pulse, q->seed, r.stream, nullptr, 0, &r.h);
+      rc = pic_create(&q->grid, &m, &q->pulse, q->seed, r.stream, arena, q->need, &r.h);
     }
     if (rc != PIC_OK || r.left == 0) {
       finish(r, rc, msg);
@@ -300,6 +416,7 @@ int pic_serve_create(double budget_bytes, int quantum, pic_server *out) {
   try {
     s = new pic_server_ctx();
     s->budget = (unsigned long long)budget_bytes;
+    s->mem.reset(new DeviceArena(s->budget));
     s->quantum = quantum;
     s->device = dev;
     s->t0 = Clock::now();

@@ -3,7 +3,9 @@
 The loop itself is native (pic_serve_* in csrc/pic_serve.cpp): a host
 worker thread admits submitted requests in submission order as soon as
 their state fits the device-memory budget next to the running ones (the
-arena size comes from pic_query), keeps every admitted simulation's fields,
+arena size comes from pic_query; later requests may pass one that does not
+fit until it has waited 1 s; the state lives in ranges of the server's own
+device memory, reserved in chunks up to the budget), keeps every admitted simulation's fields,
 particles and RNG state on the device until it finishes, advances the
 running ones together in quanta of 32 steps from one CUDA graph
 (pic_batch_*, rebuilt when the running set changes), lets a request with

@@ -136,3 +136,58 @@ def test_native_server_statuses_and_spectrum(mods):
     t0 = time.perf_counter()
     L.pic_serve_destroy(srv)
     assert time.perf_counter() - t0 < 30.0
+
+
+def test_fp32_requests_overlap_and_match_alone(mods):
+    """FP32, the serving precision: three requests submitted together run
+    co-resident (each is admitted before another finishes, so their steps
+    share the device), and each result stays as close to the same request
+    run alone as two runs alone are to each other.  FP32 deposits sum in a
+    varying order and an ionising plasma amplifies the difference, so the
+    bound is measured: four times the spread of two runs alone, plus the
+    per-step FP32 bound 2e-5."""
+    pic, serve = mods
+    cfgs = [wl.small_slab(precision="fp32", seed=41),
+            wl.small_slab(nx=12, ny=8, nz=40, z0=14, z1=30, precision="fp32", seed=42, fluence=2.0),
+            wl.small_slab(nx=8, ny=8, nz=24, z0=8, z1=16, precision="fp32", seed=43, static=True)]
+    steps = [200, 280, 240]
+    reqs = [serve.Request(q, c, s, arrival_s=0.0) for q, (c, s) in enumerate(zip(cfgs, steps))]
+    res = {r.rid: r for r in serve.Server(budget_bytes=1e12, keep_state=True).run(reqs)}
+    assert sorted(res) == [0, 1, 2]
+    # co-resident: every request was admitted before every other one finished
+    for a in res.values():
+        for b in res.values():
+            if a is not b:
+                assert a.admit_s < b.done_s, (a.rid, a.admit_s, b.rid, b.done_s)
+    for rid, r in res.items():
+        d, F = _alone(pic, reqs[rid])
+        _, F2 = _alone(pic, reqs[rid])
+        for sl in (slice(0, 3), slice(3, 6), slice(9, 12)):
+            bound = 4 * rel_l2(F2[sl], F[sl]) + 2e-5
+            assert rel_l2(r.diagnostics["fields"][sl], F[sl]) <= bound, (rid, sl, bound)
+        assert r.diagnostics["N_pairs"] == pytest.approx(d["N_pairs"], rel=1e-2)
+        assert r.diagnostics["frac_absorbed"] == pytest.approx(d["frac_absorbed"], rel=1e-2)
+        assert r.diagnostics["step"] == steps[rid]
+        assert d["N_pairs"] > 0
+
+
+def test_small_request_passes_a_head_that_does_not_fit(mods):
+    """A large request at the head of the queue that cannot fit next to a
+    running one does not hold back a later small request that fits."""
+    pic, serve = mods
+    big = wl.small_slab(nx=16, ny=16, nz=64, z0=10, z1=54, precision="fp32", seed=52)
+    run = wl.small_slab(precision="fp32", seed=51)
+    small = wl.small_slab(nx=4, ny=4, nz=16, z0=4, z1=12, precision="fp32", seed=53)
+    sz = {k: pic.query(c)["arena_bytes"] for k, c in (("run", run), ("big", big), ("small", small))}
+    # the big request fits the budget alone but not next to the running one;
+    # the small one fits next to it
+    budget = sz["big"] + sz["small"] + 4096
+    assert sz["run"] + sz["big"] > budget and sz["run"] + sz["small"] <= budget
+    reqs = [serve.Request(0, run, 600, arrival_s=0.0),
+            serve.Request(1, big, 40, arrival_s=0.005),
+            serve.Request(2, small, 40, arrival_s=0.010)]
+    res = {r.rid: r for r in serve.Server(budget_bytes=budget).run(reqs)}
+    assert sorted(res) == [0, 1, 2]
+    assert res[2].admit_s < res[0].done_s  # passed the waiting head
+    assert res[1].admit_s >= min(res[0].done_s, res[2].done_s) - 1e-6  # waited for memory
+    assert res[2].admit_s < res[1].admit_s
