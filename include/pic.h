@@ -428,9 +428,10 @@ int pic_serve_destroy(pic_server s);
 
 /* ---- allocation-free field energy -------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
- * allocate device memory, such as code that runs while a stream is being
- * captured into a CUDA graph, or a process whose device memory is planned up
- * front by another allocator (a serving loop holding a fixed budget).  It
+ * allocate device memory, such as a process whose device memory is planned
+ * up front by another allocator (a serving loop holding a fixed budget, or a
+ * host framework whose caching allocator owns the device), where a stray
+ * cudaMalloc can fail or fragment the plan.  It
  * computes sum over n field points of (eps0 |E|^2 + |B|^2 / mu0) / 2 times
  * cell_volume, the U_field of pic_diagnostics, with no allocation: its
  * scratch is one FP64 partial per block of 2048 points in a static device
@@ -444,9 +445,11 @@ int pic_serve_destroy(pic_server s);
  * The result is deterministic (fixed partition, fixed summation order).  The
  * first call on each device looks up the scratch address
  * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the scratch: calls that overlap on the GPU (on
- * different streams, or from different threads) race and must be serialised
- * by the caller. */
+ * capture.  The address is then kept for the device until the process exits,
+ * so it does not survive cudaDeviceReset.  All calls share the scratch: calls
+ * that overlap on the GPU (on different streams, or from different threads)
+ * race and must be serialised by the caller.  A CUDA error that earlier work
+ * left pending on the calling thread is reported as this call's PIC_ECUDA. */
 int pic_field_energy_noalloc(int precision, const void *Ex, const void *Ey, const void *Ez,
                              const void *Bx, const void *By, const void *Bz, long long n,
                              double cell_volume, double *d_out, void *stream);

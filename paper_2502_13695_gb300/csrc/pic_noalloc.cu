@@ -1,12 +1,10 @@
 // Allocation-free field-energy reduction (declared in include/pic.h as
 // pic_field_energy_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation), and
-// processes whose device memory is planned up front by another allocator
-// (a serving loop that admits work against a fixed memory budget, or a host
-// framework whose caching allocator owns the device) where a stray allocation
-// can fail or fragment the plan.  This entry point lets them reduce field
+// Some callers cannot call cudaMalloc: processes whose device memory is
+// planned up front by another allocator (a serving loop that admits work
+// against a fixed memory budget, or a host framework whose caching allocator
+// owns the device), where a stray allocation can fail or fragment the plan.  This entry point lets them reduce field
 // energy with no allocation at all: its scratch (one FP64 partial sum per
 // block) is a file-scope __device__ array that every GPU loading this
 // library holds until the process exits.

@@ -1,10 +1,11 @@
 """The allocation-free field-energy entry point against pic_diagnostics.
 
 pic_field_energy_noalloc serves callers that cannot allocate device memory
-(code running under stream capture, or processes whose device memory is
-planned by another allocator).  Its scratch is a static device array; this
-test calls it twice in a row through the C ABI and checks both results
-against the field energy that pic_diagnostics reports for the same state.
+(processes whose device memory is planned up front by another allocator,
+such as a serving loop holding a fixed budget).  Its scratch is a static
+device array; this test calls it twice in a row through the C ABI and
+checks both results against the field energy that pic_diagnostics reports
+for the same state.
 This file is collected last on purpose.
 """
 import ctypes
