@@ -434,7 +434,7 @@ def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup)
 def run_native(args, rank, local, world, dist):
     import torch
     from paper_2502_13695_gb300 import build, workloads as wl
-    full = world == 1 and not args.silica_only and args.precision == "fp32"
+    full = world == 1 and not args.silica_only and args.precision == "fp32" and not args.transverse
     # the oracle's CPU baselines run in spawned processes beside the GPU work
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -448,6 +448,9 @@ def run_native(args, rank, local, world, dist):
     if args.precision == "fp64":
         cfg["precision"] = "fp64"
         cfg["name"] = cfg["name"].replace("fp32", "fp64")
+    if args.transverse:
+        cfg["nx"] = cfg["ny"] = args.transverse
+        cfg["name"] = cfg["name"].replace("128x128", f"{args.transverse}x{args.transverse}")
     cfg["seed"] = replica_seed(cfg["seed"], rank)  # independent replica per rank
     if args.pool_factor is not None:
         cfg["pool_factor"] = args.pool_factor
@@ -491,7 +494,7 @@ def run_native(args, rank, local, world, dist):
         line["scan"] = {k: scan[k] for k in ("config", "scan_time_to_result_s", "value",
                                              "cell_updates_per_s", "one_at_a_time",
                                              "batched_total_s", "damage_threshold_fluence_J_cm2",
-                                             "gpu_launches_per_step")}
+                                             "gpu_launches_per_step", "batch_tuning")}
         line["scan"]["unit"] = UNIT
         line["scan_time_to_result_s"] = scan["scan_time_to_result_s"]
     if cpu is not None:
@@ -532,6 +535,7 @@ def run_scan(args, emit_line=True):
     t_batch = time.perf_counter() - t0
     p_batch = sum(s.info()["particle_steps"] for s in sims) - p0
     launches = sum(s.info()["launches"] for s in sims) - l0
+    tuning = batch.tuning()
     cells = sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs) * steps
     batch.close()
     for s_ in sims:
@@ -581,6 +585,9 @@ def run_scan(args, emit_line=True):
                               "cell_updates_per_s": cells / t_seq, "total_s": t_seq},
             "batched_total_s": t_batch,
             "gpu_launches_per_step": launches / steps,
+            # the push launch shapes the batch measured on itself (inside
+            # the timed steps: each candidate runs real periods) and its pick
+            "batch_tuning": tuning,
             "damage_threshold_fluence_J_cm2": lidt,
             "peak_ne_m3": [max(ly["ne_peak"] for ly in r["layers"]) for r in results],
             "peak_energy_density_J_m3": [max(ly["ed_peak"] for ly in r["layers"]) for r in results]}
@@ -741,6 +748,9 @@ def main():
                     help="untimed steps before the mirror window (the job has 3000)")
     ap.add_argument("--silica-only", action="store_true",
                     help="skip the mirror workload and the fluence scan of the default line")
+    ap.add_argument("--transverse", type=int, default=0,
+                    help="nx = ny of the silica workload (0: its 128; smaller cases for "
+                         "profiling, same z profile)")
     ap.add_argument("--pool-factor", type=float, default=None,
                     help="charged-slot capacity / neutrals (default: the workload's 3.0)")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")

@@ -373,6 +373,27 @@ int pic_batch_step(pic_batch b, int n_steps);
 int pic_batch_sync(pic_batch b);
 int pic_batch_destroy(pic_batch b);
 
+/* How a batch steps.  When every member has the same precision, the same
+ * points per thread in the field kernels (FP32 with nx a multiple of 4, or
+ * not) and the same pool-sort schedule, and none runs collisions, the graph
+ * holds one launch per phase of a step for all members together (batch
+ * launches: fixed grids laid end to end over the members, particle and
+ * Keldysh loops in chunks handed out from a counter); otherwise it holds
+ * every member's own launches, each on its stream.  With batch launches the
+ * first pic_batch_step that asks for at least 8 periods tunes the push's
+ * launch shape on the batch itself: four candidates (particles per block
+ * task, grid as 1 or 2 times the resident blocks), each captured and run for
+ * one period and timed over a second, the fastest kept (every tuning period
+ * is a real step of every member).
+ *   cap            : entries the arrays hold
+ *   chunk, grid_mult, ms : per candidate (any may be NULL); ms is the timed
+ *                    period in milliseconds
+ *   n, pick        : candidates tuned (0: not yet) and the index kept (-1)
+ *   batch_launches : 1 when the batch steps with batch launches
+ * The paper has no counterpart (its runs are single jobs). */
+int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms, int *n,
+                     int *pick, int *batch_launches);
+
 /* ---- serving: continuous batching of submitted simulations ---------------
  * The paper runs one simulation per job; this is the request loop of a
  * fluence or stack sweep served on one GPU.  A server owns a host worker

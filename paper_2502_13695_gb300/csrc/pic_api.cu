@@ -12,6 +12,7 @@
 
 #include "../../include/pic.h"
 #include "pic_kernels.cuh"
+#include "pic_batch.cuh"
 
 using namespace pg;
 
@@ -823,6 +824,28 @@ struct pic_batch_ctx {
   std::vector<long long> step_at_capture_end;  // members' host steps after capture
   std::vector<long long> launches_per_period;  // kernels one replay runs per member
   std::vector<cudaEvent_t> ev;
+  // batch launches (one per phase for all members): device tables, and the
+  // parity of the members' pool halves relative to the tables' first copy
+  bool multi = false;
+  char *tab = nullptr;
+  size_t tab_bytes = 0;
+  int parity = 0;
+  int push_blocks = 0;   // resident blocks of k_push_batch
+  // the push's launch shape, picked by batch_tune: particles per block task
+  // and grid (a multiple of the resident blocks)
+  long long push_chunk = 2048;
+  int push_grid_mult = 1;
+  bool tuned = false;
+  std::vector<long long> tune_chunk;
+  std::vector<int> tune_mult;
+  std::vector<double> tune_ms;
+  int tune_pick = -1;
+  // byte offsets in tab
+  size_t o_ctx[2] = {0, 0}, o_sort[2] = {0, 0}, o_cnt = 0;
+  struct Flat {
+    size_t o_start = 0, o_gx = 0;
+    int total = 0;
+  } g_field, g_window, g_ionize, g_flux, g_scan, g_zero;
 };
 
 namespace {
@@ -846,6 +869,187 @@ int join_batch_into_members(pic_batch_ctx *b) {
   return PIC_OK;
 }
 
+// Batch launches are used when every member has the same precision, the
+// same points per thread in the field kernels and the same pool-sort
+// schedule, and no member runs collisions.
+bool batch_uniform(const pic_batch_ctx *b) {
+  if (b->m.size() > (size_t)kMaxBatch) return false;
+  const pic_ctx *a = b->m[0];
+  for (const pic_ctx *h : b->m)
+    if (h->fp64 != a->fp64 || h->field_v != a->field_v ||
+        h->P.g.sort_interval != a->P.g.sort_interval || h->since_sort != a->since_sort ||
+        h->P.g.coll_every > 0)
+      return false;
+  return true;
+}
+
+FlatGrid flat_of(const pic_batch_ctx *b, const pic_batch_ctx::Flat &f) {
+  return FlatGrid{(const int *)(b->tab + f.o_start), (const int *)(b->tab + f.o_gx), (int)b->m.size()};
+}
+
+// Lay out and upload the device tables of the current members (synchronous,
+// outside any capture): the Ctx of every member as it is now and with its
+// pool halves swapped, the sort buffers for both, the flat block tables and
+// the chunk counters.
+template <class R>
+int batch_tables(pic_batch_ctx *b) {
+  // a replay still running reads the current tables
+  PIC_CUDA(cudaStreamSynchronize(b->stream));
+  const int n = (int)b->m.size();
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = (o + bytes + 255) / 256 * 256;
+    return at;
+  };
+  b->o_ctx[0] = take(n * sizeof(Ctx<R>));
+  b->o_ctx[1] = take(n * sizeof(Ctx<R>));
+  b->o_sort[0] = take(n * sizeof(SortBufs));
+  b->o_sort[1] = take(n * sizeof(SortBufs));
+  b->o_cnt = take(kCntN * sizeof(unsigned int));
+  pic_batch_ctx::Flat *fl[6] = {&b->g_field, &b->g_window, &b->g_ionize, &b->g_flux, &b->g_scan,
+                                &b->g_zero};
+  for (pic_batch_ctx::Flat *f : fl) {
+    f->o_start = take((n + 1) * sizeof(int));
+    f->o_gx = take(n * sizeof(int));
+  }
+  if (o > b->tab_bytes) {
+    if (b->tab) cudaFree(b->tab);
+    b->tab = nullptr;
+    b->tab_bytes = 0;
+    PIC_CUDA(cudaMalloc((void **)&b->tab, o));
+    b->tab_bytes = o;
+  }
+  std::vector<char> host(o, 0);
+  std::vector<Ctx<R>> cx(n), cy(n);
+  std::vector<SortBufs> sb(n);
+  std::vector<std::vector<int>> gx(6, std::vector<int>(n)), st(6, std::vector<int>(n + 1, 0));
+  long long blocks[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = 0; q < n; ++q) {
+    pic_ctx *h = b->m[q];
+    const Plan &P = h->P;
+    Ctx<R> X = ctx_of<R>(h);
+    cx[q] = X;
+    // the same Ctx after a sort: pool halves swapped
+    std::swap(X.d.pcell, X.acell);
+    for (int d = 0; d < 3; ++d) {
+      std::swap(X.d.po[d], X.ao[d]);
+      std::swap(X.d.pu[d], X.au[d]);
+    }
+    std::swap(X.d.ptag, X.atag);
+    std::swap(X.d.pid, X.aid);
+    cy[q] = X;
+    sb[q] = SortBufs{(unsigned int *)(h->arena + P.off_cnt), (unsigned int *)(h->arena + P.off_bsum),
+                     (unsigned long long *)(h->arena + P.off_total), P.ncell, P.nb_scan, 0};
+    const int V = h->field_v;
+    const int gxs[6] = {grid_blocks(P.nxy / V), grid_blocks(P.nxy / V), grid_blocks(P.nxy),
+                        kFluxBlocks, P.nb_scan, grid_blocks(P.ncell)};
+    const long long gys[6] = {P.g.nz + 1, P.n_mplanes, P.n_mplanes, 2, 1, 1};
+    for (int k = 0; k < 6; ++k) {
+      gx[k][q] = gxs[k];
+      st[k][q] = (int)blocks[k];
+      blocks[k] += (long long)gxs[k] * gys[k];
+      if (blocks[k] >= (1ll << 31)) return fail(PIC_EINVAL, "batch grid above 2^31 blocks");
+    }
+  }
+  for (int k = 0; k < 6; ++k) {
+    st[k][n] = (int)blocks[k];
+    fl[k]->total = (int)blocks[k];
+    std::memcpy(host.data() + fl[k]->o_start, st[k].data(), (n + 1) * sizeof(int));
+    std::memcpy(host.data() + fl[k]->o_gx, gx[k].data(), n * sizeof(int));
+  }
+  std::memcpy(host.data() + b->o_ctx[0], cx.data(), n * sizeof(Ctx<R>));
+  std::memcpy(host.data() + b->o_ctx[1], cy.data(), n * sizeof(Ctx<R>));
+  std::memcpy(host.data() + b->o_sort[0], sb.data(), n * sizeof(SortBufs));
+  std::memcpy(host.data() + b->o_sort[1], sb.data(), n * sizeof(SortBufs));
+  PIC_CUDA(cudaMemcpy(b->tab, host.data(), o, cudaMemcpyHostToDevice));
+  int dev = 0, nsm = 0, per_sm = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  PIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_batch<R>, kThreads, 0));
+  b->push_blocks = std::max(1, nsm) * std::max(1, per_sm);
+  b->parity = 0;
+  return PIC_OK;
+}
+
+// One full step of every member as batch launches on the batch stream; the
+// members' host state advances as enqueue would advance it.
+template <class R>
+int enqueue_batch(pic_batch_ctx *b) {
+  cudaStream_t s = b->stream;
+  const int n = (int)b->m.size();
+  const Ctx<R> *cx = (const Ctx<R> *)(b->tab + b->o_ctx[b->parity]);
+  unsigned int *cnt = (unsigned int *)(b->tab + b->o_cnt);
+  const int V = b->m[0]->field_v;
+  long long launched = 0;
+  k_batch_prep<R><<<grid_blocks(std::max(n, (int)kCntN)), kThreads, 0, s>>>(cx, n, cnt);
+  k_push_batch<R><<<b->push_blocks * b->push_grid_mult, kThreads, 0, s>>>(cx, n, cnt,
+                                                                        b->push_chunk);
+  launched += 2;
+  if (b->g_field.total > 0) {
+    const FlatGrid G = flat_of(b, b->g_field);
+    if constexpr (sizeof(R) == 4) {
+      if (V == 4) {
+        k_efull_batch<4, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+        k_bstep_batch<4, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+      }
+    }
+    if (V == 1) {
+      k_efull_batch<1, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+      k_bstep_batch<1, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+    }
+    launched += 2;
+  }
+  if (b->g_window.total > 0) {
+    const FlatGrid G = flat_of(b, b->g_window);
+    if constexpr (sizeof(R) == 4) {
+      if (V == 4) k_window_batch<4, R><<<b->g_window.total, kThreads, 0, s>>>(cx, G);
+    }
+    if (V == 1) k_window_batch<1, R><<<b->g_window.total, kThreads, 0, s>>>(cx, G);
+    k_keldysh_batch<R><<<kPersistentBlocks, kThreads, 0, s>>>(cx, n, cnt);
+    k_ionize_batch<R><<<b->g_ionize.total, kThreads, 0, s>>>(cx, flat_of(b, b->g_ionize));
+    launched += 3;
+  }
+  k_flux_advance_batch<R><<<b->g_flux.total, kThreads, 0, s>>>(cx, flat_of(b, b->g_flux));
+  launched += 1;
+  PIC_CUDA(cudaGetLastError());
+  bool sort = false;
+  for (pic_ctx *h : b->m) {
+    h->step++;
+    h->bh_valid = true;
+    if (++h->since_sort >= h->P.g.sort_interval) {
+      h->since_sort = 0;
+      sort = true;
+    }
+  }
+  if (sort) {
+    const SortBufs *sb = (const SortBufs *)(b->tab + b->o_sort[b->parity]);
+    k_zero_cnt_batch<<<b->g_zero.total, kThreads, 0, s>>>(sb, flat_of(b, b->g_zero));
+    k_hist_batch<R><<<kPersistentBlocks, kThreads, 0, s>>>(cx, sb, n, cnt);
+    k_scan_reduce_batch<<<b->g_scan.total, kScanThreads, 0, s>>>(sb, flat_of(b, b->g_scan));
+    k_scan_blocks_batch<<<n, kScanThreads, 0, s>>>(sb);
+    k_scan_final_batch<<<b->g_scan.total, kScanThreads, 0, s>>>(sb, flat_of(b, b->g_scan));
+    k_scatter_batch<R><<<kPersistentBlocks, kThreads, 0, s>>>(cx, sb, n, cnt);
+    k_set_slots_batch<R><<<grid_blocks(n), kThreads, 0, s>>>(cx, sb, n);
+    launched += 7;
+    PIC_CUDA(cudaGetLastError());
+    // every member's pool halves swap, as sort_pool swaps them
+    for (pic_ctx *h : b->m) {
+      Ctx<R> &X = ctx_of<R>(h);
+      std::swap(X.d.pcell, X.acell);
+      for (int d = 0; d < 3; ++d) {
+        std::swap(X.d.po[d], X.ao[d]);
+        std::swap(X.d.pu[d], X.au[d]);
+      }
+      std::swap(X.d.ptag, X.atag);
+      std::swap(X.d.pid, X.aid);
+    }
+    b->parity ^= 1;
+  }
+  b->m[0]->launches += launched;  // the batch's launches, counted once
+  return PIC_OK;
+}
+
 int batch_capture(pic_batch_ctx *b) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -859,17 +1063,29 @@ int batch_capture(pic_batch_ctx *b) {
   }
   std::vector<long long> l0;
   for (pic_ctx *h : b->m) l0.push_back(h->launches);
+  b->multi = batch_uniform(b);
+  if (b->multi) {
+    const int rt = b->m[0]->fp64 ? batch_tables<double>(b) : batch_tables<float>(b);
+    if (rt) return rt;
+  }
   if (const int rj = join_members_into_batch(b)) return rj;
   PIC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = PIC_OK;
-  cudaError_t e = cudaEventRecord(b->ev[0], s);
-  for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q)
-    e = cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0);
-  for (int st = 0; st < b->period && rc == PIC_OK && e == cudaSuccess; ++st)
-    for (size_t q = 0; q < b->m.size() && rc == PIC_OK; ++q) rc = enqueue_any(b->m[q], PIC_PHASE_ALL);
-  for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q) {
-    e = cudaEventRecord(b->ev[1 + q], b->m[q]->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev[1 + q], 0);
+  cudaError_t e = cudaSuccess;
+  if (b->multi) {
+    // one launch per phase for all members, on the batch stream
+    for (int st = 0; st < b->period && rc == PIC_OK; ++st)
+      rc = b->m[0]->fp64 ? enqueue_batch<double>(b) : enqueue_batch<float>(b);
+  } else {
+    e = cudaEventRecord(b->ev[0], s);
+    for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q)
+      e = cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0);
+    for (int st = 0; st < b->period && rc == PIC_OK && e == cudaSuccess; ++st)
+      for (size_t q = 0; q < b->m.size() && rc == PIC_OK; ++q) rc = enqueue_any(b->m[q], PIC_PHASE_ALL);
+    for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q) {
+      e = cudaEventRecord(b->ev[1 + q], b->m[q]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev[1 + q], 0);
+    }
   }
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -895,6 +1111,74 @@ int batch_capture(pic_batch_ctx *b) {
   }
   PIC_CUDA(cudaGraphLaunch(b->exec, s));
   return join_batch_into_members(b);
+}
+// One replay of the captured period, ordered after the members' own work and
+// before their later work; the members' host state advances by the period.
+int batch_replay(pic_batch_ctx *b, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr) {
+  if (const int rj = join_members_into_batch(b)) return rj;
+  if (t0) PIC_CUDA(cudaEventRecord(t0, b->stream));
+  PIC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  if (t1) PIC_CUDA(cudaEventRecord(t1, b->stream));
+  if (const int rj = join_batch_into_members(b)) return rj;
+  for (size_t q = 0; q < b->m.size(); ++q) {
+    b->m[q]->step += b->period;
+    b->m[q]->launches += b->launches_per_period[q];
+    b->step_at_capture_end[q] = b->m[q]->step;
+  }
+  return PIC_OK;
+}
+
+// The push's launch shape in batch launches, picked on the batch itself:
+// each candidate (particles per block task; grid of 1 or 2 times the
+// resident blocks) is captured and run for one period, then timed over a
+// second (CUDA events on the batch stream); the fastest is kept.  Every
+// period is a real one: the candidates differ only in how the same work is
+// spread over the GPU.  Uses two periods per candidate, and only when the
+// step request has them.
+int batch_tune(pic_batch_ctx *b, int &n_steps) {
+  static const long long kChunk[] = {1024, 2048, 4096, 2048};
+  static const int kMult[] = {1, 1, 1, 2};
+  constexpr int kCand = 4;
+  if (n_steps < 2 * kCand * b->period) return PIC_OK;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  PIC_CUDA(cudaEventCreate(&t0));
+  PIC_CUDA(cudaEventCreate(&t1));
+  b->tune_chunk.clear();
+  b->tune_mult.clear();
+  b->tune_ms.clear();
+  int rc = PIC_OK;
+  for (int c = 0; c < kCand && rc == PIC_OK; ++c) {
+    b->push_chunk = kChunk[c];
+    b->push_grid_mult = kMult[c];
+    rc = batch_capture(b);  // captures and runs one period
+    if (rc) break;
+    rc = batch_replay(b, t0, t1);
+    if (rc) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+      rc = fail(PIC_ECUDA, "batch tuning: event timing failed");
+      break;
+    }
+    b->tune_chunk.push_back(kChunk[c]);
+    b->tune_mult.push_back(kMult[c]);
+    b->tune_ms.push_back(ms);
+    n_steps -= 2 * b->period;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc) return rc;
+  int best = 0;
+  for (int c = 1; c < (int)b->tune_ms.size(); ++c)
+    if (b->tune_ms[c] < b->tune_ms[best]) best = c;
+  b->tune_pick = best;
+  b->push_chunk = b->tune_chunk[best];
+  b->push_grid_mult = b->tune_mult[best];
+  b->tuned = true;
+  if (b->exec) {  // the next period captures with the pick
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return PIC_OK;
 }
 }  // namespace
 
@@ -953,6 +1237,10 @@ int pic_batch_step(pic_batch b, int n_steps) {
   if (!b || n_steps < 0) return fail(PIC_EINVAL, "bad batch step arguments");
   for (pic_ctx *h : b->m)
     if (h->sticky) return fail(h->sticky, "a batch member holds a device error");
+  if (!b->tuned && batch_uniform(b)) {
+    const int rt = batch_tune(b, n_steps);
+    if (rt) return rt;
+  }
   while (n_steps > 0) {
     if (n_steps < b->period) {
       // tail: members step one by one on their streams, ordered after the batch stream
@@ -975,16 +1263,24 @@ int pic_batch_step(pic_batch b, int n_steps) {
       const int rc = batch_capture(b);
       if (rc) return rc;
     } else {
-      if (const int rj = join_members_into_batch(b)) return rj;
-      PIC_CUDA(cudaGraphLaunch(b->exec, b->stream));
-      if (const int rj = join_batch_into_members(b)) return rj;
-      for (size_t q = 0; q < b->m.size(); ++q) {
-        b->m[q]->step += b->period;
-        b->m[q]->launches += b->launches_per_period[q];
-        b->step_at_capture_end[q] = b->m[q]->step;
-      }
+      const int rc = batch_replay(b);
+      if (rc) return rc;
     }
     n_steps -= b->period;
+  }
+  return PIC_OK;
+}
+
+int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms, int *n,
+                     int *pick, int *batch_launches) {
+  if (!b || !n || !pick) return fail(PIC_EINVAL, "null pointer");
+  *n = (int)b->tune_ms.size();
+  *pick = b->tune_pick;
+  if (batch_launches) *batch_launches = b->multi ? 1 : 0;
+  for (int c = 0; c < *n && c < cap; ++c) {
+    if (chunk) chunk[c] = b->tune_chunk[c];
+    if (grid_mult) grid_mult[c] = b->tune_mult[c];
+    if (ms) ms[c] = b->tune_ms[c];
   }
   return PIC_OK;
 }
@@ -1003,6 +1299,7 @@ int pic_batch_destroy(pic_batch b) {
   if (!b) return PIC_OK;
   cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->tab) cudaFree(b->tab);
   for (auto &e : b->ev) cudaEventDestroy(e);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;

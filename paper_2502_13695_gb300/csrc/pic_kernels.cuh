@@ -52,6 +52,16 @@ struct Ctx {
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Block coordinates of a launch: blockIdx and gridDim for a simulation's own
+// launch, or, for a batch launch that covers many simulations, the block's
+// place (x, y) in one member's grid of gx x gy blocks.
+struct Blk {
+  int x, y, gx, gy;
+};
+__device__ __forceinline__ Blk blk_here() {
+  return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+}
+
 template <class R>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double part[32];
@@ -201,17 +211,19 @@ __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], con
 // flight per thread matter more than resident warps.
 template <class R> struct PushOcc { static constexpr int v = 2; };
 
+// Pushes the slots first + threadIdx.x + j stride below last (and below the
+// slots in use); returns how many live particles this thread pushed.
 template <class R>
-__global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
+__device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long first,
+                                             unsigned long long last, unsigned long long stride) {
   const Dev<R> &D = X.d;
-  const unsigned long long n = min(*D.nslots, D.cap);
+  const unsigned long long n = min(min(*D.nslots, D.cap), last);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
   const R dl_inv[3] = {D.idx, D.idy, D.idz};
   const R c2inv = R(1.0 / (kC * kC));
   double pushed = 0.0;
   const uint32_t jstamp = D.jtouch[D.nz + 1] + 1u;  // the next field pass
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  unsigned long long p = first + threadIdx.x;
   // each thread loads its next particle's state one iteration ahead, so that
   // round trip overlaps the current particle's gather and deposit
   int cell_n = -1;
@@ -328,8 +340,15 @@ __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
       D.pu[d][p] = u[d];
     }
   }
+  return pushed;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
+  const double pushed = push_items(X, blockIdx.x * (unsigned long long)blockDim.x, ~0ull,
+                                   (unsigned long long)gridDim.x * blockDim.x);
   const double tot = block_sum<R>(pushed);
-  if (threadIdx.x == 0 && tot != 0.0) atomicAdd(D.acc + 4, tot);
+  if (threadIdx.x == 0 && tot != 0.0) atomicAdd(X.d.acc + 4, tot);
 }
 
 // ---------------------------------------------------------------------------
@@ -437,17 +456,17 @@ __device__ __forceinline__ void b_out(const Dev<R> &D, int d, long long o, const
 }
 
 template <int V, int kMode, class R>
-__global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
+__device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
   // the E step of this pass has read the current: count the pass and clear
   // the host-write flag
-  if (kMode != kPrime && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (kMode != kPrime && bk.x == 0 && bk.y == 0 && threadIdx.x == 0) {
     D.jtouch[D.nz + 1] += 1u;
     D.jtouch[D.nz] = 0u;
   }
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const int r = (bk.x * blockDim.x + threadIdx.x) * V;
   if (r >= nxy) return;
-  const int k = blockIdx.y;
+  const int k = bk.y;
   const int j = r / nx, i = r - j * nx;
   const long long o = (long long)k * nxy + r;
   const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
@@ -480,6 +499,11 @@ __global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
                                (i + V == nx) ? oj + V - nx : oj + V, nxy, D.inv_e0sq);
     }
   }
+}
+
+template <int V, int kMode, class R>
+__global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
+  bstep_body<V, kMode>(D, blk_here());
 }
 
 template <class R>
@@ -536,11 +560,11 @@ __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) 
 // Joule work J.(E^n + E^{n+1})/2, J cleared for the next deposit.  Three
 // blocks per SM (80 registers) measured faster than two at 100 registers.
 template <int V, class R>
-__global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
+__device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
   const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-  const int k = blockIdx.y;
+  const int r = (bk.x * blockDim.x + threadIdx.x) * V;
+  const int k = bk.y;
   // the current is nonzero only on node planes within reach of a particle
   // deposited since the last field pass (cell planes k - 3 .. k + 2) or
   // after a host write
@@ -694,15 +718,20 @@ __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
   if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
 }
 
+template <int V, class R>
+__global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
+  efull_body<V>(X, blk_here());
+}
+
 // ---------------------------------------------------------------------------
 // Amplitude window + Keldysh threshold, one thread per material cell
 // ---------------------------------------------------------------------------
 template <int V, class R>
-__global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
+__device__ __forceinline__ void window_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-  const int mp = blockIdx.y;
+  const int r = (bk.x * blockDim.x + threadIdx.x) * V;
+  const int mp = bk.y;
   const long long m = (long long)mp * nxy + r;
   uint32_t miss = 0;  // cells whose threshold k_keldysh must recompute
   bool hot = false;   // a cell at or above the skip amplitude
@@ -789,7 +818,7 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
   }
   // stamp the plane for k_ionize, which skips planes without such cells
   if (__syncthreads_or(hot) && threadIdx.x == 0) D.hot[mp] = (uint32_t)*D.step + 1u;
-  if (threadIdx.x == 0 && blockIdx.x == 0 && mp == 0) D.hot[gridDim.y] = (uint32_t)*D.step + 1u;
+  if (threadIdx.x == 0 && bk.x == 0 && mp == 0) D.hot[bk.gy] = (uint32_t)*D.step + 1u;
   // warp-aggregated append of the misses to k_keldysh's work list
   const int cnt = __popc(miss);
   int incl = cnt;
@@ -806,18 +835,28 @@ __global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
   for (; miss; miss &= miss - 1) X.work[base++] = (int)(m + __ffs(miss) - 1);
 }
 
-// Keldysh thresholds of the queued cells, one thread per cell.
+template <int V, class R>
+__global__ void __launch_bounds__(256) k_window(Ctx<R> X) {
+  window_body<V>(X, blk_here());
+}
+
+// Keldysh thresholds of the queued cells, one thread per cell: queue
+// entries q = first + threadIdx.x + j stride below last.
 template <class R>
-__global__ void __launch_bounds__(256) k_keldysh(Ctx<R> X) {
+__device__ __forceinline__ void keldysh_items(const Ctx<R> &X, int first, int last, int stride) {
   const Dev<R> &D = X.d;
-  const int n = *X.work_n;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+  for (int q = first + threadIdx.x; q < last; q += stride) {
     const long long m = X.work[q];
     const int k = D.kplane[(int)(m / D.nxy)];
     const R amp = D.eamp[m];
     D.T[m] = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms);
     D.ckey[m] = amp;
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_keldysh(Ctx<R> X) {
+  keldysh_items(X, blockIdx.x * blockDim.x, *X.work_n, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -944,17 +983,17 @@ __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32
 // six blocks per SM (40 registers): the kernel waits on its loads, and 64
 // registers (four blocks) measured 22% slower.
 template <class R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 3) k_ionize(Ctx<R> X) {
+__device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;  // cell in material plane blockIdx.y
-  const int mp = blockIdx.y;
+  const int r = bk.x * blockDim.x + threadIdx.x;  // cell in material plane bk.y
+  const int mp = bk.y;
   {
     // only cells at or above the skip amplitude can have a nonzero
     // threshold; a neutral may sit in the plane above or below its birth
     // plane, so a plane is skipped when neither it nor those hold one
-    const uint32_t stamp = D.hot[gridDim.y];
+    const uint32_t stamp = D.hot[bk.gy];
     if (stamp != 0xFFFFFFFFu && D.hot[mp] != stamp && (mp == 0 || D.hot[mp - 1] != stamp) &&
-        (mp + 1 == (int)gridDim.y || D.hot[mp + 1] != stamp))
+        (mp + 1 == bk.gy || D.hot[mp + 1] != stamp))
       return;
   }
   const long long m = (long long)mp * D.nxy + r;
@@ -1082,6 +1121,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 3) k_ionize(Ctx<R> X
   atomicAdd(D.acc + 3, nd);
 }
 
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 3) k_ionize(Ctx<R> X) {
+  ionize_body(X, blk_here());
+}
+
 // First step index at which any neutral of a cell could have left it.
 template <class R>
 __global__ void k_init_material(Ctx<R> X) {
@@ -1149,11 +1193,11 @@ __global__ void k_init_material(Ctx<R> X) {
 constexpr int kFluxBlocks = 16;
 
 template <class R>
-__global__ void __launch_bounds__(256) k_flux_advance(Dev<R> D) {
-  const int q = blockIdx.y;
+__device__ __forceinline__ void flux_advance_body(const Dev<R> &D, Blk bk) {
+  const int q = bk.y;
   const long long base = (long long)D.flux_k[q] * D.nxy, basem = base - D.nxy;
   double f = 0.0, b = 0.0;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < D.nxy; r += gridDim.x * blockDim.x) {
+  for (int r = bk.x * blockDim.x + threadIdx.x; r < D.nxy; r += bk.gx * blockDim.x) {
     const double cby = kC * 0.5 * ((double)D.B[1][basem + r] + (double)D.B[1][base + r]);
     const double cbx = kC * 0.5 * ((double)D.B[0][basem + r] + (double)D.B[0][base + r]);
     const double ex = (double)D.E[0][base + r], ey = (double)D.E[1][base + r];
@@ -1167,18 +1211,18 @@ __global__ void __launch_bounds__(256) k_flux_advance(Dev<R> D) {
   const double bs = block_sum<R>(b);
   __shared__ int last;
   if (threadIdx.x == 0) {
-    double *p = D.flux_part + 2 * (q * gridDim.x + blockIdx.x);
+    double *p = D.flux_part + 2 * (q * bk.gx + bk.x);
     p[0] = fs;
     p[1] = bs;
     __threadfence();
-    last = atomicAdd(D.flux_cnt, 1u) == 2u * gridDim.x - 1u;
+    last = atomicAdd(D.flux_cnt, 1u) == 2u * (unsigned)bk.gx - 1u;
     if (last) {
       __threadfence();
       for (int qq = 0; qq < 2; ++qq) {
         double F = 0.0, B = 0.0;
-        for (unsigned x = 0; x < gridDim.x; ++x) {
-          F += __ldcg(D.flux_part + 2 * (qq * gridDim.x + x));
-          B += __ldcg(D.flux_part + 2 * (qq * gridDim.x + x) + 1);
+        for (int x = 0; x < bk.gx; ++x) {
+          F += __ldcg(D.flux_part + 2 * (qq * bk.gx + x));
+          B += __ldcg(D.flux_part + 2 * (qq * bk.gx + x) + 1);
         }
         D.acc[8 + 2 * qq] += F * D.flux_scale;
         D.acc[9 + 2 * qq] += B * D.flux_scale;
@@ -1187,6 +1231,11 @@ __global__ void __launch_bounds__(256) k_flux_advance(Dev<R> D) {
       *D.step += 1;
     }
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_flux_advance(Dev<R> D) {
+  flux_advance_body(D, blk_here());
 }
 
 // ---------------------------------------------------------------------------
@@ -1212,14 +1261,22 @@ __device__ __forceinline__ int sort_key(const Dev<R> &D, int c, unsigned long lo
   }
 }
 
+// Slots first + threadIdx.x + j stride below last (and below the slots in use).
 template <bool kByFrame, class R>
-__global__ void k_hist(Dev<R> D, unsigned int *cnt) {
-  const unsigned long long n = min(*D.nslots, D.cap);
-  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void hist_items(const Dev<R> &D, unsigned int *cnt,
+                                           unsigned long long first, unsigned long long last,
+                                           unsigned long long stride) {
+  const unsigned long long n = min(min(*D.nslots, D.cap), last);
+  for (unsigned long long p = first + threadIdx.x; p < n; p += stride) {
     const int c = D.pcell[p];
     if (c >= 0) atomicAdd(cnt + sort_key<kByFrame>(D, c, p), 1u);
   }
+}
+
+template <bool kByFrame, class R>
+__global__ void k_hist(Dev<R> D, unsigned int *cnt) {
+  hist_items<kByFrame>(D, cnt, blockIdx.x * (unsigned long long)blockDim.x, ~0ull,
+                       (unsigned long long)gridDim.x * blockDim.x);
 }
 
 constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * kScanItems;
@@ -1254,9 +1311,9 @@ __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned
   return excl;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const unsigned int *cnt, long long n,
-                                                               unsigned int *bsum) {
-  const long long base = (long long)blockIdx.x * kScanChunk;
+__device__ __forceinline__ void scan_reduce_body(const unsigned int *cnt, long long n,
+                                                 unsigned int *bsum, int bx) {
+  const long long base = (long long)bx * kScanChunk;
   unsigned int s = 0;
   for (int q = 0; q < kScanItems; ++q) {
     const long long idx = base + (long long)q * kScanThreads + threadIdx.x;
@@ -1264,7 +1321,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const unsigned int
   }
   unsigned int tot;
   block_excl_scan(s, tot);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  if (threadIdx.x == 0) bsum[bx] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const unsigned int *cnt, long long n,
+                                                               unsigned int *bsum) {
+  scan_reduce_body(cnt, n, bsum, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(unsigned int *bsum, int nb,
@@ -1284,9 +1346,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(unsigned int *bsum
 // Each thread scans kScanItems consecutive counts, moved as 16-byte vectors
 // (the arena is 256-byte aligned, so a thread's run starts on a 64-byte
 // boundary); a ragged last run goes element by element.
-__global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, long long n,
-                                                              const unsigned int *bsum) {
-  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+__device__ __forceinline__ void scan_final_body(unsigned int *cnt, long long n,
+                                                const unsigned int *bsum, int bx) {
+  const long long base = (long long)bx * kScanChunk + (long long)threadIdx.x * kScanItems;
   const bool full = base + kScanItems <= n;
   unsigned int v[kScanItems];
   if (full) {
@@ -1307,7 +1369,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, 
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) s += v[q];
   unsigned int tot;
-  unsigned int ex = block_excl_scan(s, tot) + bsum[blockIdx.x];
+  unsigned int ex = block_excl_scan(s, tot) + bsum[bx];
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     const unsigned int e = ex;
@@ -1326,12 +1388,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, 
   }
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(unsigned int *cnt, long long n,
+                                                              const unsigned int *bsum) {
+  scan_final_body(cnt, n, bsum, blockIdx.x);
+}
+
+// Slots first + threadIdx.x + j stride below last (and below the slots in use).
 template <bool kByFrame, class R>
-__global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor) {
+__device__ __forceinline__ void scatter_items(const Ctx<R> &X, unsigned int *cursor,
+                                              unsigned long long first, unsigned long long last,
+                                              unsigned long long stride) {
   const Dev<R> &D = X.d;
-  const unsigned long long n = min(*D.nslots, D.cap);
-  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
+  const unsigned long long n = min(min(*D.nslots, D.cap), last);
+  for (unsigned long long p = first + threadIdx.x; p < n; p += stride) {
     const int c = D.pcell[p];
     if (c < 0) continue;
     const unsigned int q = atomicAdd(cursor + sort_key<kByFrame>(D, c, p), 1u);
@@ -1344,6 +1413,12 @@ __global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor)
     X.atag[q] = D.ptag[p];
     X.aid[q] = D.pid[p];
   }
+}
+
+template <bool kByFrame, class R>
+__global__ void __launch_bounds__(256) k_scatter(Ctx<R> X, unsigned int *cursor) {
+  scatter_items<kByFrame>(X, cursor, blockIdx.x * (unsigned long long)blockDim.x, ~0ull,
+                          (unsigned long long)gridDim.x * blockDim.x);
 }
 
 __global__ void k_set_slots(unsigned long long *nslots, const unsigned long long *total) {

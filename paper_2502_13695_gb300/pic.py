@@ -30,6 +30,7 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
            "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
+           "pic_batch_tuning",
            "pic_damage", "pic_get_intensity_max", "pic_save", "pic_load",
            "pic_checkpoint_config", "pic_serve_create", "pic_serve_submit",
            "pic_serve_poll", "pic_serve_destroy"]
@@ -149,6 +150,7 @@ def lib():
         L.pic_batch_step.argtypes = [vp, i]
         L.pic_batch_sync.argtypes = [vp]
         L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_tuning.argtypes = [vp, i, vp, vp, vp, P(i), P(i), P(i)]
         L.pic_profile_read.argtypes = [vp, vp, vp]
         L.pic_save.argtypes = [vp, ctypes.c_char_p]
         L.pic_load.argtypes = [ctypes.c_char_p, vp, vp, ctypes.c_size_t, P(vp)]
@@ -449,6 +451,19 @@ class Batch:
 
     def sync(self):
         _check(lib().pic_batch_sync(self._h))
+
+    def tuning(self) -> dict:
+        """How the batch steps (pic_batch_tuning): batch launches or not, and
+        the push launch shapes the tuner measured and the one it kept."""
+        cap = 16
+        chunk, mult, ms = np.zeros(cap, np.int64), np.zeros(cap, np.int32), np.zeros(cap)
+        n, pick, bl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().pic_batch_tuning(self._h, cap, _ptr(chunk), _ptr(mult), _ptr(ms),
+                                      ctypes.byref(n), ctypes.byref(pick), ctypes.byref(bl)))
+        k = n.value
+        return dict(batch_launches=bool(bl.value), pick=pick.value,
+                    candidates=[dict(chunk=int(chunk[q]), grid_mult=int(mult[q]), ms=float(ms[q]))
+                                for q in range(k)])
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -49,3 +49,78 @@ def test_batch_of_uneven_instances_matches_oracle(oracle_mod):
     assert sims[1].scalars()["step"] == 136
     assert rel_l2(sims[1].fields()[0:3], o.fields()[0:3]) <= 1e-12
     batch.close()
+
+
+def test_fp32_batch_launches_match_members_alone():
+    """FP32 members with four x points per thread in the field kernels, one
+    of them without material (no window or ionisation blocks): the batch's
+    one-launch-per-phase steps give each member what it gives alone (FP32
+    deposits sum in a varying order, so the bound is FP32's), and the
+    launches per step do not grow with the number of members."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2502_13695_gb300 import build, pic
+    build.build()
+    cfgs = [wl.small_slab(nx=8, ny=8, nz=32, z0=10, z1=22, precision="fp32", seed=61),
+            wl.small_slab(nx=12, ny=8, nz=48, z0=14, z1=36, precision="fp32", seed=62,
+                          fluence=2.0),
+            wl.vacuum_box(nx=8, ny=4, nz=40, precision="fp32"),
+            wl.small_slab(nx=4, ny=8, nz=24, z0=8, z1=16, precision="fp32", seed=63,
+                          static=True)]
+    sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
+    batch = pic.Batch(sims)
+    l0 = sum(s.info()["launches"] for s in sims)
+    batch.step(96)
+    batch.sync()
+    per_step = (sum(s.info()["launches"] for s in sims) - l0) / 96
+    assert per_step < 12, per_step  # 8 a step plus 7 every 16 steps
+    for c, g in zip(cfgs, sims):
+        a = pic.Simulation(c)
+        a.step(96)
+        a.sync()
+        assert g.scalars()["step"] == 96
+        Fg, Fa = g.fields(), a.fields()
+        for sl in (slice(0, 3), slice(3, 6), slice(9, 12)):
+            if np.abs(Fa[sl]).max() > 0:
+                assert rel_l2(Fg[sl], Fa[sl]) <= 1e-4, (c["name"], sl)
+        dg, da = g.diagnostics(), a.diagnostics()
+        assert dg["N_pairs"] == pytest.approx(da["N_pairs"], rel=1e-2)
+        assert dg["U_fwd_front"] == pytest.approx(da["U_fwd_front"], rel=1e-4)
+        a.close()
+    assert sims[1].diagnostics()["N_pairs"] > 0
+    batch.close()
+
+
+def test_batch_tunes_its_push_shape_on_itself():
+    """A step request of eight periods or more tunes the push launch shape:
+    four candidates, each timed over a real period, the fastest kept; the
+    members still step exactly as many steps and match their runs alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2502_13695_gb300 import build, pic
+    build.build()
+    cfgs = [wl.small_slab(nx=8, ny=8, nz=32, z0=10, z1=22, precision="fp64", seed=71),
+            wl.small_slab(nx=8, ny=12, nz=40, z0=12, z1=30, precision="fp64", seed=72,
+                          fluence=2.0)]
+    sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
+    batch = pic.Batch(sims)
+    assert batch.tuning()["candidates"] == []
+    batch.step(8 * 32 + 10)
+    batch.sync()
+    tu = batch.tuning()
+    assert tu["batch_launches"]
+    assert len(tu["candidates"]) == 4 and 0 <= tu["pick"] < 4
+    assert all(c["ms"] > 0 for c in tu["candidates"])
+    assert tu["candidates"][tu["pick"]]["ms"] == min(c["ms"] for c in tu["candidates"])
+    for c, g in zip(cfgs, sims):
+        assert g.scalars()["step"] == 8 * 32 + 10
+        a = pic.Simulation(c)
+        a.step(8 * 32 + 10)
+        Fg, Fa = g.fields(), a.fields()
+        for sl in (slice(0, 3), slice(3, 6), slice(9, 12)):
+            assert rel_l2(Fg[sl], Fa[sl]) <= 1e-12
+        assert np.array_equal(g.material()["alive"], a.material()["alive"])
+        a.close()
+    batch.close()
