@@ -1,7 +1,9 @@
-"""One rank of the two-rank z decomposition test (run as a subprocess by
-tests/test_decomp.py with the torchrun environment variables set): the slab
-of the shared test state advanced by an FP64 oracle engine, exchanging over
-gloo; writes its owned fields and particles to <out>/rank<r>.npz."""
+"""One rank of the z decomposition tests (run as a subprocess by
+tests/test_decomp.py and tests/test_gpu_decomp.py with the torchrun
+environment variables set): the slab of the shared test state advanced by
+an FP64 engine, the oracle or (third argument "gpu") the CUDA library on
+cuda:0, exchanging over gloo; writes its owned fields and particles to
+<out>/rank<r>.npz."""
 import os
 import sys
 
@@ -20,10 +22,18 @@ from paper_2502_13695_gb300 import decomp  # noqa: E402
 
 def main():
     out, steps = sys.argv[1], int(sys.argv[2])
+    engine = sys.argv[3] if len(sys.argv) > 3 else "oracle"
     rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
     dist.init_process_group("gloo")
     cfg, F, P = case()
-    slab = decomp.ZSlab(cfg, rank, world, oracle.Sim, dist)
+    if engine == "gpu":
+        import torch
+        from paper_2502_13695_gb300 import pic
+        torch.cuda.set_device(0)
+        make = pic.Simulation
+    else:
+        make = oracle.Sim
+    slab = decomp.ZSlab(cfg, rank, world, make, dist)
     slab.set_state(F, P)
     slab.step(steps)
     k0, Fo = slab.owned_fields()

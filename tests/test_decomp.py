@@ -31,16 +31,15 @@ def test_slab_bounds():
         decomp.slab_bounds(10, 2)
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_ranks_match_one_domain(oracle_mod, tmp_path, world):
-    from decomp_case import case
-    from paper_2502_13695_gb300 import decomp
+def run_ranks(tmp_path, world, engine="oracle"):
+    """Run the decomposition worker on `world` gloo ranks; returns nothing,
+    the ranks write their results under tmp_path."""
     port = _free_port()
     procs = []
     for r in range(world):
         env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(world),
                    MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
-        procs.append(subprocess.Popen([sys.executable, WORKER, str(tmp_path), str(STEPS)],
+        procs.append(subprocess.Popen([sys.executable, WORKER, str(tmp_path), str(STEPS), engine],
                                       env=env, text=True, stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE))
     try:
@@ -51,6 +50,13 @@ def test_ranks_match_one_domain(oracle_mod, tmp_path, world):
                 p.kill()
     for p, (o, e) in zip(procs, outs):
         assert p.returncode == 0, e[-3000:]
+
+
+def check_against_one_domain(oracle_mod, tmp_path, world):
+    """The ranks' owned planes and particles against the single-domain oracle
+    run of the same state."""
+    from decomp_case import case
+    from paper_2502_13695_gb300 import decomp
     cfg, F, P = case()
     s = oracle_mod.Sim(cfg)
     s.set_fields(F)
@@ -98,3 +104,9 @@ def test_ranks_match_one_domain(oracle_mod, tmp_path, world):
     assert crossed > 20
     for face in b[1:-1]:
         assert np.max(np.abs(G[9, face - 2:face + 2])) > 0
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_match_one_domain(oracle_mod, tmp_path, world):
+    run_ranks(tmp_path, world)
+    check_against_one_domain(oracle_mod, tmp_path, world)
