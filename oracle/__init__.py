@@ -12,6 +12,9 @@ Parity status of each function (pins are in ``tests/test_oracle_*.py``):
   dawson          pinned: scipy.special.dawsn, series limits, maximum
   keldysh_W       pinned: multiphoton (gamma >> 1) and tunnelling (gamma << 1)
                   closed forms derived from Sec. 2.1
+  elliptic tables pinned: scipy ellipk / ellipe at the nodes, the linear
+                  interpolation bound between them, the in-situ values
+                  past the last node, the rate within 1e-5 of in situ
   boris           pinned: exact gyration angle, |u| conservation, pure-E
                   kick, E x B drift
   particle pass   pinned: discrete continuity to roundoff, TSC partition of
@@ -94,7 +97,7 @@ class Config(ctypes.Structure):
                 ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("keldysh_terms", ctypes.c_int), ("n_layers", ctypes.c_int),
                 ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int),
-                ("shape", ctypes.c_int), ("pad_shape", ctypes.c_int), ("w0", ctypes.c_double),
+                ("shape", ctypes.c_int), ("elliptic_table", ctypes.c_int), ("w0", ctypes.c_double),
                 ("layers", Layer * MAX_LAYERS)]
 
 
@@ -166,6 +169,9 @@ def lib(openmp: bool = False):
             L.or_boris.argtypes = [d, d, vp, vp, vp]
             L.or_threads.restype = i
             L.or_threads.argtypes = []
+            L.or_sim_ellip.argtypes = [vp, d, _P(d), _P(d)]
+            L.or_keldysh_W_table.restype = d
+            L.or_keldysh_W_table.argtypes = [d, d, d, d, i, vp, vp, i]
             if openmp:
                 _lib_omp = L
             else:
@@ -273,6 +279,7 @@ def make_config(cfg: dict) -> Config:
     c.coll_every = cfg.get("coll_every", 0)
     c.shape = 1 if p.get("shape", "gauss") == "sin2" else 0
     c.w0 = float(p.get("w0", 0.0))
+    c.elliptic_table = int(cfg.get("elliptic_table", 0))
     layers = cfg["layers"]
     c.n_layers = len(layers)
     for n, ly in enumerate(layers):
@@ -436,6 +443,13 @@ class Sim:
         a = np.zeros(1, dtype=np.int32)
         self._L.or_cell_threshold(self._h, int(layer), float(E), _ptr(T), _ptr(a))
         return (1 << 64) - 1 if a[0] else int(T[0])
+
+    def ellip(self, m: float):
+        """(K(m), E(m)) as this simulation's rate uses them: from its
+        elliptic tables when it has them, else in situ."""
+        K, KmE = ctypes.c_double(), ctypes.c_double()
+        self._L.or_sim_ellip(self._h, float(m), ctypes.byref(K), ctypes.byref(KmE))
+        return K.value, K.value - KmE.value
 
     def spot(self, x: float, y: float) -> float:
         return self._L.or_spot(self._h, float(x), float(y))

@@ -90,7 +90,7 @@ typedef struct {
   int imax_every; /* intensity record interval in steps: 0 = 0.5 fs, < 0 off */
   int coll_every; /* steps between binary-collision passes, 0 = none */
   int shape;      /* temporal envelope: 0 Gaussian, 1 sine-squared (Sec. 3) */
-  int pad_shape;
+  int elliptic_table; /* 0: K and E in situ; N >= 2: read from N-point tables */
   double w0;      /* Gaussian spot radius (1/e^2 of the intensity), 0 = plane wave */
   or_layer layers[OR_MAX_LAYERS];
 } or_config;
@@ -238,8 +238,47 @@ double or_dawson(double z) {
 /* ------------------------------------------------------------------------ */
 /* Keldysh rate W (returned) and, when parts is not NULL, its pieces:
  * parts[0] = gamma, [1] = x, [2] = floor(x + 1), [3] = Q(gamma, x). */
+/* The paper reads K and E from tabulated data files of 1000 points (Sec.
+ * 2.1); their range, spacing and interpolation are not given.  Reading:
+ * tabK[i] = K(i / N), tabE[i] = E(i / N) for i = 0 .. N - 1 (N = 1000 in the
+ * paper), linear interpolation in m between the two neighbouring entries,
+ * and, past the last entry (m > 1 - 1/N, where K diverges logarithmically
+ * and no finite table reaches), the in-situ value.  Returns K and K - E as
+ * or_ellip_KE does. */
+void or_ellip_table(const double *tabK, const double *tabE, int N, double m, double mc,
+                    double *K, double *KmE) {
+  double u = m * (double)N;
+  double fi = floor(u);
+  if (tabK && N >= 2 && fi >= 0.0 && fi < (double)(N - 1)) {
+    int i = (int)fi;
+    double f = u - fi;
+    double k = tabK[i] + f * (tabK[i + 1] - tabK[i]);
+    double e = tabE[i] + f * (tabE[i + 1] - tabE[i]);
+    *K = k;
+    *KmE = k - e;
+    return;
+  }
+  or_ellip_KE(m, mc, K, KmE);
+}
+
+static double keldysh_rate(double E, double omega, double gap_J, double mstar_kg, int nterms,
+                           int *terms_used, double parts[4], const double *tabK,
+                           const double *tabE, int ntab);
+
 double or_keldysh_parts(double E, double omega, double gap_J, double mstar_kg,
                         int nterms, int *terms_used, double parts[4]) {
+  return keldysh_rate(E, omega, gap_J, mstar_kg, nterms, terms_used, parts, NULL, NULL, 0);
+}
+
+/* The rate with K and E from N-point tables (or_ellip_table). */
+double or_keldysh_W_table(double E, double omega, double gap_J, double mstar_kg, int nterms,
+                          const double *tabK, const double *tabE, int ntab) {
+  return keldysh_rate(E, omega, gap_J, mstar_kg, nterms, NULL, NULL, tabK, tabE, ntab);
+}
+
+static double keldysh_rate(double E, double omega, double gap_J, double mstar_kg, int nterms,
+                           int *terms_used, double parts[4], const double *tabK,
+                           const double *tabE, int ntab) {
   if (terms_used) *terms_used = 0;
   if (parts) parts[0] = parts[1] = parts[2] = parts[3] = 0.0;
   if (!(E > 0.0)) return 0.0;
@@ -249,8 +288,8 @@ double or_keldysh_parts(double E, double omega, double gap_J, double mstar_kg,
   if (!(g2 < 1e300)) return 0.0;
   double gam1 = g2 / (1.0 + g2), gam2 = 1.0 / (1.0 + g2);
   double K1, KmE1, K2, KmE2;
-  or_ellip_KE(gam1, gam2, &K1, &KmE1);
-  or_ellip_KE(gam2, gam1, &K2, &KmE2);
+  or_ellip_table(tabK, tabE, ntab, gam1, gam2, &K1, &KmE1);
+  or_ellip_table(tabK, tabE, ntab, gam2, gam1, &K2, &KmE2);
   double E2 = K2 - KmE2;
   double x = (2.0 / OR_PI) * (gap_J / (OR_HBAR * omega)) * E2 / sqrt(gam1);
   double N = floor(x + 1.0);
@@ -384,6 +423,9 @@ typedef struct {
    * the +z (fwd) and -z (bwd) wave power through them */
   int flux_plane[2];
   double U_fwd[2], U_bwd[2];
+  /* elliptic tables (elliptic_table > 0): K(i / N), E(i / N) */
+  double *tabK, *tabE;
+  int ntab;
 } or_sim;
 
 static long fidx(const or_sim *s, int i, int j, int k) {
@@ -517,6 +559,17 @@ or_sim *or_create(const or_config *cfg) {
   s->Talways = calloc(s->nmat ? s->nmat : 1, 1);
   s->alive = calloc(s->nmat ? s->nmat : 1, sizeof(uint32_t));
   s->imax = calloc((size_t)s->nxy * nz, sizeof(double));
+  if (cfg->elliptic_table >= 2) {
+    s->ntab = cfg->elliptic_table;
+    s->tabK = malloc((size_t)s->ntab * sizeof(double));
+    s->tabE = malloc((size_t)s->ntab * sizeof(double));
+    for (int i = 0; i < s->ntab; i++) {
+      double m = (double)i / (double)s->ntab, K, KmE;
+      or_ellip_KE(m, 1.0 - m, &K, &KmE);
+      s->tabK[i] = K;
+      s->tabE[i] = K - KmE;
+    }
+  }
   /* the paper records the intensity every 0.5 fs (Sec. 5, Plasma Screening) */
   s->imax_every = cfg->imax_every > 0
                       ? cfg->imax_every
@@ -535,6 +588,8 @@ or_sim *or_create(const or_config *cfg) {
 
 void or_destroy(or_sim *s) {
   if (!s) return;
+  free(s->tabK);
+  free(s->tabE);
   free(s->imax);
   for (int c = 0; c < NCOMP; c++) free(s->F[c]);
   free(s->layer_of_plane);
@@ -854,8 +909,8 @@ void or_window_keldysh_pass(or_sim *s) {
           if (v > mx) mx = v;
         }
         s->eamp[m] = mx;
-        double W = or_keldysh_W(mx, s->omega, s->gapJ[L], s->mstar[L],
-                                s->cfg.keldysh_terms, NULL);
+        double W = keldysh_rate(mx, s->omega, s->gapJ[L], s->mstar[L],
+                                s->cfg.keldysh_terms, NULL, NULL, s->tabK, s->tabE, s->ntab);
         ion_threshold(W, ly->n_mol, s->dt, &s->T[m], &s->Talways[m]);
       }
   }
@@ -1577,6 +1632,11 @@ void or_set_flux(or_sim *s, const double in[4]) {
   s->U_bwd[1] = in[3];
 }
 
+/* K and K - E of a simulation as its rate sees them (its tables or in situ). */
+void or_sim_ellip(const or_sim *s, double m, double *K, double *KmE) {
+  or_ellip_table(s->tabK, s->tabE, s->ntab, m, 1.0 - m, K, KmE);
+}
+
 /* Threads the parallel loops use: 1 in the serial build. */
 int or_threads(void) {
 #ifdef _OPENMP
@@ -1594,7 +1654,8 @@ double or_incident(const or_sim *s, double t) { return e_inc(s, t); }
  * item-by-item checks of a larger run's thresholds). */
 void or_cell_threshold(const or_sim *s, int L, double E, uint64_t *T, int *always) {
   uint8_t a = 0;
-  double W = or_keldysh_W(E, s->omega, s->gapJ[L], s->mstar[L], s->cfg.keldysh_terms, NULL);
+  double W = keldysh_rate(E, s->omega, s->gapJ[L], s->mstar[L], s->cfg.keldysh_terms, NULL, NULL,
+                          s->tabK, s->tabE, s->ntab);
   ion_threshold(W, s->cfg.layers[L].n_mol, s->dt, T, &a);
   *always = a;
 }

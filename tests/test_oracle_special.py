@@ -228,3 +228,56 @@ def test_ponderomotive_energy_matches_paper(oracle_mod):
         Up = np.mean(ek)
         assert Up == pytest.approx(QE ** 2 * E0 ** 2 / (4 * m * OMEGA ** 2) / QE, rel=2e-3)
         assert Up == pytest.approx(paper_eV, rel=0.01)
+
+
+def test_elliptic_tables_nodes_interpolation_and_tail(oracle_mod):
+    """The paper's 1000-point tables (reading: K(i/N), E(i/N) for
+    i < N, linear in m between neighbours, in situ past the last entry):
+    node values are scipy's, values between nodes are exactly the linear
+    interpolation of scipy's node values and within the interpolation bound
+    h^2/8 max|f''| of the true function, and past the last node the value is
+    the in-situ one."""
+    from scipy.special import ellipe, ellipk
+    from paper_2502_13695_gb300 import workloads as wl
+    N = 1000
+    s = oracle_mod.Sim(dict(wl.small_slab(), elliptic_table=N))
+    for i in (0, 1, 17, 500, 998, 999):
+        K, E = s.ellip(i / N)
+        assert K == pytest.approx(ellipk(i / N), rel=2e-15)
+        assert E == pytest.approx(ellipe(i / N), rel=2e-15)
+    rng = np.random.default_rng(3)
+    for m in np.concatenate([rng.uniform(0.0, 0.999, 200), [0.5005, 0.9985]]):
+        i = int(np.floor(m * N))
+        f = m * N - i
+        K, E = s.ellip(m)
+        Kl = ellipk(i / N) + f * (ellipk((i + 1) / N) - ellipk(i / N))
+        El = ellipe(i / N) + f * (ellipe((i + 1) / N) - ellipe(i / N))
+        assert K == pytest.approx(Kl, rel=1e-13) and E == pytest.approx(El, rel=1e-13)
+        if m < 0.99:  # near m = 1 the log singularity of K needs finer sampling
+            h = 1.0 / N
+            xs = np.linspace(i / N, (i + 1) / N, 11)
+            d2K = np.max(np.abs(ellipk(xs + h / 10) - 2 * ellipk(xs) + ellipk(xs - h / 10)))
+            d2K /= (h / 10) ** 2
+            assert abs(K - ellipk(m)) <= 1.5 * h * h / 8 * d2K + 1e-15
+    for m in (0.9991, 0.99999, 1 - 1e-12):
+        K, E = s.ellip(m)
+        assert K == pytest.approx(ellipk(m), rel=1e-13) and E == pytest.approx(ellipe(m), rel=1e-13)
+
+
+def test_elliptic_tables_move_the_rate_little(oracle_mod):
+    """With 1000-point tables the ionisation thresholds of silica stay
+    within 3e-5 of the in-situ ones over the fields the workloads reach
+    (Keldysh gamma 0.3 to 2; the exponent of W amplifies the tables' 1e-6
+    in K), and differ from them (the tables are used)."""
+    from paper_2502_13695_gb300 import workloads as wl
+    cfg = wl.small_slab()
+    a = oracle_mod.Sim(cfg)
+    b = oracle_mod.Sim(dict(cfg, elliptic_table=1000))
+    diffs = []
+    for E in np.geomspace(1.5e10, 8e10, 40):
+        Ta, Tb = a.threshold(0, E), b.threshold(0, E)
+        if 0 < Ta < (1 << 64) - 1:
+            diffs.append(abs(Tb / Ta - 1))
+    assert len(diffs) > 20
+    assert max(diffs) < 3e-5
+    assert max(diffs) > 1e-7
