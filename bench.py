@@ -310,7 +310,8 @@ ALG_BYTES = {  # FP32 algorithmic bytes per unit of work of each kernel class
 # what bounds each kernel class in practice, as measured (ncu counters and
 # timing experiments), where it is not DRAM bandwidth
 LIMITER = {
-    "push": "issue rate of the deposit's ~26 global vector reductions per particle",
+    "push": "L1 sector throughput of the gather loads and current reductions "
+            "(~39 + 21 sectors per particle, L1 ~72% busy)",
     "keldysh": "FP32 issue (series of Dawson terms)",
     "ionize": "load latency and integer issue (Philox draws)",
     "collide": "issue rate and lane divergence of the per-pair arithmetic",

@@ -90,6 +90,12 @@ typedef struct {
                           records every 0.5 fs): 0 = round(0.5 fs / dt), < 0 off */
   int coll_every;      /* steps between binary-collision passes among electrons
                           and holes (Sec. 2.2), each over coll_every * dt; 0 = none */
+  int elliptic_table;  /* complete elliptic integrals of the Keldysh rate: 0 in
+                          situ (arithmetic-geometric mean); N >= 2 from N-point
+                          tables as the paper reads them (Sec. 2.1: 1000
+                          points): K(i/N), E(i/N), i < N, linear in the
+                          parameter between entries, in situ past the last */
+  int reserved_grid;
 } pic_grid;
 
 /* One dielectric layer: z cells [z0, z1) over the whole transverse plane.
@@ -380,19 +386,21 @@ int pic_batch_destroy(pic_batch b);
  * launches: fixed grids laid end to end over the members, particle and
  * Keldysh loops in chunks handed out from a counter); otherwise it holds
  * every member's own launches, each on its stream.  With batch launches the
- * first pic_batch_step that asks for at least 8 periods tunes the push's
+ * first pic_batch_step that asks for at least 4 periods tunes the push's
  * launch shape on the batch itself: four candidates (particles per block
- * task, grid as 1 or 2 times the resident blocks), each captured and run for
- * one period and timed over a second, the fastest kept (every tuning period
- * is a real step of every member).
+ * task, grid as 1 or 2 times the resident blocks), each captured with CUDA
+ * events around its push launches and run for one period; the one with the
+ * least push time per particle push is kept (every tuning period is a real
+ * step of every member).
  *   cap            : entries the arrays hold
- *   chunk, grid_mult, ms : per candidate (any may be NULL); ms is the timed
- *                    period in milliseconds
+ *   chunk, grid_mult, ms, ns_per_push : per candidate (any may be NULL): the
+ *                    shape, its push time over the period [ms] and per
+ *                    particle push [ns]
  *   n, pick        : candidates tuned (0: not yet) and the index kept (-1)
  *   batch_launches : 1 when the batch steps with batch launches
  * The paper has no counterpart (its runs are single jobs). */
-int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms, int *n,
-                     int *pick, int *batch_launches);
+int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms,
+                     double *ns_per_push, int *n, int *pick, int *batch_launches);
 
 /* ---- serving: continuous batching of submitted simulations ---------------
  * The paper runs one simulation per job; this is the request loop of a

@@ -66,6 +66,8 @@ struct Plan {
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t off_flux_part, off_flux_cnt;
+  size_t off_ktab;               // elliptic tables (elliptic_table > 0)
+  std::vector<double> ktab;      // the same tables on the host, K and E interleaved
   int flux_plane[2];  // node planes of the Poynting split (front, back)
   size_t total;
 };
@@ -83,6 +85,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   if (!(g.pool_factor >= 0)) return fail(PIC_EINVAL, "pool_factor must be >= 0");
   if (g.keldysh_terms < 0 || g.sort_interval < 0 || g.coll_every < 0)
     return fail(PIC_EINVAL, "negative count");
+  if (g.elliptic_table != 0 && (g.elliptic_table < 2 || g.elliptic_table > 1000000))
+    return fail(PIC_EINVAL, "elliptic_table must be 0 or 2 .. 1000000 points");
   if (mat->n_layers < 0 || mat->n_layers > PIC_MAX_LAYERS || (mat->n_layers && !mat->layers))
     return fail(PIC_EINVAL, "bad layer count");
   if (!(pulse->lambda > 0 && pulse->fwhm > 0 && pulse->fluence >= 0) ||
@@ -218,6 +222,15 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_step = take(8);
   P.off_acc = take(16 * 8);
   P.off_flux_part = take(2 * kFluxBlocks * 2 * 8);
+  P.off_ktab = take((size_t)2 * std::max(g.elliptic_table, 1) * R);
+  P.ktab.clear();
+  for (int i = 0; i < g.elliptic_table; ++i) {
+    const double m = (double)i / (double)g.elliptic_table;
+    double K, KmE;
+    ellip_k_kme<double>(m, 1.0 - m, K, KmE);
+    P.ktab.push_back(K);
+    P.ktab.push_back(K - KmE);
+  }
   P.off_flux_cnt = take(16);
   P.off_err = take(16);
   P.off_ne = take(P.nfield * 8);
@@ -265,7 +278,9 @@ std::vector<LayerK> layer_constants(const Plan &P) {
     double e = 1e3, last_ok = 0.0;
     k.e_skip = 0.0;
     for (int it = 0; it < 4000; ++it, e *= 1.01) {
-      const double p = keldysh_probability<double>(e, k, P.g.keldysh_terms);
+      const double p = keldysh_probability<double>(e, k, P.g.keldysh_terms, nullptr,
+                                                   P.ktab.empty() ? nullptr : P.ktab.data(),
+                                                   P.g.elliptic_table);
       if (p * 18446744073709551616.0 >= 1.0 / 16.0) break;
       last_ok = e;
     }
@@ -447,6 +462,8 @@ void bind(pic_ctx *h) {
   D.imax_every = P.imax_every;
   D.inv_e0sq = R(P.E0 > 0.0 ? 1.0 / (P.E0 * P.E0) : 1.0);
   D.acc = (double *)(A + P.off_acc);
+  D.ktab = P.ktab.empty() ? nullptr : (const R *)(A + P.off_ktab);
+  D.ntab = P.g.elliptic_table;
   D.flux_k[0] = P.flux_plane[0];
   D.flux_k[1] = P.flux_plane[1];
   D.flux_scale = kC * kEps0 * P.g.dx * P.g.dy * P.dt;
@@ -689,6 +706,13 @@ int init_state(pic_ctx *h) {
     h->h2d_bytes += (long long)(h->lk.size() * sizeof(LayerK) + lr.size() * sizeof(LayerR<R>));
     PIC_CUDA(cudaStreamSynchronize(s));  // lr is a host temporary
   }
+  if (!P.ktab.empty()) {
+    std::vector<R> kt(P.ktab.begin(), P.ktab.end());
+    PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_ktab, kt.data(), kt.size() * sizeof(R),
+                             cudaMemcpyHostToDevice, s));
+    h->h2d_bytes += (long long)(kt.size() * sizeof(R));
+    PIC_CUDA(cudaStreamSynchronize(s));  // kt is a host temporary
+  }
   if (P.nmat > 0) k_init_material<R><<<grid_blocks(P.nmat), kThreads, 0, s>>>(ctx_of<R>(h));
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaStreamSynchronize(s));
@@ -838,8 +862,12 @@ struct pic_batch_ctx {
   bool tuned = false;
   std::vector<long long> tune_chunk;
   std::vector<int> tune_mult;
-  std::vector<double> tune_ms;
+  std::vector<double> tune_ms;     // push time over the tuning period
+  std::vector<double> tune_cost;   // push time per particle push [ns]
   int tune_pick = -1;
+  // while tuning, event pairs around every push of the captured period
+  bool time_push = false;
+  std::vector<cudaEvent_t> tev;
   // byte offsets in tab
   size_t o_ctx[2] = {0, 0}, o_sort[2] = {0, 0}, o_cnt = 0;
   struct Flat {
@@ -975,7 +1003,7 @@ int batch_tables(pic_batch_ctx *b) {
 // One full step of every member as batch launches on the batch stream; the
 // members' host state advances as enqueue would advance it.
 template <class R>
-int enqueue_batch(pic_batch_ctx *b) {
+int enqueue_batch(pic_batch_ctx *b, int st) {
   cudaStream_t s = b->stream;
   const int n = (int)b->m.size();
   const Ctx<R> *cx = (const Ctx<R> *)(b->tab + b->o_ctx[b->parity]);
@@ -983,8 +1011,12 @@ int enqueue_batch(pic_batch_ctx *b) {
   const int V = b->m[0]->field_v;
   long long launched = 0;
   k_batch_prep<R><<<grid_blocks(std::max(n, (int)kCntN)), kThreads, 0, s>>>(cx, n, cnt);
+  // external record nodes: inside a capture a plain record is only an edge
+  if (b->time_push) PIC_CUDA(cudaEventRecordWithFlags(b->tev[2 * st], s, cudaEventRecordExternal));
   k_push_batch<R><<<b->push_blocks * b->push_grid_mult, kThreads, 0, s>>>(cx, n, cnt,
                                                                         b->push_chunk);
+  if (b->time_push)
+    PIC_CUDA(cudaEventRecordWithFlags(b->tev[2 * st + 1], s, cudaEventRecordExternal));
   launched += 2;
   if (b->g_field.total > 0) {
     const FlatGrid G = flat_of(b, b->g_field);
@@ -1075,7 +1107,7 @@ int batch_capture(pic_batch_ctx *b) {
   if (b->multi) {
     // one launch per phase for all members, on the batch stream
     for (int st = 0; st < b->period && rc == PIC_OK; ++st)
-      rc = b->m[0]->fp64 ? enqueue_batch<double>(b) : enqueue_batch<float>(b);
+      rc = b->m[0]->fp64 ? enqueue_batch<double>(b, st) : enqueue_batch<float>(b, st);
   } else {
     e = cudaEventRecord(b->ev[0], s);
     for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q)
@@ -1130,51 +1162,79 @@ int batch_replay(pic_batch_ctx *b, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nu
 
 // The push's launch shape in batch launches, picked on the batch itself:
 // each candidate (particles per block task; grid of 1 or 2 times the
-// resident blocks) is captured and run for one period, then timed over a
-// second (CUDA events on the batch stream); the fastest is kept.  Every
-// period is a real one: the candidates differ only in how the same work is
-// spread over the GPU.  Uses two periods per candidate, and only when the
+// resident blocks) is captured with event pairs around its push launches and
+// run for one period; its cost is the push time over the particle pushes of
+// that period, so the growth of the particle count while the candidates take
+// turns does not favour the earlier ones.  The cheapest is kept.  Every
+// tuning period is a real one (the candidates differ only in how the same
+// work spreads over the GPU); it takes one period per candidate, when the
 // step request has them.
+int batch_pushes(pic_batch_ctx *b, double *out) {
+  double sum = 0.0;
+  for (pic_ctx *h : b->m) {
+    double acc[5];
+    const int rc = copy_out(h, h->P.off_acc, acc, sizeof(acc));
+    if (rc) return rc;
+    sum += acc[4];
+  }
+  *out = sum;
+  return PIC_OK;
+}
+
 int batch_tune(pic_batch_ctx *b, int &n_steps) {
   static const long long kChunk[] = {1024, 2048, 4096, 2048};
   static const int kMult[] = {1, 1, 1, 2};
   constexpr int kCand = 4;
-  if (n_steps < 2 * kCand * b->period) return PIC_OK;
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
-  PIC_CUDA(cudaEventCreate(&t0));
-  PIC_CUDA(cudaEventCreate(&t1));
+  if (n_steps < kCand * b->period) return PIC_OK;
+  if (b->tev.empty()) {
+    b->tev.resize(2 * (size_t)b->period);
+    for (auto &e : b->tev) PIC_CUDA(cudaEventCreate(&e));
+  }
   b->tune_chunk.clear();
   b->tune_mult.clear();
   b->tune_ms.clear();
+  b->tune_cost.clear();
   int rc = PIC_OK;
   for (int c = 0; c < kCand && rc == PIC_OK; ++c) {
     b->push_chunk = kChunk[c];
     b->push_grid_mult = kMult[c];
-    rc = batch_capture(b);  // captures and runs one period
+    double before = 0.0, after = 0.0;
+    PIC_CUDA(cudaStreamSynchronize(b->stream));
+    rc = batch_pushes(b, &before);
     if (rc) break;
-    rc = batch_replay(b, t0, t1);
+    b->time_push = true;
+    rc = batch_capture(b);  // captures with the timing events and runs one period
+    b->time_push = false;
     if (rc) break;
-    float ms = 0.f;
-    if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
-      rc = fail(PIC_ECUDA, "batch tuning: event timing failed");
-      break;
+    PIC_CUDA(cudaStreamSynchronize(b->stream));
+    double ms = 0.0;
+    for (int st = 0; st < b->period; ++st) {
+      float t = 0.f;
+      const cudaError_t et = cudaEventElapsedTime(&t, b->tev[2 * st], b->tev[2 * st + 1]);
+      if (et != cudaSuccess) {
+        rc = fail(PIC_ECUDA, std::string("batch tuning: event timing: ") + cudaGetErrorString(et));
+        break;
+      }
+      ms += t;
     }
+    if (rc) break;
+    rc = batch_pushes(b, &after);
+    if (rc) break;
     b->tune_chunk.push_back(kChunk[c]);
     b->tune_mult.push_back(kMult[c]);
     b->tune_ms.push_back(ms);
-    n_steps -= 2 * b->period;
+    b->tune_cost.push_back(ms * 1e6 / std::max(after - before, 1.0));
+    n_steps -= b->period;
   }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
   if (rc) return rc;
   int best = 0;
-  for (int c = 1; c < (int)b->tune_ms.size(); ++c)
-    if (b->tune_ms[c] < b->tune_ms[best]) best = c;
+  for (int c = 1; c < (int)b->tune_cost.size(); ++c)
+    if (b->tune_cost[c] < b->tune_cost[best]) best = c;
   b->tune_pick = best;
   b->push_chunk = b->tune_chunk[best];
   b->push_grid_mult = b->tune_mult[best];
   b->tuned = true;
-  if (b->exec) {  // the next period captures with the pick
+  if (b->exec) {  // the next period captures with the pick, without events
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
@@ -1271,8 +1331,8 @@ int pic_batch_step(pic_batch b, int n_steps) {
   return PIC_OK;
 }
 
-int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms, int *n,
-                     int *pick, int *batch_launches) {
+int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms,
+                     double *ns_per_push, int *n, int *pick, int *batch_launches) {
   if (!b || !n || !pick) return fail(PIC_EINVAL, "null pointer");
   *n = (int)b->tune_ms.size();
   *pick = b->tune_pick;
@@ -1281,6 +1341,7 @@ int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, dou
     if (chunk) chunk[c] = b->tune_chunk[c];
     if (grid_mult) grid_mult[c] = b->tune_mult[c];
     if (ms) ms[c] = b->tune_ms[c];
+    if (ns_per_push) ns_per_push[c] = b->tune_cost[c];
   }
   return PIC_OK;
 }
@@ -1300,6 +1361,7 @@ int pic_batch_destroy(pic_batch b) {
   cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->tab) cudaFree(b->tab);
+  for (auto &e : b->tev) cudaEventDestroy(e);
   for (auto &e : b->ev) cudaEventDestroy(e);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1893,7 +1955,7 @@ int pic_set_scalars(pic_handle h, long long step, const double in[4]) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 constexpr size_t kStageBytes = size_t(64) << 20;
 
 struct CkptHeader {

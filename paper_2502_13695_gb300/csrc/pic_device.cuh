@@ -95,6 +95,8 @@ struct Dev {
   R *imax;
   int imax_every;
   R inv_e0sq;
+  const R *ktab;                  // elliptic tables (K, E interleaved), or null
+  int ntab;
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
                                   // [4] pushes [8..11] Poynting fwd/bwd front, back
   // Poynting split: node planes (front, back), c eps0 dx dy dt, per-block
@@ -279,9 +281,32 @@ __host__ __device__ __forceinline__ float dawson_of_square<float>(float y) {
 // r = e^{-a} (every later Dawson factor is smaller past the maximum of F),
 // is below half an ulp of the sum, or after `nterms` terms.
 // ---------------------------------------------------------------------------
+// K and K - E from an N-point table (K(i/N), E(i/N) interleaved, i < N;
+// linear in m between neighbouring entries) while m lies inside it, else by
+// the AGM.
+template <class R>
+__host__ __device__ __forceinline__ void ellip_tab_k_kme(R m, R mc, const R *tab, int ntab, R &K,
+                                                         R &KmE) {
+  if (tab) {
+    const R u = m * R(ntab);
+    const R fi = floor(u);
+    if (fi >= R(0) && fi < R(ntab - 1)) {
+      const int i = (int)fi;
+      const R f = u - fi;
+      const R k = tab[2 * i] + f * (tab[2 * i + 2] - tab[2 * i]);
+      const R e = tab[2 * i + 1] + f * (tab[2 * i + 3] - tab[2 * i + 1]);
+      K = k;
+      KmE = k - e;
+      return;
+    }
+  }
+  ellip_k_kme(m, mc, K, KmE);
+}
+
 template <class R>
 __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterms,
-                                                 int *terms_out = nullptr) {
+                                                 int *terms_out = nullptr,
+                                                 const R *tab = nullptr, int ntab = 0) {
   if (terms_out) *terms_out = 0;
   if (!(E > R(0))) return R(0);
   const R g = R(L.kG) / E;
@@ -289,8 +314,8 @@ __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterm
   if (!(g2 < R(1e30))) return R(0);
   const R gam1 = g2 / (R(1) + g2), gam2 = R(1) / (R(1) + g2);
   R K1, KmE1, K2, KmE2;
-  ellip_k_kme(gam1, gam2, K1, KmE1);
-  ellip_k_kme(gam2, gam1, K2, KmE2);
+  ellip_tab_k_kme(gam1, gam2, tab, ntab, K1, KmE1);
+  ellip_tab_k_kme(gam2, gam1, tab, ntab, K2, KmE2);
   const R E2 = K2 - KmE2;
   const R x = R(L.kX) * E2 / sqrt(gam1);
   const R N = floor(x + R(1));
@@ -319,8 +344,10 @@ __host__ __device__ inline R keldysh_probability(R E, const LayerK &L, int nterm
 
 template <class R>
 __host__ __device__ inline unsigned long long keldysh_threshold(R E, const LayerK &L, int nterms,
-                                                                int *terms_out = nullptr) {
-  const R p = keldysh_probability<R>(E, L, nterms, terms_out);
+                                                                int *terms_out = nullptr,
+                                                                const R *tab = nullptr,
+                                                                int ntab = 0) {
+  const R p = keldysh_probability<R>(E, L, nterms, terms_out, tab, ntab);
   if (!(p < R(1))) return ~0ull;
   const double scaled = (double)p * 18446744073709551616.0;  // exact: power of 2
   return (unsigned long long)scaled;

@@ -849,7 +849,8 @@ __device__ __forceinline__ void keldysh_items(const Ctx<R> &X, int first, int la
     const long long m = X.work[q];
     const int k = D.kplane[(int)(m / D.nxy)];
     const R amp = D.eamp[m];
-    D.T[m] = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms);
+    D.T[m] = keldysh_threshold<R>(amp, D.layers[D.layer_of_plane[k]], D.keldysh_terms, nullptr,
+                                  D.ktab, D.ntab);
     D.ckey[m] = amp;
   }
 }
@@ -1188,8 +1189,9 @@ __global__ void k_init_material(Ctx<R> X) {
 // the waves going along +z, ((Ex + c By) / 2, (Ey - c Bx) / 2), and along -z,
 // ((Ex - c By) / 2, (Ey + c Bx) / 2).  Each block writes its FP64 sums of
 // |fwd|^2 and |bwd|^2; the last block to finish (counted with one atomic,
-// nothing waits) adds them in block order times c eps0 dx dy dt to the time
-// integrals, advances the step and resets the count.
+// nothing waits) adds them up in a fixed order (one warp's loads and a
+// shuffle tree) times c eps0 dx dy dt to the time integrals, advances the
+// step and resets the count.
 constexpr int kFluxBlocks = 16;
 
 template <class R>
@@ -1216,17 +1218,27 @@ __device__ __forceinline__ void flux_advance_body(const Dev<R> &D, Blk bk) {
     p[1] = bs;
     __threadfence();
     last = atomicAdd(D.flux_cnt, 1u) == 2u * (unsigned)bk.gx - 1u;
-    if (last) {
-      __threadfence();
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    // the first warp loads the partials together (lane x sums blocks x,
+    // x + 32, ...) and adds them up in a fixed shuffle tree
+    __threadfence();
+    const int lane = threadIdx.x;
+    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int x = lane; x < bk.gx; x += 32)
+#pragma unroll
       for (int qq = 0; qq < 2; ++qq) {
-        double F = 0.0, B = 0.0;
-        for (int x = 0; x < bk.gx; ++x) {
-          F += __ldcg(D.flux_part + 2 * (qq * bk.gx + x));
-          B += __ldcg(D.flux_part + 2 * (qq * bk.gx + x) + 1);
-        }
-        D.acc[8 + 2 * qq] += F * D.flux_scale;
-        D.acc[9 + 2 * qq] += B * D.flux_scale;
+        acc4[2 * qq] += __ldcg(D.flux_part + 2 * (qq * bk.gx + x));
+        acc4[2 * qq + 1] += __ldcg(D.flux_part + 2 * (qq * bk.gx + x) + 1);
       }
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int sft = 16; sft > 0; sft >>= 1) acc4[v] += __shfl_xor_sync(0xffffffffu, acc4[v], sft);
+    if (lane == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) D.acc[8 + v] += acc4[v] * D.flux_scale;
       *D.flux_cnt = 0u;
       *D.step += 1;
     }

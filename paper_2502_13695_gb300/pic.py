@@ -49,7 +49,8 @@ class Grid(ctypes.Structure):
                 ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("pool_factor", ctypes.c_double),
                 ("keldysh_terms", ctypes.c_int), ("sort_interval", ctypes.c_int),
-                ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int)]
+                ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int),
+                ("elliptic_table", ctypes.c_int), ("reserved_grid", ctypes.c_int)]
 
 
 class Layer(ctypes.Structure):
@@ -150,7 +151,7 @@ def lib():
         L.pic_batch_step.argtypes = [vp, i]
         L.pic_batch_sync.argtypes = [vp]
         L.pic_batch_destroy.argtypes = [vp]
-        L.pic_batch_tuning.argtypes = [vp, i, vp, vp, vp, P(i), P(i), P(i)]
+        L.pic_batch_tuning.argtypes = [vp, i, vp, vp, vp, vp, P(i), P(i), P(i)]
         L.pic_profile_read.argtypes = [vp, vp, vp]
         L.pic_save.argtypes = [vp, ctypes.c_char_p]
         L.pic_load.argtypes = [ctypes.c_char_p, vp, vp, ctypes.c_size_t, P(vp)]
@@ -184,6 +185,7 @@ def c_structs(cfg: dict):
     g.sort_interval = cfg.get("sort_interval", 0)
     g.imax_every = cfg.get("imax_every", 0)
     g.coll_every = cfg.get("coll_every", 0)
+    g.elliptic_table = cfg.get("elliptic_table", 0)
     layers = (Layer * max(1, len(cfg["layers"])))()
     for n, ly in enumerate(cfg["layers"]):
         L = layers[n]
@@ -218,7 +220,8 @@ def checkpoint_config(path: str) -> dict:
                precision="fp64" if g.precision == PIC_FP64 else "fp32",
                pool_factor=g.pool_factor, keldysh_terms=g.keldysh_terms,
                sort_interval=g.sort_interval, imax_every=g.imax_every,
-               coll_every=g.coll_every, seed=int(seed.value), step=int(step.value))
+               coll_every=g.coll_every, elliptic_table=g.elliptic_table,
+               seed=int(seed.value), step=int(step.value))
     cfg["layers"] = [
         {f: getattr(layers[q], f) for f in (
             "z0", "z1", "ppc", "n_index", "gap_eV", "me_star", "mh_star", "n_mol",
@@ -456,13 +459,15 @@ class Batch:
         """How the batch steps (pic_batch_tuning): batch launches or not, and
         the push launch shapes the tuner measured and the one it kept."""
         cap = 16
-        chunk, mult, ms = np.zeros(cap, np.int64), np.zeros(cap, np.int32), np.zeros(cap)
+        chunk, mult = np.zeros(cap, np.int64), np.zeros(cap, np.int32)
+        ms, cost = np.zeros(cap), np.zeros(cap)
         n, pick, bl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().pic_batch_tuning(self._h, cap, _ptr(chunk), _ptr(mult), _ptr(ms),
+        _check(lib().pic_batch_tuning(self._h, cap, _ptr(chunk), _ptr(mult), _ptr(ms), _ptr(cost),
                                       ctypes.byref(n), ctypes.byref(pick), ctypes.byref(bl)))
         k = n.value
         return dict(batch_launches=bool(bl.value), pick=pick.value,
-                    candidates=[dict(chunk=int(chunk[q]), grid_mult=int(mult[q]), ms=float(ms[q]))
+                    candidates=[dict(chunk=int(chunk[q]), grid_mult=int(mult[q]),
+                                     push_ms=float(ms[q]), ns_per_push=float(cost[q]))
                                 for q in range(k)])
 
     def close(self):

@@ -253,6 +253,7 @@ def paper_silica(fluence_Jcm2=1.2, ppc=2, collisions=False, precision="fp32", se
                paper_pulse(fluence_Jcm2), seed=seed, precision=precision, pool_factor=2.0,
                dz=5e-9, name="paper-silica-240x240x206-5nm")
     cfg["coll_every"] = 1 if collisions else 0
+    cfg["elliptic_table"] = 1000  # Sec. 2.1: K and E read from 1000-point tables
     cfg["steps"] = paper_steps(cfg)
     return cfg
 
@@ -273,5 +274,6 @@ def paper_mirror(fluence_Jcm2=0.7, pairs=5, ppc=2, collisions=False, precision="
     cfg = grid(240, 240, z + 4, 40e-9, lay, paper_pulse(fluence_Jcm2), seed=seed,
                precision=precision, pool_factor=2.0, dz=d, name=f"paper-mirror-{pairs}pairs")
     cfg["coll_every"] = 1 if collisions else 0
+    cfg["elliptic_table"] = 1000
     cfg["steps"] = paper_steps(cfg)
     return cfg

@@ -93,9 +93,10 @@ def test_fp32_batch_launches_match_members_alone():
 
 
 def test_batch_tunes_its_push_shape_on_itself():
-    """A step request of eight periods or more tunes the push launch shape:
-    four candidates, each timed over a real period, the fastest kept; the
-    members still step exactly as many steps and match their runs alone."""
+    """A step request of four periods or more tunes the push launch shape:
+    four candidates, each timed over a real period, the one with the least
+    push time per particle push kept; the members still step exactly as many
+    steps and match their runs alone."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.fail("GPU tests need a CUDA device")
@@ -112,8 +113,9 @@ def test_batch_tunes_its_push_shape_on_itself():
     tu = batch.tuning()
     assert tu["batch_launches"]
     assert len(tu["candidates"]) == 4 and 0 <= tu["pick"] < 4
-    assert all(c["ms"] > 0 for c in tu["candidates"])
-    assert tu["candidates"][tu["pick"]]["ms"] == min(c["ms"] for c in tu["candidates"])
+    assert all(c["push_ms"] > 0 and c["ns_per_push"] > 0 for c in tu["candidates"])
+    cost = [c["ns_per_push"] for c in tu["candidates"]]
+    assert cost[tu["pick"]] == min(cost)
     for c, g in zip(cfgs, sims):
         assert g.scalars()["step"] == 8 * 32 + 10
         a = pic.Simulation(c)

@@ -320,3 +320,36 @@ def test_particles_then_advance_then_fields_fp64(pic, oracle_mod):
     nz_comps = [c for c in range(15) if np.linalg.norm(Fo[c]) > 0]
     assert_fields_close(Fg, Fo, TOL64, comps=nz_comps, what="split phases")
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_elliptic_tables_match_oracle(pic, oracle_mod, precision):
+    """The paper's 1000-point elliptic tables on both sides: thresholds
+    from an oracle state to 1e-12 (FP64; FP32 within its series bound
+    1e-3), and in FP64 a 60-step run with the oracle's decisions."""
+    cfg = dict(wl.small_slab(precision="fp64"), elliptic_table=1000)
+    o = oracle_mod.Sim(cfg)
+    o.step(45)
+    g = pic.Simulation(dict(cfg, precision=precision))
+    g.load_state(oracle_state_for_gpu(o))
+    g.phases(4)
+    o.phases(4)
+    Tg = g.material()["T"].astype(np.float64)
+    To = o.material()["T"].astype(np.float64)
+    hot = (To > 0) & (To < 2.0 ** 64 - 2)
+    assert hot.sum() > 100
+    tol = 1e-12 if precision == "fp64" else 1e-3
+    assert np.max(np.abs(Tg[hot] / To[hot] - 1)) < tol
+    if precision == "fp64":
+        o2, g2 = oracle_mod.Sim(cfg), pic.Simulation(cfg)
+        o2.step(60)
+        g2.step(60)
+        assert np.array_equal(g2.material()["alive"], o2.material()["alive"])
+        Fg, Fo = g2.fields(), o2.fields()
+        for sl in (slice(0, 3), slice(3, 6), slice(9, 12), slice(12, 15)):
+            assert rel_l2(Fg[sl], Fo[sl]) <= TOL64
+        assert_particles_close(g2.particles(), o2.particles(), cfg, 1e-11, 1e-11, "tables")
+        # the tables are in use: in-situ thresholds differ slightly
+        a = oracle_mod.Sim(dict(cfg, elliptic_table=0))
+        a.set_material(o.material()["alive"], o.material()["win"])
+        assert a.threshold(0, 3e10) != o.threshold(0, 3e10)
