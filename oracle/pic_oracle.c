@@ -92,6 +92,9 @@ typedef struct {
   int shape;      /* temporal envelope: 0 Gaussian, 1 sine-squared (Sec. 3) */
   int elliptic_table; /* 0: K and E in situ; N >= 2: read from N-point tables */
   double w0;      /* Gaussian spot radius (1/e^2 of the intensity), 0 = plane wave */
+  int pml_cells;  /* 0: periodic x and y; L > 0: absorbing layers of L cells on each
+                     side of the x and y seams, particles entering them removed */
+  int pad_pml;
   or_layer layers[OR_MAX_LAYERS];
 } or_config;
 
@@ -426,7 +429,12 @@ typedef struct {
   /* elliptic tables (elliptic_table > 0): K(i / N), E(i / N) */
   double *tabK, *tabE;
   int ntab;
+  /* absorbing transverse layers: the convolution terms of the x and y
+   * derivatives in the curl (pml_cells > 0) */
+  double *psi[8];
 } or_sim;
+
+enum { PEYX, PEZX, PEXY, PEZY, PBYX, PBZX, PBXY, PBZY };
 
 static long fidx(const or_sim *s, int i, int j, int k) {
   int nx = s->cfg.nx, ny = s->cfg.ny;
@@ -478,7 +486,8 @@ double or_spot(const or_sim *s, double x, double y) {
 or_sim *or_create(const or_config *cfg) {
   const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
   if (nx < 4 || ny < 4 || nz < 8 || cfg->n_layers < 0 ||
-      cfg->n_layers > OR_MAX_LAYERS)
+      cfg->n_layers > OR_MAX_LAYERS || cfg->pml_cells < 0 || 2 * cfg->pml_cells >= nx ||
+      2 * cfg->pml_cells >= ny)
     return NULL;
   or_sim *s = calloc(1, sizeof(or_sim));
   s->cfg = *cfg;
@@ -559,6 +568,8 @@ or_sim *or_create(const or_config *cfg) {
   s->Talways = calloc(s->nmat ? s->nmat : 1, 1);
   s->alive = calloc(s->nmat ? s->nmat : 1, sizeof(uint32_t));
   s->imax = calloc((size_t)s->nxy * nz, sizeof(double));
+  if (cfg->pml_cells > 0)
+    for (int q = 0; q < 8; q++) s->psi[q] = calloc(s->nfield, sizeof(double));
   if (cfg->elliptic_table >= 2) {
     s->ntab = cfg->elliptic_table;
     s->tabK = malloc((size_t)s->ntab * sizeof(double));
@@ -590,6 +601,7 @@ void or_destroy(or_sim *s) {
   if (!s) return;
   free(s->tabK);
   free(s->tabE);
+  for (int q = 0; q < 8; q++) free(s->psi[q]);
   free(s->imax);
   for (int c = 0; c < NCOMP; c++) free(s->F[c]);
   free(s->layer_of_plane);
@@ -714,6 +726,11 @@ void or_particle_pass(or_sim *s) {
     if (cn[2] < 2 || cn[2] >= nz - 2) continue; /* outflow: deleted */
     cn[0] = (cn[0] % nx + nx) % nx;
     cn[1] = (cn[1] % ny + ny) % ny;
+    {
+      /* outflow through the absorbing transverse layers */
+      int L = s->cfg.pml_cells;
+      if (L > 0 && (cn[0] < L || cn[0] >= nx - L || cn[1] < L || cn[1] >= ny - L)) continue;
+    }
     s->pid[w] = s->pid[p];
     s->pcell[w] = (int32_t)(((long)cn[2] * ny + cn[1]) * nx + cn[0]);
     for (int d = 0; d < 3; d++) {
@@ -730,6 +747,32 @@ void or_particle_pass(or_sim *s) {
 /* Field pass: B half step, E with Lorentz polarisation and Silver-Mueller   */
 /* z faces, B half step, J cleared.                                          */
 /* ------------------------------------------------------------------------ */
+/* Absorbing transverse layers (the paper's outflow boundaries, Sec. 3.1):
+ * a convolutional perfectly matched layer (Roden and Gedney, Microw. Opt.
+ * Technol. Lett. 27, 334 (2000)) with kappa = 1 and alpha = 0, of L cells on
+ * each side of the periodic seam of x (and of y), so that a wave leaving
+ * through either face crosses 2 L graded cells.  A position p (in cells)
+ * lies at depth d = L - p below L, p - (n - L) above n - L, else 0; the
+ * conductivity is sigma = sigma_max (d / L)^3, sigma_max = 0.8 (3 + 1) /
+ * (eta0 delta) for cells of size delta.  Over a time step h a derivative df
+ * of the curl becomes df + psi, psi <- b psi + (b - 1) df, with
+ * b = exp(-sigma h / eps0) (1 outside the layers, where psi stays 0). */
+static double pml_b(const or_sim *s, double p, int n, double delta, double h) {
+  int L = s->cfg.pml_cells;
+  double d = p < L ? L - p : (p > n - L ? p - (n - L) : 0.0);
+  if (!(d > 0.0)) return 1.0;
+  double smax = 0.8 * 4.0 / (OR_MU0 * OR_C * delta);
+  double r = d / L;
+  return exp(-smax * r * r * r * h / OR_EPS0);
+}
+
+/* The layer's derivative: df + psi with psi advanced in place. */
+static double pml_d(const or_sim *s, int q, long o, double b, double df) {
+  if (!s->psi[q]) return df;
+  s->psi[q][o] = b * s->psi[q][o] + (b - 1.0) * df;
+  return df + s->psi[q][o];
+}
+
 static void b_half(or_sim *s) {
   const int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->cfg.nz;
   const double h = 0.5 * s->dt, dx = s->cfg.dx, dy = s->cfg.dy,
@@ -741,14 +784,17 @@ static void b_half(or_sim *s) {
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) {
         long o = fidx(s, i, j, k);
+        /* x derivatives at x = i + 1/2, y derivatives at y = j + 1/2 */
+        double bxh = pml_b(s, i + 0.5, nx, dx, h), byh = pml_b(s, j + 0.5, ny, dy, h);
         if (k < nz) {
-          Bx[o] -= h * ((Ez[fidx(s, i, j + 1, k)] - Ez[o]) / dy -
-                        (Ey[fidx(s, i, j, k + 1)] - Ey[o]) / dz);
-          By[o] -= h * ((Ex[fidx(s, i, j, k + 1)] - Ex[o]) / dz -
-                        (Ez[fidx(s, i + 1, j, k)] - Ez[o]) / dx);
+          double dEz_dy = pml_d(s, PBXY, o, byh, (Ez[fidx(s, i, j + 1, k)] - Ez[o]) / dy);
+          double dEz_dx = pml_d(s, PBYX, o, bxh, (Ez[fidx(s, i + 1, j, k)] - Ez[o]) / dx);
+          Bx[o] -= h * (dEz_dy - (Ey[fidx(s, i, j, k + 1)] - Ey[o]) / dz);
+          By[o] -= h * ((Ex[fidx(s, i, j, k + 1)] - Ex[o]) / dz - dEz_dx);
         }
-        Bz[o] -= h * ((Ey[fidx(s, i + 1, j, k)] - Ey[o]) / dx -
-                      (Ex[fidx(s, i, j + 1, k)] - Ex[o]) / dy);
+        double dEy_dx = pml_d(s, PBZX, o, bxh, (Ey[fidx(s, i + 1, j, k)] - Ey[o]) / dx);
+        double dEx_dy = pml_d(s, PBZY, o, byh, (Ex[fidx(s, i, j + 1, k)] - Ex[o]) / dy);
+        Bz[o] -= h * (dEy_dx - dEx_dy);
       }
 }
 
@@ -795,8 +841,10 @@ static void e_full(or_sim *s) {
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) {
         long o = fidx(s, i, j, k);
-        double dBz_dy = (Bz[o] - Bz[fidx(s, i, j - 1, k)]) / dy;
-        double dBz_dx = (Bz[o] - Bz[fidx(s, i - 1, j, k)]) / dx;
+        /* x derivatives at x = i, y derivatives at y = j (absorbing layers) */
+        double bxi = pml_b(s, (double)i, nx, dx, dt), byi = pml_b(s, (double)j, ny, dy, dt);
+        double dBz_dy = pml_d(s, PEXY, o, byi, (Bz[o] - Bz[fidx(s, i, j - 1, k)]) / dy);
+        double dBz_dx = pml_d(s, PEYX, o, bxi, (Bz[o] - Bz[fidx(s, i - 1, j, k)]) / dx);
         double ex0 = Ex[o], ey0 = Ey[o], ex1, ey1;
         if (k == 0) {
           /* the polarised component's own node: Ex at ((i + 1/2) dx, j dy),
@@ -829,9 +877,9 @@ static void e_full(or_sim *s) {
         Ex[o] = ex1;
         Ey[o] = ey1;
         if (k < nz) {
-          double az = dt * (c2 * ((By[o] - By[fidx(s, i - 1, j, k)]) / dx -
-                                  (Bx[o] - Bx[fidx(s, i, j - 1, k)]) / dy) -
-                            Jz[o] / OR_EPS0);
+          double dBy_dx = pml_d(s, PEZX, o, bxi, (By[o] - By[fidx(s, i - 1, j, k)]) / dx);
+          double dBx_dy = pml_d(s, PEZY, o, byi, (Bx[o] - Bx[fidx(s, i, j - 1, k)]) / dy);
+          double az = dt * (c2 * (dBy_dx - dBx_dy) - Jz[o] / OR_EPS0);
           double ez0 = Ez[o];
           double ez1 = e_point(s, L, ez0, az, &s->F[FPZ][o], &s->F[FQZ][o]);
           joule += Jz[o] * 0.5 * (ez0 + ez1);

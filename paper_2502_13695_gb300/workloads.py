@@ -216,6 +216,62 @@ def random_fields(cfg, seed, e_amp=1e10, b_amp=30.0, j_amp=0.0, p_amp=0.0):
     return F
 
 
+def vacuum_packet(cfg, axis, pol, sign=1, center=None, width=8.0, z_width=8.0, lam_cells=10.0):
+    """Fields of a light packet running along +x (axis 0) or +y (axis 1), or
+    along -x / -y (sign -1), built from a vector potential A so that the
+    discrete div B and div E are zero: B is the Yee curl of A sampled on the
+    E nodes, E = sign c dA/du with u the axis.  A = g(u) cos(k (u - u0)) with
+    a Gaussian envelope g of `width` cells about u0 = `center` (default the
+    middle) and a carrier of `lam_cells` cells.
+    pol "t": A along the other transverse axis (Ey for a packet along x, Ex
+    along y), Gaussian of `z_width` cells about the middle plane in z;
+    pol "z": A = Az, uniform in z (Ez, with By or Bx)."""
+    c = 299792458.0
+    nx, ny, nz, d = cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"] if axis == 0 else cfg["dy"]
+    n = nx if axis == 0 else ny
+    u0 = (n / 2 if center is None else center) * d
+    k = 2 * math.pi / (lam_cells * d)
+    dz = cfg["dz"]
+
+    def env(u):
+        return np.exp(-((u - u0) / (width * d)) ** 2)
+
+    def A(u):
+        return env(u) * np.cos(k * (u - u0))
+
+    def dA(u):
+        return env(u) * (-2 * (u - u0) / (width * d) ** 2 * np.cos(k * (u - u0)) -
+                         k * np.sin(k * (u - u0)))
+
+    def along(v):  # values over u, broadcast onto the (z, y, x) grid
+        return v[None, None, :] if axis == 0 else v[None, :, None]
+
+    u = np.arange(n + 1) * d
+    ones = np.ones((nz + 1, ny, nx))
+    F = np.zeros((15, nz + 1, ny, nx))
+    if pol == "t":
+        zz = np.arange(nz + 2)[:, None, None] * dz
+        gz = np.exp(-((zz - nz / 2 * dz) / (z_width * dz)) ** 2)
+        Au = along(A(u)) * gz                      # on E nodes along u, all z planes
+        dAu = np.diff(Au, axis=2 if axis == 0 else 1) / d  # at u + 1/2
+        dAz = np.diff(along(A(u[:n])) * gz, axis=0) / dz   # at k + 1/2
+        e = sign * c * along(dA(u[:n])) * gz[:nz + 1]
+        if axis == 0:  # A = Ay: Ey, Bz = dAy/dx, Bx = -dAy/dz
+            F[1], F[5], F[3] = e * ones, dAu[:nz + 1] * ones, -dAz * ones
+        else:          # A = Ax: Ex, Bz = -dAx/dy, By = dAx/dz
+            F[0], F[5], F[4] = e * ones, -dAu[:nz + 1] * ones, dAz * ones
+    else:
+        dAu = np.diff(along(A(u)), axis=2 if axis == 0 else 1) / d
+        F[2] = sign * c * along(dA(u[:n])) * ones
+        if axis == 0:
+            F[4] = -dAu * ones  # By = -dAz/dx
+        else:
+            F[3] = dAu * ones   # Bx = dAz/dy
+    for comp in (2, 3, 4):      # Ez, Bx, By live on k + 1/2: none on plane nz
+        F[comp, nz] = 0.0
+    return F
+
+
 # --------------------------------------------------------------------------
 # The paper's own geometry (Sec. 3): Table 1 materials with a static
 # permittivity (Sec. 2.3), 7 fs sine-squared pulse with a 4.65 um spot,
