@@ -95,7 +95,14 @@ typedef struct {
                           tables as the paper reads them (Sec. 2.1: 1000
                           points): K(i/N), E(i/N), i < N, linear in the
                           parameter between entries, in situ past the last */
-  int reserved_grid;
+  int pml_cells;       /* transverse faces (Sec. 3.1 uses outflow faces): 0
+                          periodic in x and y; L > 0 (2 L < nx, ny) absorbing
+                          layers of L cells on each side of the x = 0 and y = 0
+                          seams: a convolutional PML (Roden and Gedney 2000,
+                          kappa 1, alpha 0, conductivity sigma_max (d / L)^3 at
+                          depth d, sigma_max = 0.8 * 4 / (eta0 * cell size)),
+                          and a particle that ends a push inside them leaves
+                          the simulation, as through the z faces */
 } pic_grid;
 
 /* One dielectric layer: z cells [z0, z1) over the whole transverse plane.
@@ -385,13 +392,15 @@ int pic_batch_destroy(pic_batch b);
  * holds one launch per phase of a step for all members together (batch
  * launches: fixed grids laid end to end over the members, particle and
  * Keldysh loops in chunks handed out from a counter); otherwise it holds
- * every member's own launches, each on its stream.  With batch launches the
- * first pic_batch_step that asks for at least 4 periods tunes the push's
- * launch shape on the batch itself: four candidates (particles per block
- * task, grid as 1 or 2 times the resident blocks), each captured with CUDA
- * events around its push launches and run for one period; the one with the
- * least push time per particle push is kept (every tuning period is a real
- * step of every member).
+ * every member's own launches, each on its stream.  With batch launches, a
+ * pic_batch_step with at least 4 periods left tunes the push's launch shape
+ * on the batch itself once the members hold particles (four per resident
+ * push thread, or a 64th of their pools; checked before each period
+ * until then): four candidates (particles per block task, grid as 1 or 2
+ * times the resident blocks), each captured with CUDA events around its push
+ * launches and run for one period; the one with the least push time per
+ * particle push is kept (every tuning period is a real step of every
+ * member).
  *   cap            : entries the arrays hold
  *   chunk, grid_mult, ms, ns_per_push : per candidate (any may be NULL): the
  *                    shape, its push time over the period [ms] and per

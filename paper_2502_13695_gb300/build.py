@@ -11,7 +11,7 @@ LIB = os.path.join(BUILD, "libpicgb300.so")
 SOURCES = [os.path.join(CSRC, "pic_api.cu"), os.path.join(CSRC, "pic_noalloc.cu"),
            os.path.join(CSRC, "pic_serve.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("pic_device.cuh", "pic_kernels.cuh",
-                                                  "dawson_f32_table.inc")] + [
+                                                  "pic_batch.cuh", "dawson_f32_table.inc")] + [
     os.path.join(os.path.dirname(HERE), "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]

@@ -67,8 +67,12 @@ struct Plan {
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t off_flux_part, off_flux_cnt;
   size_t off_ktab;               // elliptic tables (elliptic_table > 0)
+  size_t off_psi[8];             // absorbing-layer convolution terms (pml_cells > 0)
+  size_t off_pmlb;               // their decay factors: E along x, y; B along x, y
+  std::vector<double> pmlb;      // the same factors on the host
   std::vector<double> ktab;      // the same tables on the host, K and E interleaved
   int flux_plane[2];  // node planes of the Poynting split (front, back)
+  int flux_blocks;    // blocks per flux plane
   size_t total;
 };
 
@@ -87,6 +91,8 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
     return fail(PIC_EINVAL, "negative count");
   if (g.elliptic_table != 0 && (g.elliptic_table < 2 || g.elliptic_table > 1000000))
     return fail(PIC_EINVAL, "elliptic_table must be 0 or 2 .. 1000000 points");
+  if (g.pml_cells < 0 || 2 * g.pml_cells >= g.nx || 2 * g.pml_cells >= g.ny)
+    return fail(PIC_EINVAL, "pml_cells must be >= 0 with 2 pml_cells < nx, ny");
   if (mat->n_layers < 0 || mat->n_layers > PIC_MAX_LAYERS || (mat->n_layers && !mat->layers))
     return fail(PIC_EINVAL, "bad layer count");
   if (!(pulse->lambda > 0 && pulse->fwhm > 0 && pulse->fluence >= 0) ||
@@ -221,7 +227,9 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   P.off_nslots = take(8);
   P.off_step = take(8);
   P.off_acc = take(16 * 8);
-  P.off_flux_part = take(2 * kFluxBlocks * 2 * 8);
+  P.flux_blocks = (int)std::min<long long>(std::max<long long>((P.nxy + kThreads - 1) / kThreads, 1),
+                                            kFluxMaxBlocks);
+  P.off_flux_part = take(2 * kFluxMaxBlocks * 2 * 8);
   P.off_ktab = take((size_t)2 * std::max(g.elliptic_table, 1) * R);
   P.ktab.clear();
   for (int i = 0; i < g.elliptic_table; ++i) {
@@ -230,6 +238,26 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
     ellip_k_kme<double>(m, 1.0 - m, K, KmE);
     P.ktab.push_back(K);
     P.ktab.push_back(K - KmE);
+  }
+  // absorbing layers: eight convolution terms over the field points and the
+  // decay factors b = exp(-sigma h / eps0) of each position, E (integer
+  // positions, h = dt) then B (half-integer ones, h = dt / 2), x then y
+  const bool pml = g.pml_cells > 0;
+  for (int q = 0; q < 8; ++q) P.off_psi[q] = take(pml ? P.nfield * R : 1);
+  P.off_pmlb = take((size_t)2 * (g.nx + g.ny) * R);
+  P.pmlb.clear();
+  if (pml) {
+    const int L = g.pml_cells;
+    const int n[2] = {g.nx, g.ny};
+    const double cell[2] = {g.dx, g.dy};
+    for (int half = 0; half < 2; ++half)
+      for (int ax = 0; ax < 2; ++ax)
+        for (int i = 0; i < n[ax]; ++i) {
+          const double p = i + 0.5 * half, h = half ? 0.5 * P.dt : P.dt;
+          const double d = p < L ? L - p : (p > n[ax] - L ? p - (n[ax] - L) : 0.0);
+          const double smax = 0.8 * 4.0 / (kMu0 * kC * cell[ax]), r = d / L;
+          P.pmlb.push_back(d > 0.0 ? std::exp(-smax * r * r * r * h / kEps0) : 1.0);
+        }
   }
   P.off_flux_cnt = take(16);
   P.off_err = take(16);
@@ -464,6 +492,15 @@ void bind(pic_ctx *h) {
   D.acc = (double *)(A + P.off_acc);
   D.ktab = P.ktab.empty() ? nullptr : (const R *)(A + P.off_ktab);
   D.ntab = P.g.elliptic_table;
+  D.pml = P.g.pml_cells;
+  for (int q = 0; q < 8; ++q) D.psi[q] = D.pml ? (R *)(A + P.off_psi[q]) : nullptr;
+  {
+    const R *b = (const R *)(A + P.off_pmlb);
+    D.pml_bE[0] = b;
+    D.pml_bE[1] = b + P.g.nx;
+    D.pml_bB[0] = b + P.g.nx + P.g.ny;
+    D.pml_bB[1] = b + 2 * P.g.nx + P.g.ny;
+  }
   D.flux_k[0] = P.flux_plane[0];
   D.flux_k[1] = P.flux_plane[1];
   D.flux_scale = kC * kEps0 * P.g.dx * P.g.dy * P.dt;
@@ -547,6 +584,14 @@ int sort_pool(pic_ctx *h, bool by_frame) {
   return PIC_OK;
 }
 
+// Calls f(std::true_type) for grids with absorbing transverse layers (the
+// field kernels instantiated with their terms), else f(std::false_type).
+template <class F>
+void with_layers(bool on, F &&f) {
+  if (on) f(std::true_type{});
+  else f(std::false_type{});
+}
+
 // Bh = B - (dt/2) curl E from the current fields, unless the last field
 // pass left it valid (nothing but the host writes E or B between passes).
 template <class R>
@@ -555,16 +600,19 @@ int prime_bh(pic_ctx *h) {
   const Plan &P = h->P;
   Ctx<R> &X = ctx_of<R>(h);
   cudaStream_t s = h->stream;
-  if constexpr (sizeof(R) == 4) {
-    if (h->field_v == 4) {
-      const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
-      k_bstep<4, kPrime, R><<<grid, kThreads, 0, s>>>(X.d);
+  with_layers(P.g.pml_cells > 0, [&](auto lay) {
+    constexpr bool kLay = decltype(lay)::value;
+    if constexpr (sizeof(R) == 4) {
+      if (h->field_v == 4) {
+        const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
+        k_bstep<4, kPrime, R, kLay><<<grid, kThreads, 0, s>>>(X.d);
+      }
     }
-  }
-  if (h->field_v == 1) {
-    const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
-    k_bstep<1, kPrime, R><<<grid, kThreads, 0, s>>>(X.d);
-  }
+    if (h->field_v == 1) {
+      const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
+      k_bstep<1, kPrime, R, kLay><<<grid, kThreads, 0, s>>>(X.d);
+    }
+  });
   PIC_CUDA(cudaGetLastError());
   h->launches += 1;
   h->bh_valid = true;
@@ -621,18 +669,21 @@ int enqueue(pic_ctx *h, int mask) {
     prof_begin(h, PIC_PROF_FIELDS);
     const int rp = prime_bh<R>(h);
     if (rp) return rp;
-    if constexpr (sizeof(R) == 4) {
-      if (h->field_v == 4) {
-        const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
-        k_efull<4, R><<<grid, kThreads, 0, s>>>(X);
-        k_bstep<4, kFullRecord, R><<<grid, kThreads, 0, s>>>(X.d);
+    with_layers(P.g.pml_cells > 0, [&](auto lay) {
+      constexpr bool kLay = decltype(lay)::value;
+      if constexpr (sizeof(R) == 4) {
+        if (h->field_v == 4) {
+          const dim3 grid(grid_blocks(P.nxy / 4), (unsigned)(P.g.nz + 1));
+          k_efull<4, R, kLay><<<grid, kThreads, 0, s>>>(X);
+          k_bstep<4, kFullRecord, R, kLay><<<grid, kThreads, 0, s>>>(X.d);
+        }
       }
-    }
-    if (h->field_v == 1) {
-      const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
-      k_efull<1, R><<<grid, kThreads, 0, s>>>(X);
-      k_bstep<1, kFullRecord, R><<<grid, kThreads, 0, s>>>(X.d);
-    }
+      if (h->field_v == 1) {
+        const dim3 grid(grid_blocks(P.nxy), (unsigned)(P.g.nz + 1));
+        k_efull<1, R, kLay><<<grid, kThreads, 0, s>>>(X);
+        k_bstep<1, kFullRecord, R, kLay><<<grid, kThreads, 0, s>>>(X.d);
+      }
+    });
     prof_end(h);
     h->launches += 2;
     h->bh_valid = true;
@@ -660,7 +711,7 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (mask & PIC_PHASE_ADVANCE) {
     prof_begin(h, PIC_PROF_OTHER);
-    k_flux_advance<R><<<dim3(kFluxBlocks, 2), kThreads, 0, s>>>(X.d);
+    k_flux_advance<R><<<dim3(P.flux_blocks, 2), kThreads, 0, s>>>(X.d);
     prof_end(h);
     h->launches += 1;
     h->step++;
@@ -705,6 +756,12 @@ int init_state(pic_ctx *h) {
                              cudaMemcpyHostToDevice, s));
     h->h2d_bytes += (long long)(h->lk.size() * sizeof(LayerK) + lr.size() * sizeof(LayerR<R>));
     PIC_CUDA(cudaStreamSynchronize(s));  // lr is a host temporary
+  }
+  if (!P.pmlb.empty()) {
+    std::vector<R> pb(P.pmlb.begin(), P.pmlb.end());
+    PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_pmlb, pb.data(), pb.size() * sizeof(R),
+                             cudaMemcpyHostToDevice, h->stream));
+    PIC_CUDA(cudaStreamSynchronize(h->stream));
   }
   if (!P.ktab.empty()) {
     std::vector<R> kt(P.ktab.begin(), P.ktab.end());
@@ -971,7 +1028,7 @@ int batch_tables(pic_batch_ctx *b) {
                      (unsigned long long *)(h->arena + P.off_total), P.ncell, P.nb_scan, 0};
     const int V = h->field_v;
     const int gxs[6] = {grid_blocks(P.nxy / V), grid_blocks(P.nxy / V), grid_blocks(P.nxy),
-                        kFluxBlocks, P.nb_scan, grid_blocks(P.ncell)};
+                        P.flux_blocks, P.nb_scan, grid_blocks(P.ncell)};
     const long long gys[6] = {P.g.nz + 1, P.n_mplanes, P.n_mplanes, 2, 1, 1};
     for (int k = 0; k < 6; ++k) {
       gx[k][q] = gxs[k];
@@ -1020,16 +1077,21 @@ int enqueue_batch(pic_batch_ctx *b, int st) {
   launched += 2;
   if (b->g_field.total > 0) {
     const FlatGrid G = flat_of(b, b->g_field);
-    if constexpr (sizeof(R) == 4) {
-      if (V == 4) {
-        k_efull_batch<4, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
-        k_bstep_batch<4, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+    bool any_layers = false;
+    for (const pic_ctx *h : b->m) any_layers |= h->P.g.pml_cells > 0;
+    with_layers(any_layers, [&](auto lay) {
+      constexpr bool kLay = decltype(lay)::value;
+      if constexpr (sizeof(R) == 4) {
+        if (V == 4) {
+          k_efull_batch<4, R, kLay><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+          k_bstep_batch<4, R, kLay><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+        }
       }
-    }
-    if (V == 1) {
-      k_efull_batch<1, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
-      k_bstep_batch<1, R><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
-    }
+      if (V == 1) {
+        k_efull_batch<1, R, kLay><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+        k_bstep_batch<1, R, kLay><<<b->g_field.total, kThreads, 0, s>>>(cx, G);
+      }
+    });
     launched += 2;
   }
   if (b->g_window.total > 0) {
@@ -1181,11 +1243,34 @@ int batch_pushes(pic_batch_ctx *b, double *out) {
   return PIC_OK;
 }
 
+// Slots in use over all members (synchronous).
+int batch_slots(pic_batch_ctx *b, double *out) {
+  double sum = 0.0;
+  for (pic_ctx *h : b->m) {
+    unsigned long long n = 0;
+    const int rc = copy_out(h, h->P.off_nslots, &n, sizeof(n));
+    if (rc) return rc;
+    sum += (double)std::min<unsigned long long>(n, (unsigned long long)h->P.cap);
+  }
+  *out = sum;
+  return PIC_OK;
+}
+
 int batch_tune(pic_batch_ctx *b, int &n_steps) {
   static const long long kChunk[] = {1024, 2048, 4096, 2048};
   static const int kMult[] = {1, 1, 1, 2};
   constexpr int kCand = 4;
   if (n_steps < kCand * b->period) return PIC_OK;
+  // a push with too few particles measures nothing: tune once the members
+  // hold four particles per resident push thread (or a 64th of their
+  // pools, for batches too small to reach that)
+  {
+    PIC_CUDA(cudaStreamSynchronize(b->stream));
+    double slots = 0.0, cap = 0.0;
+    if (const int rs = batch_slots(b, &slots)) return rs;
+    for (pic_ctx *h : b->m) cap += (double)h->P.cap;
+    if (slots < std::min(4.0 * (double)b->push_blocks * kThreads, cap / 64.0)) return PIC_OK;
+  }
   if (b->tev.empty()) {
     b->tev.resize(2 * (size_t)b->period);
     for (auto &e : b->tev) PIC_CUDA(cudaEventCreate(&e));
@@ -1297,11 +1382,14 @@ int pic_batch_step(pic_batch b, int n_steps) {
   if (!b || n_steps < 0) return fail(PIC_EINVAL, "bad batch step arguments");
   for (pic_ctx *h : b->m)
     if (h->sticky) return fail(h->sticky, "a batch member holds a device error");
-  if (!b->tuned && batch_uniform(b)) {
-    const int rt = batch_tune(b, n_steps);
-    if (rt) return rt;
-  }
   while (n_steps > 0) {
+    // tune the batch's push once its members hold particles (checked before
+    // every period until then)
+    if (!b->tuned && batch_uniform(b) && b->push_blocks > 0) {
+      const int rt = batch_tune(b, n_steps);
+      if (rt) return rt;
+      if (n_steps <= 0) break;
+    }
     if (n_steps < b->period) {
       // tail: members step one by one on their streams, ordered after the batch stream
       PIC_CUDA(cudaEventRecord(b->ev[0], b->stream));

@@ -170,18 +170,18 @@ __global__ void __launch_bounds__(256) k_keldysh_batch(const Ctx<R> *ctx, int n,
   }
 }
 
-template <int V, class R>
+template <int V, class R, bool kLay>
 __global__ void __launch_bounds__(256, 3) k_efull_batch(const Ctx<R> *ctx, FlatGrid G) {
   int m;
   const Blk bk = flat_blk(G, m);
-  efull_body<V>(member_ctx(ctx, m), bk);
+  efull_body<V, kLay>(member_ctx(ctx, m), bk);
 }
 
-template <int V, class R>
+template <int V, class R, bool kLay>
 __global__ void __launch_bounds__(256) k_bstep_batch(const Ctx<R> *ctx, FlatGrid G) {
   int m;
   const Blk bk = flat_blk(G, m);
-  bstep_body<V, kFullRecord>(member_ctx(ctx, m).d, bk);
+  bstep_body<V, kFullRecord, kLay>(member_ctx(ctx, m).d, bk);
 }
 
 template <int V, class R>

@@ -97,10 +97,18 @@ struct Dev {
   R inv_e0sq;
   const R *ktab;                  // elliptic tables (K, E interleaved), or null
   int ntab;
+  // absorbing transverse layers of pml cells on each side of the x and y
+  // seams (0: periodic): the convolution terms of the layer derivatives
+  // (nfield each; order Ey/x, Ez/x, Ex/y, Ez/y, By/x, Bz/x, Bx/y, Bz/y) and
+  // the decay factors b per position: [0] along x, [1] along y, at integer
+  // positions over dt (E step) and half-integer ones over dt / 2 (B)
+  int pml;
+  R *psi[8];
+  const R *pml_bE[2], *pml_bB[2];
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
                                   // [4] pushes [8..11] Poynting fwd/bwd front, back
   // Poynting split: node planes (front, back), c eps0 dx dy dt, per-block
-  // partials (2 planes x kFluxBlocks x {fwd, bwd}) and the finished-block count
+  // partials (2 planes x blocks per plane x {fwd, bwd}) and the finished-block count
   int flux_k[2];
   double flux_scale;
   double *flux_part;

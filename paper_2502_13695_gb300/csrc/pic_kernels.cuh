@@ -62,6 +62,38 @@ __device__ __forceinline__ Blk blk_here() {
   return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
 }
 
+// Absorbing transverse layers (the paper's outflow faces, Sec. 3.1): a
+// convolutional PML (Roden and Gedney 2000; kappa = 1, alpha = 0) of
+// D.pml cells on each side of the periodic x and y seams.  A derivative df
+// of the curl inside them becomes df + psi with psi <- b psi + (b - 1) df;
+// b is 1 outside, where psi stays 0.
+enum { kPsiEYX = 0, kPsiEZX, kPsiEXY, kPsiEZY, kPsiBYX, kPsiBZX, kPsiBXY, kPsiBZY };
+
+template <class R>
+__device__ __forceinline__ bool pml_point(const Dev<R> &D, int i, int j) {
+  return D.pml > 0 && (i < D.pml || i >= D.nx - D.pml || j < D.pml || j >= D.ny - D.pml);
+}
+
+template <class R>
+__device__ __forceinline__ R pml_step(R *psi, R b, R df) {
+  const R p = b * *psi + (b - R(1)) * df;
+  *psi = p;
+  return df + p;
+}
+
+// A B point's layer derivative over the pass's half steps, all with the same
+// E: one convolution step (kMode 0: the opening half step), or two (the
+// closing half step of this step and the opening one of the next): d1 and
+// d2 for each.
+template <int kMode, class R>
+__device__ __forceinline__ void pml_two(R *psi, R b, R df, R &d1, R &d2) {
+  R p = b * *psi + (b - R(1)) * df;
+  d1 = df + p;
+  if (kMode != 0) p = b * p + (b - R(1)) * df;
+  d2 = df + p;
+  *psi = p;
+}
+
 template <class R>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double part[32];
@@ -329,11 +361,12 @@ __device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long
     // the frame reaches node planes ck - 2 .. ck + 3: mark ck for k_efull
     if (D.jtouch[ck] != jstamp) D.jtouch[ck] = jstamp;
     esirkepov(D, L.jpref[sp], co, off, cn, on);
-    if (cn[2] < 2 || cn[2] >= nz - 2) {
-      D.pcell[p] = -1;  // outflow through a z face
+    const int ni = wrap(cn[0], nx), nj = wrap(cn[1], ny);
+    if (cn[2] < 2 || cn[2] >= nz - 2 || pml_point(D, ni, nj)) {
+      D.pcell[p] = -1;  // outflow through a z face or into an absorbing layer
       continue;
     }
-    D.pcell[p] = (cn[2] * ny + wrap(cn[1], ny)) * nx + wrap(cn[0], nx);
+    D.pcell[p] = (cn[2] * ny + nj) * nx + ni;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       D.po[d][p] = on[d];
@@ -438,24 +471,27 @@ __device__ __noinline__ void record_intensity(const R *ex0, const R *ey0, const 
 // centres into it.
 enum { kPrime = 0, kFull = 1, kFullRecord = 2 };
 
+// t1 is the curl term of the first half step, t2 of the second (they differ
+// only inside the absorbing layers).
 template <int V, int kMode, class R>
-__device__ __forceinline__ void b_out(const Dev<R> &D, int d, long long o, const R *t) {
+__device__ __forceinline__ void b_out(const Dev<R> &D, int d, long long o, const R *t1,
+                                      const R *t2) {
   const R h = R(0.5) * D.dt;
   R b[V];
   ldv<V>(b, (kMode == kPrime ? D.B[d] : D.Bh[d]) + o);
 #pragma unroll
-  for (int l = 0; l < V; ++l) b[l] -= h * t[l];
+  for (int l = 0; l < V; ++l) b[l] -= h * t1[l];
   if constexpr (kMode == kPrime) {
     stv<V>(D.Bh[d] + o, b);
   } else {
     stv<V>(D.B[d] + o, b);
 #pragma unroll
-    for (int l = 0; l < V; ++l) b[l] -= h * t[l];
+    for (int l = 0; l < V; ++l) b[l] -= h * t2[l];
     stv<V>(D.Bh[d] + o, b);
   }
 }
 
-template <int V, int kMode, class R>
+template <int V, int kMode, bool kLay = false, class R>
 __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
   const int nx = D.nx, ny = D.ny, nxy = D.nxy;
   // the E step of this pass has read the current: count the pass and clear
@@ -471,14 +507,33 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
   const long long o = (long long)k * nxy + r;
   const long long oj = (j == ny - 1) ? o - (long long)(ny - 1) * nx : o + nx;
   const long long ov = (i + V == nx) ? o + V - nx : o + V;  // x + 1 of the last point
-  R ex[V], ey[V + 1], exj[V], t[V];
+  R ex[V], ey[V + 1], exj[V], t[V], t2[V];
   ldv<V>(ex, D.E[0] + o);
   ldv<V>(ey, D.E[1] + o);
   ey[V] = D.E[1][ov];
   ldv<V>(exj, D.E[0] + oj);
+  // a thread with a point in the absorbing layers takes the layer terms
+  // (kLay: instantiated for grids that have them)
+  const bool lay = kLay && (pml_point(D, i, j) || pml_point(D, i + V - 1, j));
 #pragma unroll
   for (int l = 0; l < V; ++l) t[l] = (ey[l + 1] - ey[l]) * D.idx - (exj[l] - ex[l]) * D.idy;
-  b_out<V, kMode>(D, 2, o, t);
+  if (lay) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      t2[l] = t[l];
+      if (pml_point(D, i + l, j)) {
+        R x1, x2, y1, y2;
+        pml_two<kMode>(D.psi[kPsiBZX] + o + l, D.pml_bB[0][i + l], (ey[l + 1] - ey[l]) * D.idx, x1,
+                       x2);
+        pml_two<kMode>(D.psi[kPsiBZY] + o + l, D.pml_bB[1][j], (exj[l] - ex[l]) * D.idy, y1, y2);
+        t[l] = x1 - y1;
+        t2[l] = x2 - y2;
+      }
+    }
+    b_out<V, kMode>(D, 2, o, t, t2);
+  } else {
+    b_out<V, kMode>(D, 2, o, t, t);
+  }
   if (k < D.nz) {
     R ez[V + 1], ezj[V], eyk[V], exk[V];
     ldv<V>(ez, D.E[2] + o);
@@ -488,10 +543,41 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
     ldv<V>(exk, D.E[0] + o + nxy);
 #pragma unroll
     for (int l = 0; l < V; ++l) t[l] = (ezj[l] - ez[l]) * D.idy - (eyk[l] - ey[l]) * D.idz;
-    b_out<V, kMode>(D, 0, o, t);
+    if (lay) {
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        t2[l] = t[l];
+        if (pml_point(D, i + l, j)) {
+          R y1, y2;
+          pml_two<kMode>(D.psi[kPsiBXY] + o + l, D.pml_bB[1][j], (ezj[l] - ez[l]) * D.idy, y1, y2);
+          const R dz = (eyk[l] - ey[l]) * D.idz;
+          t[l] = y1 - dz;
+          t2[l] = y2 - dz;
+        }
+      }
+      b_out<V, kMode>(D, 0, o, t, t2);
+    } else {
+      b_out<V, kMode>(D, 0, o, t, t);
+    }
 #pragma unroll
     for (int l = 0; l < V; ++l) t[l] = (exk[l] - ex[l]) * D.idz - (ez[l + 1] - ez[l]) * D.idx;
-    b_out<V, kMode>(D, 1, o, t);
+    if (lay) {
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        t2[l] = t[l];
+        if (pml_point(D, i + l, j)) {
+          R x1, x2;
+          pml_two<kMode>(D.psi[kPsiBYX] + o + l, D.pml_bB[0][i + l], (ez[l + 1] - ez[l]) * D.idx, x1,
+                         x2);
+          const R dz = (exk[l] - ex[l]) * D.idz;
+          t[l] = dz - x1;
+          t2[l] = dz - x2;
+        }
+      }
+      b_out<V, kMode>(D, 1, o, t, t2);
+    } else {
+      b_out<V, kMode>(D, 1, o, t, t);
+    }
     if constexpr (kMode == kFullRecord) {
       const int every = D.imax_every;
       if (every > 0 && ((unsigned)*D.step + 1u) % (unsigned)every == 0u)
@@ -501,9 +587,9 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
   }
 }
 
-template <int V, int kMode, class R>
+template <int V, int kMode, class R, bool kLay = false>
 __global__ void __launch_bounds__(256) k_bstep(Dev<R> D) {
-  bstep_body<V, kMode>(D, blk_here());
+  bstep_body<V, kMode, kLay>(D, blk_here());
 }
 
 template <class R>
@@ -559,7 +645,7 @@ __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) 
 // the polarisation current, Silver-Mueller faces at k = 0 (with the incident field) and k = nz,
 // Joule work J.(E^n + E^{n+1})/2, J cleared for the next deposit.  Three
 // blocks per SM (80 registers) measured faster than two at 100 registers.
-template <int V, class R>
+template <int V, bool kLay = false, class R>
 __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
   const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
@@ -602,6 +688,16 @@ __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
     for (int l = 0; l < V; ++l) {
       dBz_dy[l] = (bz[l + 1] - bzj[l]) * D.idy;
       dBz_dx[l] = (bz[l + 1] - bz[l]) * D.idx;
+    }
+    // absorbing layers: the convolution terms of the x and y derivatives
+    const bool lay = kLay && (pml_point(D, i, j) || pml_point(D, i + V - 1, j));
+    if (lay) {
+#pragma unroll
+      for (int l = 0; l < V; ++l)
+        if (pml_point(D, i + l, j)) {
+          dBz_dy[l] = pml_step(D.psi[kPsiEXY] + o + l, D.pml_bE[1][j], dBz_dy[l]);
+          dBz_dx[l] = pml_step(D.psi[kPsiEYX] + o + l, D.pml_bE[0][i + l], dBz_dx[l]);
+        }
     }
     const int L = k < nz ? D.layer_of_plane[k] : -1;
     const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
@@ -692,10 +788,22 @@ __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
       const R byp = D.Bh[1][omv];
       ldv<V>(bxj, D.Bh[0] + omj);
       ldv<V>(ez0, D.E[2] + o);
+      R dby_dx[V], dbx_dy[V];
 #pragma unroll
-      for (int l = 0; l < V; ++l)
-        az[l] = c2dt * ((by[l] - (l ? by[l - 1] : byp)) * D.idx - (bx[l] - bxj[l]) * D.idy) -
-                dtie * jz[l];
+      for (int l = 0; l < V; ++l) {
+        dby_dx[l] = (by[l] - (l ? by[l - 1] : byp)) * D.idx;
+        dbx_dy[l] = (bx[l] - bxj[l]) * D.idy;
+      }
+      if (lay) {
+#pragma unroll
+        for (int l = 0; l < V; ++l)
+          if (pml_point(D, i + l, j)) {
+            dby_dx[l] = pml_step(D.psi[kPsiEZX] + o + l, D.pml_bE[0][i + l], dby_dx[l]);
+            dbx_dy[l] = pml_step(D.psi[kPsiEZY] + o + l, D.pml_bE[1][j], dbx_dy[l]);
+          }
+      }
+#pragma unroll
+      for (int l = 0; l < V; ++l) az[l] = c2dt * (dby_dx[l] - dbx_dy[l]) - dtie * jz[l];
       if (m >= 0) {
         R pz[V], qz[V];
         ldv<V>(pz, D.P[2] + m);
@@ -718,9 +826,9 @@ __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
   if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
 }
 
-template <int V, class R>
+template <int V, class R, bool kLay = false>
 __global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
-  efull_body<V>(X, blk_here());
+  efull_body<V, kLay>(X, blk_here());
 }
 
 // ---------------------------------------------------------------------------
@@ -1182,8 +1290,8 @@ __global__ void k_init_material(Ctx<R> X) {
 }
 
 // End of a step: the Poynting split at the two flux planes (blockIdx.y = 0
-// front, 1 back; kFluxBlocks blocks per plane over a fixed partition of its
-// points) and the step counter.  At node plane k the transverse E (Ex and
+// front, 1 back; a fixed number of blocks per plane over a fixed partition
+// of its points) and the step counter.  At node plane k the transverse E (Ex and
 // Ey of the plane) is paired with B averaged over planes k - 1 and k (By and
 // Bx at k - 1/2 and k + 1/2, the same transverse positions) and split into
 // the waves going along +z, ((Ex + c By) / 2, (Ey - c Bx) / 2), and along -z,
@@ -1192,7 +1300,9 @@ __global__ void k_init_material(Ctx<R> X) {
 // nothing waits) adds them up in a fixed order (one warp's loads and a
 // shuffle tree) times c eps0 dx dy dt to the time integrals, advances the
 // step and resets the count.
-constexpr int kFluxBlocks = 16;
+// Blocks per flux plane: one field point per thread (ceil(nxy / 256)), at
+// most kFluxMaxBlocks, so each thread makes one round trip to memory.
+constexpr int kFluxMaxBlocks = 256;
 
 template <class R>
 __device__ __forceinline__ void flux_advance_body(const Dev<R> &D, Blk bk) {

@@ -50,7 +50,7 @@ class Grid(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("pool_factor", ctypes.c_double),
                 ("keldysh_terms", ctypes.c_int), ("sort_interval", ctypes.c_int),
                 ("imax_every", ctypes.c_int), ("coll_every", ctypes.c_int),
-                ("elliptic_table", ctypes.c_int), ("reserved_grid", ctypes.c_int)]
+                ("elliptic_table", ctypes.c_int), ("pml_cells", ctypes.c_int)]
 
 
 class Layer(ctypes.Structure):
@@ -186,6 +186,7 @@ def c_structs(cfg: dict):
     g.imax_every = cfg.get("imax_every", 0)
     g.coll_every = cfg.get("coll_every", 0)
     g.elliptic_table = cfg.get("elliptic_table", 0)
+    g.pml_cells = cfg.get("pml_cells", 0)
     layers = (Layer * max(1, len(cfg["layers"])))()
     for n, ly in enumerate(cfg["layers"]):
         L = layers[n]
@@ -221,6 +222,7 @@ def checkpoint_config(path: str) -> dict:
                pool_factor=g.pool_factor, keldysh_terms=g.keldysh_terms,
                sort_interval=g.sort_interval, imax_every=g.imax_every,
                coll_every=g.coll_every, elliptic_table=g.elliptic_table,
+               pml_cells=g.pml_cells,
                seed=int(seed.value), step=int(step.value))
     cfg["layers"] = [
         {f: getattr(layers[q], f) for f in (
