@@ -102,7 +102,10 @@ typedef struct {
                           kappa 1, alpha 0, conductivity sigma_max (d / L)^3 at
                           depth d, sigma_max = 0.8 * 4 / (eta0 * cell size)),
                           and a particle that ends a push inside them leaves
-                          the simulation, as through the z faces */
+                          the simulation, as through the z faces.  Their
+                          convolution state lives in the arena (checkpoints
+                          keep it); pic_set_fields / pic_set_state leave it
+                          as the run left it */
 } pic_grid;
 
 /* One dielectric layer: z cells [z0, z1) over the whole transverse plane.

@@ -67,7 +67,8 @@ struct Plan {
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
   size_t off_flux_part, off_flux_cnt;
   size_t off_ktab;               // elliptic tables (elliptic_table > 0)
-  size_t off_psi[8];             // absorbing-layer convolution terms (pml_cells > 0)
+  size_t off_psi[12];            // absorbing-layer convolution terms (pml_cells > 0):
+                                 // eight, then the B terms after a closing half step
   size_t off_pmlb;               // their decay factors: E along x, y; B along x, y
   std::vector<double> pmlb;      // the same factors on the host
   std::vector<double> ktab;      // the same tables on the host, K and E interleaved
@@ -243,7 +244,7 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
   // decay factors b = exp(-sigma h / eps0) of each position, E (integer
   // positions, h = dt) then B (half-integer ones, h = dt / 2), x then y
   const bool pml = g.pml_cells > 0;
-  for (int q = 0; q < 8; ++q) P.off_psi[q] = take(pml ? P.nfield * R : 1);
+  for (int q = 0; q < 12; ++q) P.off_psi[q] = take(pml ? P.nfield * R : 1);
   P.off_pmlb = take((size_t)2 * (g.nx + g.ny) * R);
   P.pmlb.clear();
   if (pml) {
@@ -494,6 +495,7 @@ void bind(pic_ctx *h) {
   D.ntab = P.g.elliptic_table;
   D.pml = P.g.pml_cells;
   for (int q = 0; q < 8; ++q) D.psi[q] = D.pml ? (R *)(A + P.off_psi[q]) : nullptr;
+  for (int q = 0; q < 4; ++q) D.psi_close[q] = D.pml ? (R *)(A + P.off_psi[8 + q]) : nullptr;
   {
     const R *b = (const R *)(A + P.off_pmlb);
     D.pml_bE[0] = b;

@@ -104,6 +104,9 @@ struct Dev {
   // positions over dt (E step) and half-integer ones over dt / 2 (B)
   int pml;
   R *psi[8];
+  R *psi_close[4];  // the B terms after the closing half step of the last
+                    // fused pass: a re-primed Bh (after a host write) takes
+                    // the opening half step's convolution from here
   const R *pml_bE[2], *pml_bB[2];
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
                                   // [4] pushes [8..11] Poynting fwd/bwd front, back

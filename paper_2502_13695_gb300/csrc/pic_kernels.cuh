@@ -82,16 +82,25 @@ __device__ __forceinline__ R pml_step(R *psi, R b, R df) {
 }
 
 // A B point's layer derivative over the pass's half steps, all with the same
-// E: one convolution step (kMode 0: the opening half step), or two (the
-// closing half step of this step and the opening one of the next): d1 and
-// d2 for each.
+// E: d1 and d2 for the closing half step of this step and the opening one of
+// the next (two convolution steps; the state after the first is kept in
+// psi_c), or, for kMode 0, the opening half step alone, from the state that
+// the last closing half step left in psi_c (so a Bh primed again after a
+// host write advances the convolution once, as the opening half step does).
 template <int kMode, class R>
-__device__ __forceinline__ void pml_two(R *psi, R b, R df, R &d1, R &d2) {
-  R p = b * *psi + (b - R(1)) * df;
-  d1 = df + p;
-  if (kMode != 0) p = b * p + (b - R(1)) * df;
-  d2 = df + p;
-  *psi = p;
+__device__ __forceinline__ void pml_two(R *psi, R *psi_c, R b, R df, R &d1, R &d2) {
+  if constexpr (kMode == 0) {
+    const R p = b * *psi_c + (b - R(1)) * df;
+    d1 = d2 = df + p;
+    *psi = p;
+  } else {
+    const R p1 = b * *psi + (b - R(1)) * df;
+    d1 = df + p1;
+    *psi_c = p1;
+    const R p2 = b * p1 + (b - R(1)) * df;
+    d2 = df + p2;
+    *psi = p2;
+  }
 }
 
 template <class R>
@@ -523,9 +532,10 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
       t2[l] = t[l];
       if (pml_point(D, i + l, j)) {
         R x1, x2, y1, y2;
-        pml_two<kMode>(D.psi[kPsiBZX] + o + l, D.pml_bB[0][i + l], (ey[l + 1] - ey[l]) * D.idx, x1,
-                       x2);
-        pml_two<kMode>(D.psi[kPsiBZY] + o + l, D.pml_bB[1][j], (exj[l] - ex[l]) * D.idy, y1, y2);
+        pml_two<kMode>(D.psi[kPsiBZX] + o + l, D.psi_close[kPsiBZX - kPsiBYX] + o + l,
+                       D.pml_bB[0][i + l], (ey[l + 1] - ey[l]) * D.idx, x1, x2);
+        pml_two<kMode>(D.psi[kPsiBZY] + o + l, D.psi_close[kPsiBZY - kPsiBYX] + o + l,
+                       D.pml_bB[1][j], (exj[l] - ex[l]) * D.idy, y1, y2);
         t[l] = x1 - y1;
         t2[l] = x2 - y2;
       }
@@ -549,7 +559,8 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
         t2[l] = t[l];
         if (pml_point(D, i + l, j)) {
           R y1, y2;
-          pml_two<kMode>(D.psi[kPsiBXY] + o + l, D.pml_bB[1][j], (ezj[l] - ez[l]) * D.idy, y1, y2);
+          pml_two<kMode>(D.psi[kPsiBXY] + o + l, D.psi_close[kPsiBXY - kPsiBYX] + o + l,
+                         D.pml_bB[1][j], (ezj[l] - ez[l]) * D.idy, y1, y2);
           const R dz = (eyk[l] - ey[l]) * D.idz;
           t[l] = y1 - dz;
           t2[l] = y2 - dz;
@@ -567,8 +578,8 @@ __device__ __forceinline__ void bstep_body(const Dev<R> &D, Blk bk) {
         t2[l] = t[l];
         if (pml_point(D, i + l, j)) {
           R x1, x2;
-          pml_two<kMode>(D.psi[kPsiBYX] + o + l, D.pml_bB[0][i + l], (ez[l + 1] - ez[l]) * D.idx, x1,
-                         x2);
+          pml_two<kMode>(D.psi[kPsiBYX] + o + l, D.psi_close[0] + o + l, D.pml_bB[0][i + l],
+                         (ez[l + 1] - ez[l]) * D.idx, x1, x2);
           const R dz = (exk[l] - ex[l]) * D.idz;
           t[l] = dz - x1;
           t2[l] = dz - x2;

@@ -276,8 +276,9 @@ def vacuum_packet(cfg, axis, pol, sign=1, center=None, width=8.0, z_width=8.0, l
 # The paper's own geometry (Sec. 3): Table 1 materials with a static
 # permittivity (Sec. 2.3), 7 fs sine-squared pulse with a 4.65 um spot,
 # 40 nm transverse cells, 24 fs of simulated time.  The laser runs along z
-# here (the paper's y); x and y stay periodic where the paper has outflow
-# boundaries, and the paper's 1000 neutrals per cell are reduced to ppc.
+# here (the paper's y).  The paper's transverse outflow boundaries are
+# absorbing layers of PAPER_PML cells added on each side of its 240 x 240
+# cells, and its 1000 neutrals per cell are reduced to ppc.
 # --------------------------------------------------------------------------
 NA = 6.02214076e23
 SIO2_TABLE1 = dict(n_index=1.477, gap_eV=9.0, me_star=0.6, mh_star=8.0,
@@ -287,6 +288,9 @@ HFO2_TABLE1 = dict(n_index=2.021, gap_eV=5.7, me_star=1.09, mh_star=1.12,
                    n_mol=9.68e6 / 210.49 * NA, omega0_eV=math.inf, damping=0.0,
                    mol_mass_amu=210.49, e_melt=10.7e9, e_boil=49.9e9, e_dissoc=54e9)
 T_SIN2_7FS = 7e-15 / (2.0 * math.acos(2.0 ** -0.25) / math.pi)  # full envelope duration
+
+
+PAPER_PML = 8
 
 
 def paper_pulse(fluence_Jcm2):
@@ -301,15 +305,17 @@ def paper_steps(cfg, t_end=24e-15):
 
 
 def paper_silica(fluence_Jcm2=1.2, ppc=2, collisions=False, precision="fp32", seed=9):
-    """Bulk fused silica (Sec. 3.1, Fig. 1a): 9.6 um x 9.6 um at 40 nm, along
-    the laser 0.1 um of vacuum and 0.9 um of silica at 5 nm (plus the two-cell
-    outflow bands), 300 K."""
+    """Bulk fused silica (Sec. 3.1, Fig. 1a): 9.6 um x 9.6 um at 40 nm inside
+    the absorbing transverse layers, along the laser 0.1 um of vacuum and
+    0.9 um of silica at 5 nm (plus the two-cell outflow bands), 300 K."""
     T300 = 300.0 * KB_EV_PER_K
-    cfg = grid(240, 240, 206, 40e-9, [layer(22, 202, SIO2_TABLE1, ppc, T300)],
+    n = 240 + 2 * PAPER_PML
+    cfg = grid(n, n, 206, 40e-9, [layer(22, 202, SIO2_TABLE1, ppc, T300)],
                paper_pulse(fluence_Jcm2), seed=seed, precision=precision, pool_factor=2.0,
-               dz=5e-9, name="paper-silica-240x240x206-5nm")
+               dz=5e-9, name="paper-silica-240x240x206-5nm-pml8")
     cfg["coll_every"] = 1 if collisions else 0
     cfg["elliptic_table"] = 1000  # Sec. 2.1: K and E read from 1000-point tables
+    cfg["pml_cells"] = PAPER_PML
     cfg["steps"] = paper_steps(cfg)
     return cfg
 
@@ -327,9 +333,11 @@ def paper_mirror(fluence_Jcm2=0.7, pairs=5, ppc=2, collisions=False, precision="
         for mat in (HFO2_TABLE1, SIO2_TABLE1):
             lay.append(layer(z, z + layer_cells(mat["n_index"], 0.25, d), mat, ppc, T300))
             z = lay[-1]["z1"]
-    cfg = grid(240, 240, z + 4, 40e-9, lay, paper_pulse(fluence_Jcm2), seed=seed,
+    n = 240 + 2 * PAPER_PML
+    cfg = grid(n, n, z + 4, 40e-9, lay, paper_pulse(fluence_Jcm2), seed=seed,
                precision=precision, pool_factor=2.0, dz=d, name=f"paper-mirror-{pairs}pairs")
     cfg["coll_every"] = 1 if collisions else 0
     cfg["elliptic_table"] = 1000
+    cfg["pml_cells"] = PAPER_PML
     cfg["steps"] = paper_steps(cfg)
     return cfg

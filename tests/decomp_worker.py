@@ -2,7 +2,8 @@
 tests/test_decomp.py and tests/test_gpu_decomp.py with the torchrun
 environment variables set): the slab of the shared test state advanced by
 an FP64 engine, the oracle or (third argument "gpu") the CUDA library on
-cuda:0, exchanging over gloo; writes its owned fields and particles to
+cuda:0, exchanging over gloo, with the fourth argument's cells of absorbing
+transverse layers (default 0); writes its owned fields and particles to
 <out>/rank<r>.npz."""
 import os
 import sys
@@ -23,9 +24,10 @@ from paper_2502_13695_gb300 import decomp  # noqa: E402
 def main():
     out, steps = sys.argv[1], int(sys.argv[2])
     engine = sys.argv[3] if len(sys.argv) > 3 else "oracle"
+    pml = int(sys.argv[4]) if len(sys.argv) > 4 else 0
     rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
     dist.init_process_group("gloo")
-    cfg, F, P = case()
+    cfg, F, P = case(pml)
     if engine == "gpu":
         import torch
         from paper_2502_13695_gb300 import pic

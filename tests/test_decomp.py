@@ -31,7 +31,7 @@ def test_slab_bounds():
         decomp.slab_bounds(10, 2)
 
 
-def run_ranks(tmp_path, world, engine="oracle"):
+def run_ranks(tmp_path, world, engine="oracle", pml=0):
     """Run the decomposition worker on `world` gloo ranks; returns nothing,
     the ranks write their results under tmp_path."""
     port = _free_port()
@@ -39,7 +39,8 @@ def run_ranks(tmp_path, world, engine="oracle"):
     for r in range(world):
         env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(world),
                    MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
-        procs.append(subprocess.Popen([sys.executable, WORKER, str(tmp_path), str(STEPS), engine],
+        procs.append(subprocess.Popen([sys.executable, WORKER, str(tmp_path), str(STEPS), engine,
+                                       str(pml)],
                                       env=env, text=True, stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE))
     try:
@@ -52,12 +53,12 @@ def run_ranks(tmp_path, world, engine="oracle"):
         assert p.returncode == 0, e[-3000:]
 
 
-def check_against_one_domain(oracle_mod, tmp_path, world):
+def check_against_one_domain(oracle_mod, tmp_path, world, pml=0):
     """The ranks' owned planes and particles against the single-domain oracle
     run of the same state."""
     from decomp_case import case
     from paper_2502_13695_gb300 import decomp
-    cfg, F, P = case()
+    cfg, F, P = case(pml)
     s = oracle_mod.Sim(cfg)
     s.set_fields(F)
     s.set_particles(P)
@@ -101,7 +102,10 @@ def check_against_one_domain(oracle_mod, tmp_path, world):
     slab_of = lambda k: int(np.searchsorted(b, k, side="right")) - 1  # noqa: E731
     start_slab = {int(i): slab_of(k) for i, k in zip(P["id"], k_start)}
     crossed = sum(1 for i, q in ids.items() if start_slab[i] != slab_of(k_end[q]))
-    assert crossed > 20
+    # (the layers take most of the particles: four in ten columns are inside)
+    assert crossed > (20 if pml == 0 else 10)
+    if pml:
+        assert len(po["id"]) < len(P["id"]) // 2
     for face in b[1:-1]:
         assert np.max(np.abs(G[9, face - 2:face + 2])) > 0
 
@@ -110,3 +114,10 @@ def check_against_one_domain(oracle_mod, tmp_path, world):
 def test_ranks_match_one_domain(oracle_mod, tmp_path, world):
     run_ranks(tmp_path, world)
     check_against_one_domain(oracle_mod, tmp_path, world)
+
+
+def test_ranks_match_one_domain_with_absorbing_layers(oracle_mod, tmp_path):
+    """The transverse layers act within each slab's planes (their convolution
+    terms and the particle outflow), so the slabs still equal one domain."""
+    run_ranks(tmp_path, 2, pml=1)
+    check_against_one_domain(oracle_mod, tmp_path, 2, pml=1)

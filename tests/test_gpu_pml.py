@@ -5,8 +5,9 @@ FP64 runs follow the oracle to roundoff: the vector-potential vacuum packets
 of the oracle's pins, in both polarisations and along x and y, and a full
 run with material, ionisation, a focused pulse and particles leaving
 through the layers.  FP32 runs stay within FP32 rounding of the packet and
-absorb it as well.  Batches with and without layers, and a checkpoint taken
-inside the layers' run, continue as the uninterrupted run does.
+absorb it as well.  Host writes of the fields mid-run, batches with and
+without layers, and a checkpoint taken inside the layers' run continue as
+the oracle's or the uninterrupted run does.
 """
 import os
 
@@ -60,6 +61,31 @@ def test_vacuum_packet_through_layers_fp64(pic, oracle_mod, axis, pol):
         assert np.linalg.norm(Fg[:6] - Fo[:6]) <= 1e-12 * scale, n
         assert abs(g.diagnostics()["U_field"] - o.diagnostics()["U_field"]) <= 1e-11 * U0, n
     assert g.diagnostics()["U_field"] < (5e-5 if pol == "t" else 8e-4) * U0
+    g.close()
+
+
+def test_host_field_writes_inside_a_layers_run(pic, oracle_mod):
+    """A host write of E and B makes the library prime Bh again; the layers'
+    convolution state then takes the opening half step once, from where the
+    last closing half step left it, as the oracle's run does."""
+    cfg = _box(0, 8)
+    F = wl.vacuum_packet(cfg, 0, "z")
+    o, g = oracle_mod.Sim(cfg), pic.Simulation(cfg)
+    o.set_fields(F)
+    g.set_fields(F)
+    scale = np.linalg.norm(F[:6])
+    for _ in range(3):
+        o.step(20)
+        g.step(20)
+        G = g.fields()
+        G[4, 10:12] *= 1.5  # a write the oracle gets too
+        Fo = o.fields()
+        Fo[4, 10:12] *= 1.5
+        g.set_fields(G)
+        o.set_fields(Fo)
+    o.step(30)
+    g.step(30)
+    assert np.linalg.norm(g.fields()[:6] - o.fields()[:6]) <= 1e-12 * scale
     g.close()
 
 
