@@ -9,13 +9,17 @@
  *
  * Plain loops in the order the step is defined, all arithmetic in double:
  *   particle pass  : TSC gather (Sec. 4.1 "shape function"), relativistic Boris
- *                    push, Esirkepov charge-conserving deposit, z outflow
+ *                    push, Esirkepov charge-conserving deposit, z outflow and
+ *                    outflow into the absorbing transverse layers
  *   field pass     : Yee update with a Lorentz polarisation current (Sec. 2.3,
  *                    refraction) advanced by a Crank-Nicolson oscillator step,
- *                    laser injected through a Silver-Mueller boundary (Sec. 3)
+ *                    laser injected through a Silver-Mueller boundary (Sec. 3),
+ *                    optional convolutional PML layers at the x and y seams
+ *                    (the outflow transverse faces of Sec. 3.1)
  *   amplitude      : maximum of |E| over the last optical cycle (Sec. 2.1,
  *                    rolling window)
- *   Keldysh rate   : Sec. 2.1, Eqs. for x, W and Q, first 500 terms of Q
+ *   Keldysh rate   : Sec. 2.1, Eqs. for x, W and Q, first 500 terms of Q;
+ *                    K and E in situ or from N-point tables (Sec. 2.1)
  *   ionisation     : one event per molecule (Sec. 2.1), electron + hole with
  *                    the Table 1 effective masses (Sec. 3.2)
  *   diagnostics    : energies, TSC number and energy density (Sec. 4.1-4.2),
