@@ -707,7 +707,8 @@ int enqueue(pic_ctx *h, int mask) {
   }
   if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
     prof_begin(h, PIC_PROF_IONIZE);
-    k_ionize<R><<<dim3(grid_blocks(P.nxy), P.n_mplanes), kThreads, 0, s>>>(X);
+    k_ionize<R><<<dim3(grid_blocks((P.nxy + kIonizeCells - 1) / kIonizeCells), P.n_mplanes),
+                  kThreads, 0, s>>>(X);
     prof_end(h);
     h->launches += 1;
   }
@@ -1029,7 +1030,8 @@ int batch_tables(pic_batch_ctx *b) {
     sb[q] = SortBufs{(unsigned int *)(h->arena + P.off_cnt), (unsigned int *)(h->arena + P.off_bsum),
                      (unsigned long long *)(h->arena + P.off_total), P.ncell, P.nb_scan, 0};
     const int V = h->field_v;
-    const int gxs[6] = {grid_blocks(P.nxy / V), grid_blocks(P.nxy / V), grid_blocks(P.nxy),
+    const int gxs[6] = {grid_blocks(P.nxy / V), grid_blocks(P.nxy / V),
+                        grid_blocks((P.nxy + kIonizeCells - 1) / kIonizeCells),
                         P.flux_blocks, P.nb_scan, grid_blocks(P.ncell)};
     const long long gys[6] = {P.g.nz + 1, P.n_mplanes, P.n_mplanes, 2, 1, 1};
     for (int k = 0; k < 6; ++k) {

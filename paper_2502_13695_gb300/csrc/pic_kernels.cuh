@@ -1098,14 +1098,17 @@ __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32
   }
 }
 
-// One thread per material cell (a thread per slot pair measured twice as
-// slow: four threads repeat the cell's index and threshold loads).  FP32:
-// six blocks per SM (40 registers): the kernel waits on its loads, and 64
-// registers (four blocks) measured 22% slower.
+// Each thread takes kIonizeCells material cells of a plane, a grid row of
+// threads apart, and loads the next cell's three words while it draws for
+// the current one.  (A thread per slot pair measured twice as
+// slow as a thread per cell: four threads repeat the cell's index and
+// threshold loads.)  FP32: six blocks per SM (40 registers): the kernel
+// waits on its loads, and 64 registers (four blocks) measured 22% slower.
+constexpr int kIonizeCells = 4;
+
 template <class R>
 __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
-  const int r = bk.x * blockDim.x + threadIdx.x;  // cell in material plane bk.y
   const int mp = bk.y;
   {
     // only cells at or above the skip amplitude can have a nonzero
@@ -1116,129 +1119,142 @@ __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
         (mp + 1 == bk.gy || D.hot[mp + 1] != stamp))
       return;
   }
-  const long long m = (long long)mp * D.nxy + r;
-  const bool active = r < D.nxy;
+  const int nx = D.nx, nxy = D.nxy;
   const long long step = *D.step;
-  uint32_t alive = 0, ion = 0;
-  int i = 0, j = 0;
   const int k = D.kplane[mp], L = D.layer_of_plane[k];
-  uint32_t c = 0;
-  R t1 = R(0);
-  // the cell's three words are loaded together (one round trip)
-  unsigned long long Town = 0;
-  uint32_t leave = 0;
-  if (active) {
-    alive = D.alive[m];
-    Town = D.T[m];
-    leave = D.leave_step[m];
+  const long long mbase = (long long)mp * nxy;
+  const int stride = bk.gx * blockDim.x;
+  R t1;
+  if constexpr (sizeof(R) == 4)
+    t1 = R((int)(step + 1)) * D.dt;
+  else
+    t1 = R((double)(step + 1) * D.dt_d);
+  // the cell's three words, loaded one cell ahead
+  uint32_t alive_n = 0, leave_n = 0;
+  unsigned long long T_n = 0;
+  {
+    const int r = bk.x * blockDim.x + threadIdx.x;
+    if (r < nxy) {
+      alive_n = D.alive[mbase + r];
+      T_n = D.T[mbase + r];
+      leave_n = D.leave_step[mbase + r];
+    }
   }
-  if (alive) {
-    const int nx = D.nx, nxy = D.nxy;
-    j = r / nx;
-    i = r - j * nx;
-    c = (uint32_t)((long long)k * nxy + r);
-    // neutrals that may have left the birth cell by t^{n+1}: their own
-    // leave step (64-step units, rounded down) has been reached
-    uint32_t exc = 0;
-    if ((unsigned long long)(step + 1) >= (unsigned long long)leave) {
-      const uint16_t *ls = X.leave16 + m * X.ppc_max;
-      for (uint32_t bits = alive; bits; bits &= bits - 1) {
+  for (int r0 = bk.x * blockDim.x; r0 < nxy; r0 += stride) {
+    const int r = r0 + threadIdx.x;
+    const long long m = mbase + r;
+    const uint32_t alive = alive_n, leave = leave_n;
+    const unsigned long long Town = T_n;
+    if (r + stride < nxy) {
+      alive_n = D.alive[m + stride];
+      T_n = D.T[m + stride];
+      leave_n = D.leave_step[m + stride];
+    }
+    uint32_t ion = 0, c = 0;
+    int i = 0, j = 0;
+    if (alive) {
+      j = r / nx;
+      i = r - j * nx;
+      c = (uint32_t)((long long)k * nxy + r);
+      // neutrals that may have left the birth cell by t^{n+1}: their own
+      // leave step (64-step units, rounded down) has been reached
+      uint32_t exc = 0;
+      if ((unsigned long long)(step + 1) >= (unsigned long long)leave) {
+        const uint16_t *ls = X.leave16 + m * X.ppc_max;
+        for (uint32_t bits = alive; bits; bits &= bits - 1) {
+          const uint32_t s = __ffs(bits) - 1;
+          if ((unsigned long long)(step + 1) >= 64ull * ls[s]) exc |= 1u << s;
+        }
+      }
+      // birth-cell threshold for every other alive neutral: one block per
+      // group of eight slots decides on the top 16 bits; the rare ties draw
+      // their low 48 bits afterwards
+      if (Town == ~0ull) {
+        ion = alive & ~exc;
+      } else if (Town != 0ull) {
+        const uint32_t th = (uint32_t)(Town >> 48);
+        uint32_t tie = 0;
+        for (uint32_t bits = alive & ~exc; bits;) {
+          const uint32_t g = (uint32_t)(__ffs(bits) - 1) >> 3;
+          const uint32_t gm = 0xFFu << (8 * g);
+          uint32_t lt, eq;
+          ion_compare8(draw(D.seed, (uint32_t)step, c, g, kStreamIon), th, lt, eq);
+          ion |= bits & gm & (lt << (8 * g));
+          tie |= bits & gm & (eq << (8 * g));
+          bits &= ~gm;
+        }
+        for (; tie; tie &= tie - 1) {
+          const uint32_t s = __ffs(tie) - 1;
+          const uint4 b = draw(D.seed, (uint32_t)step, c, s, kStreamIonLow);
+          const unsigned long long lo48 = ((unsigned long long)(b.y & 0xFFFFu) << 32) | b.x;
+          if (lo48 < (Town & 0xFFFFFFFFFFFFull)) ion |= 1u << s;
+        }
+      }
+      // the few neutrals that may have crossed a face: exact position,
+      // threshold of that cell
+      const R sig = X.lr[L].sig_v;
+      for (uint32_t bits = exc; bits; bits &= bits - 1) {
         const uint32_t s = __ffs(bits) - 1;
-        if ((unsigned long long)(step + 1) >= 64ull * ls[s]) exc |= 1u << s;
+        Neutral<R> nu;
+        const unsigned long long Tuse =
+            neutral_at(D, sig, i, j, k, c, s, t1, nu)
+                ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+                : 0ull;
+        if (Tuse == 0ull) continue;
+        const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 3, kStreamIon);
+        if (ionises(ion_h16(w, s), Tuse, D.seed, (uint32_t)step, c, s)) ion |= 1u << s;
       }
     }
-    // birth-cell threshold for every other alive neutral: one block per
-    // group of eight slots decides on the top 16 bits; the rare ties draw
-    // their low 48 bits afterwards
-    if (Town == ~0ull) {
-      ion = alive & ~exc;
-    } else if (Town != 0ull) {
-      const uint32_t th = (uint32_t)(Town >> 48);
-      uint32_t tie = 0;
-      for (uint32_t bits = alive & ~exc; bits;) {
-        const uint32_t g = (uint32_t)(__ffs(bits) - 1) >> 3;
-        const uint32_t gm = 0xFFu << (8 * g);
-        uint32_t lt, eq;
-        ion_compare8(draw(D.seed, (uint32_t)step, c, g, kStreamIon), th, lt, eq);
-        ion |= bits & gm & (lt << (8 * g));
-        tie |= bits & gm & (eq << (8 * g));
-        bits &= ~gm;
-      }
-      for (; tie; tie &= tie - 1) {
-        const uint32_t s = __ffs(tie) - 1;
-        const uint4 b = draw(D.seed, (uint32_t)step, c, s, kStreamIonLow);
-        const unsigned long long lo48 = ((unsigned long long)(b.y & 0xFFFFu) << 32) | b.x;
-        if (lo48 < (Town & 0xFFFFFFFFFFFFull)) ion |= 1u << s;
-      }
+    // warp-aggregated reservation of pool slots (most warps ionise nothing)
+    if (__ballot_sync(0xffffffffu, ion != 0u) == 0u) continue;
+    const int npair = __popc(ion);
+    int incl = npair;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int sft = 1; sft < 32; sft <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, sft);
+      if (lane >= sft) incl += v;
     }
-    // the few neutrals that may have crossed a face: exact position,
-    // threshold of that cell
-    const R sig = X.lr[L].sig_v;
-    if constexpr (sizeof(R) == 4)
-      t1 = R((int)(step + 1)) * D.dt;
-    else
-      t1 = R((double)(step + 1) * D.dt_d);
-    for (uint32_t bits = exc; bits; bits &= bits - 1) {
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long basew = 0;
+    if (lane == 31 && total) basew = atomicAdd(D.nslots, 2ull * (unsigned long long)total);
+    basew = __shfl_sync(0xffffffffu, basew, 31);
+    if (!npair) continue;
+    unsigned long long slot = basew + 2ull * (unsigned long long)(incl - npair);
+    const LayerR<R> &Ly = X.lr[L];
+    const int ppc = Ly.ppc;
+    uint32_t done = 0;
+    for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
       const uint32_t s = __ffs(bits) - 1;
-      Neutral<R> nu;
-      const unsigned long long Tuse =
-          neutral_at(D, sig, i, j, k, c, s, t1, nu)
-              ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-              : 0ull;
-      if (Tuse == 0ull) continue;
-      const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 3, kStreamIon);
-      if (ionises(ion_h16(w, s), Tuse, D.seed, (uint32_t)step, c, s)) ion |= 1u << s;
-    }
-  }
-  // warp-aggregated reservation of pool slots (most warps ionise nothing)
-  if (__ballot_sync(0xffffffffu, ion != 0u) == 0u) return;
-  const int npair = __popc(ion);
-  int incl = npair;
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int sft = 1; sft < 32; sft <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, sft);
-    if (lane >= sft) incl += v;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  unsigned long long basew = 0;
-  if (lane == 31 && total) basew = atomicAdd(D.nslots, 2ull * (unsigned long long)total);
-  basew = __shfl_sync(0xffffffffu, basew, 31);
-  if (!npair) return;
-  unsigned long long slot = basew + 2ull * (unsigned long long)(incl - npair);
-  const LayerR<R> &Ly = X.lr[L];
-  const int ppc = Ly.ppc;
-  uint32_t done = 0;
-  for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
-    const uint32_t s = __ffs(bits) - 1;
-    if (slot + 1 >= D.cap) {
-      atomicOr(D.err, kErrPool);
-      break;
-    }
-    Neutral<R> nu;
-    neutral_at(D, Ly.sig_v, i, j, k, c, s, t1, nu);
-    const int ncell = (nu.cell[2] * D.ny + nu.cell[1]) * D.nx + nu.cell[0];
-    const unsigned long long gid = (unsigned long long)c * ppc + s;
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-      const unsigned long long q = slot + sp;
-      D.pid[q] = 2ull * gid + sp;
-      D.pcell[q] = ncell;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        D.po[d][q] = nu.off[d];
-        D.pu[d][q] = nu.u[d];
+      if (slot + 1 >= D.cap) {
+        atomicOr(D.err, kErrPool);
+        break;
       }
-      D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
+      Neutral<R> nu;
+      neutral_at(D, Ly.sig_v, i, j, k, c, s, t1, nu);
+      const int ncell = (nu.cell[2] * D.ny + nu.cell[1]) * D.nx + nu.cell[0];
+      const unsigned long long gid = (unsigned long long)c * ppc + s;
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        const unsigned long long q = slot + sp;
+        D.pid[q] = 2ull * gid + sp;
+        D.pcell[q] = ncell;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          D.po[d][q] = nu.off[d];
+          D.pu[d][q] = nu.u[d];
+        }
+        D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
+      }
+      done |= 1u << s;
     }
-    done |= 1u << s;
+    D.alive[m] = alive & ~done;
+    const double nd = (double)__popc(done);
+    const LayerK &LK = D.layers[L];
+    atomicAdd(D.acc + 1, nd * LK.wmac);
+    atomicAdd(D.acc + 2, nd * LK.wmac * LK.gapJ);
+    atomicAdd(D.acc + 3, nd);
   }
-  D.alive[m] = alive & ~done;
-  const double nd = (double)__popc(done);
-  const LayerK &LK = D.layers[L];
-  atomicAdd(D.acc + 1, nd * LK.wmac);
-  atomicAdd(D.acc + 2, nd * LK.wmac * LK.gapJ);
-  atomicAdd(D.acc + 3, nd);
 }
 
 template <class R>
