@@ -251,12 +251,18 @@ __device__ __forceinline__ void esirkepov(const Dev<R> &D, const R jpref[3], con
 // registers (four and three blocks) measured slower: the gather's loads in
 // flight per thread matter more than resident warps.
 template <class R> struct PushOcc { static constexpr int v = 2; };
+// blocks of consecutive slots a block of the push takes before it jumps a
+// grid ahead (1: plain grid stride)
+constexpr int kPushRun = 4;
 
-// Pushes the slots first + threadIdx.x + j stride below last (and below the
-// slots in use); returns how many live particles this thread pushed.
+// Pushes slots below last (and below the slots in use) in runs of `run`
+// consecutive blocks of threads: the thread's slots are first + threadIdx.x
+// + i blockDim.x + j stride (i < run); returns how many live particles this
+// thread pushed.
 template <class R>
 __device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long first,
-                                             unsigned long long last, unsigned long long stride) {
+                                             unsigned long long last, unsigned long long stride,
+                                             int run = 1) {
   const Dev<R> &D = X.d;
   const unsigned long long n = min(min(*D.nslots, D.cap), last);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
@@ -265,6 +271,10 @@ __device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long
   double pushed = 0.0;
   const uint32_t jstamp = D.jtouch[D.nz + 1] + 1u;  // the next field pass
   unsigned long long p = first + threadIdx.x;
+  int ip = 0;  // place of p in its run
+  const unsigned long long bd = blockDim.x, jump = stride - (unsigned long long)(run - 1) * bd;
+  unsigned long long pn = 0;
+  int ipn = 0;
   // each thread loads its next particle's state one iteration ahead, so that
   // round trip overlaps the current particle's gather and deposit
   int cell_n = -1;
@@ -279,13 +289,17 @@ __device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long
     }
     tag_n = D.ptag[p];
   }
-  for (; p < n; p += stride) {
+  for (; p < n; p = pn, ip = ipn) {
+    // the thread's next slot: one block of threads on in the run, or the
+    // start of the next run
+    ipn = ip + 1 < run ? ip + 1 : 0;
+    pn = ip + 1 < run ? p + bd : p + jump;
     const int cell = cell_n;
     R off[3] = {off_n[0], off_n[1], off_n[2]};
     R u[3] = {u_n[0], u_n[1], u_n[2]};
     const uint32_t tag = tag_n;
-    if (p + stride < n) {
-      const unsigned long long q = p + stride;
+    if (pn < n) {
+      const unsigned long long q = pn;
       cell_n = D.pcell[q];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -387,8 +401,11 @@ __device__ __forceinline__ double push_items(const Ctx<R> &X, unsigned long long
 
 template <class R>
 __global__ void __launch_bounds__(256, PushOcc<R>::v) k_push(Ctx<R> X) {
-  const double pushed = push_items(X, blockIdx.x * (unsigned long long)blockDim.x, ~0ull,
-                                   (unsigned long long)gridDim.x * blockDim.x);
+  // runs of kPushRun blocks of consecutive slots of the cell-sorted pool, a
+  // grid of runs apart: a block's particles stay in a compact region for a
+  // few iterations, so its gathers reuse field lines in L1
+  const unsigned long long run = (unsigned long long)kPushRun * blockDim.x;
+  const double pushed = push_items(X, blockIdx.x * run, ~0ull, gridDim.x * run, kPushRun);
   const double tot = block_sum<R>(pushed);
   if (threadIdx.x == 0 && tot != 0.0) atomicAdd(X.d.acc + 4, tot);
 }
