@@ -65,6 +65,7 @@ struct Dev {
   const int *layer_of_plane;      // nz, -1 vacuum
   const int *mplane;              // nz, -1 vacuum
   const int *kplane;              // n_mplanes: z plane of material plane
+  const int *vplane;              // the other node planes 0 .. nz (no material)
   const LayerK *layers;
   // amplitude window and Keldysh threshold, per material cell
   R *win;                         // NW x nmat

@@ -673,12 +673,21 @@ __device__ __forceinline__ R e_point(const LayerR<R> &L, R e0, R a, R &p, R &q) 
 // the polarisation current, Silver-Mueller faces at k = 0 (with the incident field) and k = nz,
 // Joule work J.(E^n + E^{n+1})/2, J cleared for the next deposit.  Three
 // blocks per SM (80 registers) measured faster than two at 100 registers.
-template <int V, bool kLay = false, class R>
+// kPlanes: 0 every node plane (k = bk.y); 1 the interior planes without
+// material (D.vplane[bk.y]); 2 the material planes (D.kplane[bk.y]); 3 the
+// two faces (bk.y 0: k = 0, 1: k = nz).  Each compiles only the code its
+// planes need (face boundary and laser source, polarisation).
+template <int V, bool kLay = false, int kPlanes = 0, class R>
 __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
   const Dev<R> &D = X.d;
   const int nx = D.nx, ny = D.ny, nz = D.nz, nxy = D.nxy;
   const int r = (bk.x * blockDim.x + threadIdx.x) * V;
-  const int k = bk.y;
+  constexpr bool kFaces = kPlanes == 0 || kPlanes == 3;
+  constexpr bool kMaterial = kPlanes == 0 || kPlanes == 2;
+  const int k = kPlanes == 0   ? bk.y
+                : kPlanes == 1 ? D.vplane[bk.y]
+                : kPlanes == 2 ? D.kplane[bk.y]
+                               : (bk.y == 0 ? 0 : D.nz);
   // the current is nonzero only on node planes within reach of a particle
   // deposited since the last field pass (cell planes k - 3 .. k + 2) or
   // after a host write
@@ -727,9 +736,9 @@ __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
           dBz_dx[l] = pml_step(D.psi[kPsiEYX] + o + l, D.pml_bE[0][i + l], dBz_dx[l]);
         }
     }
-    const int L = k < nz ? D.layer_of_plane[k] : -1;
+    const int L = (kMaterial && k < nz) ? D.layer_of_plane[k] : -1;
     const long long m = L >= 0 ? (long long)D.mplane[k] * nxy + r : -1;
-    if (k == 0 || k == nz) {
+    if (kFaces && (k == 0 || k == nz)) {
       const R al = D.alpha, cc = R(kC);
       const R inv = R(1) / (R(1) + al);
       if (k == 0) {
@@ -854,9 +863,9 @@ __device__ __forceinline__ void efull_body(const Ctx<R> &X, Blk bk) {
   if (threadIdx.x == 0 && tot != R(0)) atomicAdd(D.acc + 0, (double)tot * D.dt_d * D.V_d);
 }
 
-template <int V, class R, bool kLay = false>
-__global__ void __launch_bounds__(256, 3) k_efull(Ctx<R> X) {
-  efull_body<V, kLay>(X, blk_here());
+template <int V, class R, bool kLay = false, int kPlanes = 0>
+__global__ void __launch_bounds__(256, kPlanes == 1 ? 4 : 3) k_efull(Ctx<R> X) {
+  efull_body<V, kLay, kPlanes>(X, blk_here());
 }
 
 // ---------------------------------------------------------------------------
