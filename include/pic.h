@@ -389,13 +389,20 @@ int pic_batch_step(pic_batch b, int n_steps);
 int pic_batch_sync(pic_batch b);
 int pic_batch_destroy(pic_batch b);
 
-/* How a batch steps.  When every member has the same precision, the same
- * points per thread in the field kernels (FP32 with nx a multiple of 4, or
- * not) and the same pool-sort schedule, and none runs collisions, the graph
- * holds one launch per phase of a step for all members together (batch
- * launches: fixed grids laid end to end over the members, particle and
- * Keldysh loops in chunks handed out from a counter); otherwise it holds
- * every member's own launches, each on its stream.  With batch launches, a
+/* How a batch steps.  By default the graph holds every member's own
+ * launches, each on its stream (branches the device runs side by side).
+ * pic_batch_set_launches(b, 1) asks for batch launches instead: when every
+ * member has the same precision, the same points per thread in the field
+ * kernels (FP32 with nx a multiple of 4, or not) and the same pool-sort
+ * schedule, and none runs collisions, the graph then holds one launch per
+ * phase of a step for all members together (fixed grids laid end to end
+ * over the members, particle and Keldysh loops in chunks handed out from a
+ * counter), so that launches per step do not grow with the member count.
+ * Measured on one GB300, member branches were faster both for the 64-member
+ * fluence scan (4.25 s against 4.39 s) and for the serving trace (time to
+ * result p99 2.0 s against 2.9 s), so they stay the default.  The setting
+ * takes effect at the next capture; 0 returns to member branches.  With
+ * batch launches, a
  * pic_batch_step with at least 4 periods left tunes the push's launch shape
  * on the batch itself once the members hold particles (four per resident
  * push thread, or a 64th of their pools; checked before each period
@@ -411,6 +418,7 @@ int pic_batch_destroy(pic_batch b);
  *   n, pick        : candidates tuned (0: not yet) and the index kept (-1)
  *   batch_launches : 1 when the batch steps with batch launches
  * The paper has no counterpart (its runs are single jobs). */
+int pic_batch_set_launches(pic_batch b, int one_launch_per_phase);
 int pic_batch_tuning(pic_batch b, int cap, long long *chunk, int *grid_mult, double *ms,
                      double *ns_per_push, int *n, int *pick, int *batch_launches);
 

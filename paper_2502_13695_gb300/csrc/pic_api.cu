@@ -948,6 +948,7 @@ struct pic_batch_ctx {
   // batch launches (one per phase for all members): device tables, and the
   // parity of the members' pool halves relative to the tables' first copy
   bool multi = false;
+  bool one_launch = false;  // batch launches allowed (pic_batch_set_launches)
   char *tab = nullptr;
   size_t tab_bytes = 0;
   int parity = 0;
@@ -998,7 +999,7 @@ int join_batch_into_members(pic_batch_ctx *b) {
 // same points per thread in the field kernels and the same pool-sort
 // schedule, and no member runs collisions.
 bool batch_uniform(const pic_batch_ctx *b) {
-  if (b->m.size() > (size_t)kMaxBatch) return false;
+  if (!b->one_launch || b->m.size() > (size_t)kMaxBatch) return false;
   const pic_ctx *a = b->m[0];
   for (const pic_ctx *h : b->m)
     if (h->fp64 != a->fp64 || h->field_v != a->field_v ||
@@ -1416,6 +1417,20 @@ int pic_batch_create(pic_handle const *members, int n, void *stream, pic_batch *
   b->ev.resize(n + 1);
   for (auto &e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   *out = b;
+  return PIC_OK;
+}
+
+int pic_batch_set_launches(pic_batch b, int one_launch_per_phase) {
+  if (!b) return fail(PIC_EINVAL, "null batch");
+  const bool on = one_launch_per_phase != 0;
+  if (on != b->one_launch) {
+    PIC_CUDA(cudaStreamSynchronize(b->stream));  // a replay may still run
+    b->one_launch = on;
+    if (b->exec) {  // the next step captures in the requested form
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
   return PIC_OK;
 }
 

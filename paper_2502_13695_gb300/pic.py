@@ -30,7 +30,7 @@ EXPORTS = ["pic_query", "pic_create", "pic_step", "pic_step_phases", "pic_sync",
            "pic_set_particles", "pic_get_material", "pic_set_material",
            "pic_get_scalars", "pic_set_scalars", "pic_profile", "pic_profile_read",
            "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
-           "pic_batch_tuning",
+           "pic_batch_tuning", "pic_batch_set_launches",
            "pic_damage", "pic_get_intensity_max", "pic_save", "pic_load",
            "pic_checkpoint_config", "pic_serve_create", "pic_serve_submit",
            "pic_serve_poll", "pic_serve_destroy"]
@@ -152,6 +152,7 @@ def lib():
         L.pic_batch_sync.argtypes = [vp]
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_batch_tuning.argtypes = [vp, i, vp, vp, vp, vp, P(i), P(i), P(i)]
+        L.pic_batch_set_launches.argtypes = [vp, i]
         L.pic_profile_read.argtypes = [vp, vp, vp]
         L.pic_save.argtypes = [vp, ctypes.c_char_p]
         L.pic_load.argtypes = [ctypes.c_char_p, vp, vp, ctypes.c_size_t, P(vp)]
@@ -442,7 +443,7 @@ class Batch:
     """Simulations advanced together from one CUDA graph (see pic_batch_*).
     Every member must have been created on its own stream."""
 
-    def __init__(self, sims, stream=None):
+    def __init__(self, sims, stream=None, one_launch_per_phase=False):
         self.sims = list(sims)
         self.stream = stream  # None: the batch owns a private stream
         arr = (ctypes.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
@@ -450,6 +451,13 @@ class Batch:
         sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
         _check(lib().pic_batch_create(arr, len(self.sims), sp, ctypes.byref(h)))
         self._h = h
+        if one_launch_per_phase:
+            self.set_launches(True)
+
+    def set_launches(self, one_launch_per_phase: bool):
+        """Batch launches (one per phase for all members) or, by default,
+        every member's own launches (pic_batch_set_launches)."""
+        _check(lib().pic_batch_set_launches(self._h, int(bool(one_launch_per_phase))))
 
     def step(self, n: int):
         _check(lib().pic_batch_step(self._h, int(n)))

@@ -1,5 +1,7 @@
 """Batched stepping (one CUDA graph for several uneven simulations) against
-the oracle: every member matches its own FP64 oracle run step for step."""
+the oracle: every member matches its own FP64 oracle run step for step,
+with each member's own launches in the graph (the default) and with batch
+launches (one per phase for all members)."""
 import numpy as np
 import pytest
 
@@ -9,7 +11,8 @@ from parity_util import assert_particles_close, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def test_batch_of_uneven_instances_matches_oracle(oracle_mod):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batch_of_uneven_instances_matches_oracle(oracle_mod, one_launch):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.fail("GPU tests need a CUDA device")
@@ -21,9 +24,10 @@ def test_batch_of_uneven_instances_matches_oracle(oracle_mod):
             wl.small_slab(nx=8, ny=4, nz=24, z0=8, z1=16, precision="fp64", seed=13,
                           static=True)]
     sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
-    batch = pic.Batch(sims)
+    batch = pic.Batch(sims, one_launch_per_phase=one_launch)
     batch.step(70)  # two graph replays of the 32-step period and a 6-step tail
     batch.sync()
+    assert batch.tuning()["batch_launches"] == one_launch
     for c, g in zip(cfgs, sims):
         o = oracle_mod.Sim(c)
         o.step(70)
@@ -69,7 +73,7 @@ def test_fp32_batch_launches_match_members_alone():
             wl.small_slab(nx=4, ny=8, nz=24, z0=8, z1=16, precision="fp32", seed=63,
                           static=True)]
     sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
-    batch = pic.Batch(sims)
+    batch = pic.Batch(sims, one_launch_per_phase=True)
     l0 = sum(s.info()["launches"] for s in sims)
     batch.step(96)
     batch.sync()
@@ -106,7 +110,7 @@ def test_batch_tunes_its_push_shape_on_itself():
             wl.small_slab(nx=8, ny=12, nz=40, z0=12, z1=30, precision="fp64", seed=72,
                           fluence=2.0)]
     sims = [pic.Simulation(c, stream=torch.cuda.Stream()) for c in cfgs]
-    batch = pic.Batch(sims)
+    batch = pic.Batch(sims, one_launch_per_phase=True)
     assert batch.tuning()["candidates"] == []
     batch.step(8 * 32 + 10)
     batch.sync()
