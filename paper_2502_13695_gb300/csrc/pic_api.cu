@@ -65,7 +65,7 @@ struct Plan {
   int imax_every;  // steps between intensity records, 0 = off
   int ppc_max;
   size_t off_ne, off_ed, off_rho, off_spec, off_part;
-  size_t off_flux_part, off_flux_cnt;
+  size_t off_flux_part;
   size_t off_ktab;               // elliptic tables (elliptic_table > 0)
   size_t off_psi[12];            // absorbing-layer convolution terms (pml_cells > 0):
                                  // eight, then the B terms after a closing half step
@@ -265,7 +265,6 @@ int validate_and_plan(const pic_grid *grid, const pic_material *mat, const pic_p
           P.pmlb.push_back(d > 0.0 ? std::exp(-smax * r * r * r * h / kEps0) : 1.0);
         }
   }
-  P.off_flux_cnt = take(16);
   P.off_err = take(16);
   P.off_ne = take(P.nfield * 8);
   P.off_ed = take(P.nfield * 8);
@@ -516,7 +515,6 @@ void bind(pic_ctx *h) {
   D.flux_k[1] = P.flux_plane[1];
   D.flux_scale = kC * kEps0 * P.g.dx * P.g.dy * P.dt;
   D.flux_part = (double *)(A + P.off_flux_part);
-  D.flux_cnt = (unsigned int *)(A + P.off_flux_cnt);
   D.err = (int *)(A + P.off_err);
   D.seed = h->seed;
   X.lr = (const LayerR<R> *)(A + P.off_lr);
@@ -1729,10 +1727,15 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
   PIC_CUDA(cudaMemcpyAsync(pg5.data(), part, pg5.size() * 8, cudaMemcpyDeviceToHost, s));
   double acc[12];
   PIC_CUDA(cudaMemcpyAsync(acc, A + P.off_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+  // the Poynting split: every flux block's running sums, added in block order
+  std::vector<double> fpart((size_t)4 * P.flux_blocks);
+  PIC_CUDA(cudaMemcpyAsync(fpart.data(), A + P.off_flux_part, fpart.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
   if (dg->n_bins > 0)
     PIC_CUDA(cudaMemcpyAsync(dg->spectrum, spec, dg->n_bins * 8, cudaMemcpyDeviceToHost, s));
   PIC_CUDA(cudaStreamSynchronize(s));
-  h->d2h_bytes += (long long)((pp.size() + pg5.size() + 12 + std::max(dg->n_bins, 0)) * 8);
+  h->d2h_bytes +=
+      (long long)((pp.size() + pg5.size() + 12 + fpart.size() + std::max(dg->n_bins, 0)) * 8);
   double kin = 0, nel = 0, nho = 0;
   for (int b = 0; b < P.diag_blocks_p; ++b) {
     kin += pp[3 * b];
@@ -1778,15 +1781,21 @@ int pic_diagnostics(pic_handle h, pic_diag *dg) {
   dg->step = h->step;
   dg->flux_plane[0] = P.flux_plane[0];
   dg->flux_plane[1] = P.flux_plane[1];
-  dg->U_fwd[0] = acc[8];
-  dg->U_bwd[0] = acc[9];
-  dg->U_fwd[1] = acc[10];
-  dg->U_bwd[1] = acc[11];
+  double U[4] = {0.0, 0.0, 0.0, 0.0};  // fwd, bwd at the front plane, then the back
+  for (int q = 0; q < 2; ++q)
+    for (int x = 0; x < P.flux_blocks; ++x) {
+      U[2 * q] += fpart[2 * ((size_t)q * P.flux_blocks + x)];
+      U[2 * q + 1] += fpart[2 * ((size_t)q * P.flux_blocks + x) + 1];
+    }
+  dg->U_fwd[0] = U[0];
+  dg->U_bwd[0] = U[1];
+  dg->U_fwd[1] = U[2];
+  dg->U_bwd[1] = U[3];
   dg->frac_reflected = dg->frac_transmitted = dg->frac_absorbed_flux = 0.0;
-  if (acc[8] > 0.0) {
-    dg->frac_reflected = acc[9] / acc[8];
-    dg->frac_transmitted = acc[10] / acc[8];
-    dg->frac_absorbed_flux = ((acc[8] - acc[9]) - (acc[10] - acc[11])) / acc[8];
+  if (U[0] > 0.0) {
+    dg->frac_reflected = U[1] / U[0];
+    dg->frac_transmitted = U[2] / U[0];
+    dg->frac_absorbed_flux = ((U[0] - U[1]) - (U[2] - U[3])) / U[0];
   }
   return PIC_OK;
 }
@@ -2099,7 +2108,7 @@ int pic_set_scalars(pic_handle h, long long step, const double in[4]) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 3;
+constexpr uint32_t kCkptVersion = 4;
 constexpr size_t kStageBytes = size_t(64) << 20;
 
 struct CkptHeader {

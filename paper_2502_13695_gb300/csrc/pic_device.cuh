@@ -110,13 +110,13 @@ struct Dev {
                     // the opening half step's convolution from here
   const R *pml_bE[2], *pml_bB[2];
   double *acc;                    // [0] joule [1] N_pairs [2] U_ion [3] events
-                                  // [4] pushes [8..11] Poynting fwd/bwd front, back
-  // Poynting split: node planes (front, back), c eps0 dx dy dt, per-block
-  // partials (2 planes x blocks per plane x {fwd, bwd}) and the finished-block count
+                                  // [4] pushes
+  // Poynting split: node planes (front, back), c eps0 dx dy dt, and each
+  // block's running sums over the steps (2 planes x blocks per plane x
+  // {fwd, bwd}; the diagnostics add them up)
   int flux_k[2];
   double flux_scale;
   double *flux_part;
-  unsigned int *flux_cnt;
   int *err;
   unsigned long long seed;
 };

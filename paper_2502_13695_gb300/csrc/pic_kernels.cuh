@@ -1348,11 +1348,11 @@ __global__ void k_init_material(Ctx<R> X) {
 // Ey of the plane) is paired with B averaged over planes k - 1 and k (By and
 // Bx at k - 1/2 and k + 1/2, the same transverse positions) and split into
 // the waves going along +z, ((Ex + c By) / 2, (Ey - c Bx) / 2), and along -z,
-// ((Ex - c By) / 2, (Ey + c Bx) / 2).  Each block writes its FP64 sums of
-// |fwd|^2 and |bwd|^2; the last block to finish (counted with one atomic,
-// nothing waits) adds them up in a fixed order (one warp's loads and a
-// shuffle tree) times c eps0 dx dy dt to the time integrals, advances the
-// step and resets the count.
+// ((Ex - c By) / 2, (Ey + c Bx) / 2).  Each block adds its FP64 sums of
+// |fwd|^2 and |bwd|^2 over its points, times c eps0 dx dy dt, to its own
+// running pair: the time integrals are the sums of the blocks' pairs, which
+// the diagnostics form in block order (no reduction across blocks, no
+// atomic, no last block per step).  The first block advances the step.
 // Blocks per flux plane: one field point per thread (ceil(nxy / 256)), at
 // most kFluxMaxBlocks, so each thread makes one round trip to memory.
 constexpr int kFluxMaxBlocks = 256;
@@ -1374,37 +1374,14 @@ __device__ __forceinline__ void flux_advance_body(const Dev<R> &D, Blk bk) {
   const double fs = block_sum<R>(f);
   __syncthreads();
   const double bs = block_sum<R>(b);
-  __shared__ int last;
+  // each block adds its partial sums, times dt and the plane's area, to its
+  // own running pair (no reduction across blocks per step: the diagnostics
+  // sum the blocks' pairs in a fixed order)
   if (threadIdx.x == 0) {
     double *p = D.flux_part + 2 * (q * bk.gx + bk.x);
-    p[0] = fs;
-    p[1] = bs;
-    __threadfence();
-    last = atomicAdd(D.flux_cnt, 1u) == 2u * (unsigned)bk.gx - 1u;
-  }
-  __syncthreads();
-  if (last && threadIdx.x < 32) {
-    // the first warp loads the partials together (lane x sums blocks x,
-    // x + 32, ...) and adds them up in a fixed shuffle tree
-    __threadfence();
-    const int lane = threadIdx.x;
-    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int x = lane; x < bk.gx; x += 32)
-#pragma unroll
-      for (int qq = 0; qq < 2; ++qq) {
-        acc4[2 * qq] += __ldcg(D.flux_part + 2 * (qq * bk.gx + x));
-        acc4[2 * qq + 1] += __ldcg(D.flux_part + 2 * (qq * bk.gx + x) + 1);
-      }
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-      for (int sft = 16; sft > 0; sft >>= 1) acc4[v] += __shfl_xor_sync(0xffffffffu, acc4[v], sft);
-    if (lane == 0) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) D.acc[8 + v] += acc4[v] * D.flux_scale;
-      *D.flux_cnt = 0u;
-      *D.step += 1;
-    }
+    p[0] += fs * D.flux_scale;
+    p[1] += bs * D.flux_scale;
+    if (bk.x == 0 && q == 0) *D.step += 1;  // nothing in this launch reads it
   }
 }
 

@@ -95,7 +95,7 @@ class _CkptHeader(ctypes.Structure):
                 ("n_layers", ctypes.c_uint32)]
 
 
-def _header_file(tmp_path, pic, cfg, magic=b"PICCKPT1", version=3):
+def _header_file(tmp_path, pic, cfg, magic=b"PICCKPT1", version=4):
     g, m, p, keep = pic.c_structs(cfg)
 
     class Head(ctypes.Structure):
