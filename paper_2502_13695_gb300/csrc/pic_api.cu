@@ -374,6 +374,11 @@ struct pic_ctx {
   std::vector<LayerK> lk;
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
+  // side stream of a step: the window, Keldysh and ionisation passes run on
+  // it while the B step runs on `stream` (fork after the E step, join before
+  // the step end)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool own_arena = false;
   uint64_t seed = 0;
   long long step = 0;
@@ -633,6 +638,37 @@ int enqueue(pic_ctx *h, int mask) {
   Ctx<R> &X = ctx_of<R>(h);
   const Plan &P = h->P;
   cudaStream_t s = h->stream;
+  // A whole step (fields, window and ionisation) overlaps the B step with
+  // the material passes, which read E^{n+1} only; with profiling on, every
+  // class runs in order on the simulation's stream so that each is timed.
+  constexpr int kOverlapMask = PIC_PHASE_FIELDS | PIC_PHASE_WINDOW | PIC_PHASE_IONIZE;
+  const bool overlap = !h->profiling && P.nmat > 0 && (mask & kOverlapMask) == kOverlapMask;
+  // window and Keldysh threshold, then ionisation, on stream st
+  auto material_passes = [&](cudaStream_t st, bool window, bool ionize) -> int {
+    if (window && P.nmat > 0) {
+      prof_begin(h, PIC_PROF_WINDOW);
+      PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), st));
+      if constexpr (sizeof(R) == 4) {
+        if (h->field_v == 4)
+          k_window<4, R><<<dim3(grid_blocks(P.nxy / 4), P.n_mplanes), kThreads, 0, st>>>(X);
+      }
+      if (h->field_v == 1)
+        k_window<1, R><<<dim3(grid_blocks(P.nxy), P.n_mplanes), kThreads, 0, st>>>(X);
+      prof_end(h);
+      prof_begin(h, PIC_PROF_KELDYSH);
+      k_keldysh<R><<<kPersistentBlocks, kThreads, 0, st>>>(X);
+      prof_end(h);
+      h->launches += 2;
+    }
+    if (ionize && P.nmat > 0) {
+      prof_begin(h, PIC_PROF_IONIZE);
+      k_ionize<R><<<dim3(grid_blocks((P.nxy + kIonizeCells - 1) / kIonizeCells), P.n_mplanes),
+                    kThreads, 0, st>>>(X);
+      prof_end(h);
+      h->launches += 1;
+    }
+    return PIC_OK;
+  };
   if (mask & PIC_PHASE_PARTICLES) {
     prof_begin(h, PIC_PROF_PUSH);
     k_push<R><<<h->push_blocks, kThreads, 0, s>>>(X);
@@ -698,44 +734,39 @@ int enqueue(pic_ctx *h, int mask) {
         if (nm) k_efull<V, R, kLay, 2><<<dim3(gx, nm), kThreads, 0, s>>>(X);
       };
       if constexpr (sizeof(R) == 4) {
-        if (h->field_v == 4) {
-          estep(std::integral_constant<int, 4>{});
+        if (h->field_v == 4) estep(std::integral_constant<int, 4>{});
+      }
+      if (h->field_v == 1) estep(std::integral_constant<int, 1>{});
+    });
+    if (overlap) {
+      // fork: the window, Keldysh and ionisation passes need E^{n+1} only
+      PIC_CUDA(cudaEventRecord(h->ev_fork, s));
+      PIC_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+      const int rw = material_passes(h->aux, true, true);
+      if (rw) return rw;
+      PIC_CUDA(cudaEventRecord(h->ev_join, h->aux));
+    }
+    with_layers(P.g.pml_cells > 0, [&](auto lay) {
+      constexpr bool kLay = decltype(lay)::value;
+      if constexpr (sizeof(R) == 4) {
+        if (h->field_v == 4)
           k_bstep<4, kFullRecord, R, kLay>
               <<<dim3(grid_blocks(P.nxy / 4), P.g.nz + 1), kThreads, 0, s>>>(X.d);
-        }
       }
-      if (h->field_v == 1) {
-        estep(std::integral_constant<int, 1>{});
+      if (h->field_v == 1)
         k_bstep<1, kFullRecord, R, kLay><<<dim3(grid_blocks(P.nxy), P.g.nz + 1), kThreads, 0, s>>>(
             X.d);
-      }
     });
+    if (overlap) PIC_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));  // join
     prof_end(h);
     // E step (one launch, or faces + vacuum + material) and the B step
     h->launches += h->efull_split ? 2 + (P.vplane.empty() ? 0 : 1) + (P.n_mplanes ? 1 : 0) : 2;
     h->bh_valid = true;
   }
-  if ((mask & PIC_PHASE_WINDOW) && P.nmat > 0) {
-    prof_begin(h, PIC_PROF_WINDOW);
-    PIC_CUDA(cudaMemsetAsync(X.work_n, 0, sizeof(int), s));
-    if constexpr (sizeof(R) == 4) {
-      if (h->field_v == 4)
-        k_window<4, R><<<dim3(grid_blocks(P.nxy / 4), P.n_mplanes), kThreads, 0, s>>>(X);
-    }
-    if (h->field_v == 1)
-      k_window<1, R><<<dim3(grid_blocks(P.nxy), P.n_mplanes), kThreads, 0, s>>>(X);
-    prof_end(h);
-    prof_begin(h, PIC_PROF_KELDYSH);
-    k_keldysh<R><<<kPersistentBlocks, kThreads, 0, s>>>(X);
-    prof_end(h);
-    h->launches += 2;
-  }
-  if (P.nmat > 0 && (mask & PIC_PHASE_IONIZE)) {
-    prof_begin(h, PIC_PROF_IONIZE);
-    k_ionize<R><<<dim3(grid_blocks((P.nxy + kIonizeCells - 1) / kIonizeCells), P.n_mplanes),
-                  kThreads, 0, s>>>(X);
-    prof_end(h);
-    h->launches += 1;
+  if (!overlap) {
+    const int rw = material_passes(s, (mask & PIC_PHASE_WINDOW) != 0,
+                                   (mask & PIC_PHASE_IONIZE) != 0);
+    if (rw) return rw;
   }
   if (mask & PIC_PHASE_ADVANCE) {
     prof_begin(h, PIC_PROF_OTHER);
@@ -768,6 +799,15 @@ int init_state(pic_ctx *h) {
   h->push_blocks = std::max(1, nsm) * std::max(1, per_sm);
   PIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coll_prep<R>, 32 * kCollWarps, 0));
   h->coll_blocks = std::max(1, nsm) * std::max(1, per_sm);
+  if (!h->aux) {
+    // the side stream at the highest priority: its passes are the longer
+    // branch of a step, the B step fills the SMs they leave
+    int lo = 0, hi = 0;
+    PIC_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    PIC_CUDA(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi));
+    PIC_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    PIC_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_lop, P.lop.data(), P.lop.size() * sizeof(int),
                            cudaMemcpyHostToDevice, s));
   PIC_CUDA(cudaMemcpyAsync(h->arena + P.off_mplane, P.mplane.data(), P.mplane.size() * sizeof(int),
@@ -1538,6 +1578,12 @@ int pic_profile_read(pic_handle h, double ms[PIC_PROF_N], long long launches[PIC
 int pic_destroy(pic_handle h) {
   if (!h) return PIC_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamDestroy(h->aux);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto &r : h->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
