@@ -337,7 +337,10 @@ LIMITER = {
 def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup):
     """Time `steps` full steps of cfg after `prerun + warmup` untimed ones
     (CUDA events on the simulation's stream, clocks sampled meanwhile), then
-    one whole job of cfg["steps"] steps through the public API (e2e).
+    up to 200 more steps with every kernel class timed by events (the
+    classes then run in order, without the overlap of a plain step, and the
+    events add their own cost: a breakdown, not the step time), then one
+    whole job of cfg["steps"] steps through the public API (e2e).
     Returns the fields of a bench line for this workload."""
     import torch
     from paper_2502_13695_gb300 import pic
@@ -348,7 +351,6 @@ def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup)
     sim.sync()
     stream = sim.stream
     i0, s0 = sim.info(), sim.scalars()
-    sim.profile(True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -365,10 +367,17 @@ def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup)
         torch.cuda.synchronize()
         nvtx_pop()
     ms = ev0.elapsed_time(ev1)
-    prof = sim.profile_read()
-    sim.profile(False)
     sim.sync()
     i1, s1 = sim.info(), sim.scalars()
+    # the per-class breakdown, from its own profiled steps
+    prof_steps = min(steps, 200)
+    sim.profile(True)
+    sim.step(prof_steps)
+    sim.sync()
+    prof = sim.profile_read()
+    sim.profile(False)
+    i2 = sim.info()
+    psteps_prof = i2["particle_steps"] - i1["particle_steps"]
     psteps = i1["particle_steps"] - i0["particle_steps"]
     events = s1["n_events"] - s0["n_events"]
     launches = i1["launches"] - i0["launches"]
@@ -392,7 +401,7 @@ def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup)
         limiter = "FP64 issue (series of Dawson terms)"
     unit_name, per_unit = table.get(dom, ("step", 0.0))
     if dom == "push":
-        units = psteps / max(dom_n, 1)
+        units = psteps_prof / max(dom_n, 1)
     elif dom in ("sort", "collide"):
         units = (i1["n_particles"] + i0["n_particles"]) / 2
     elif unit_name == "field point":
@@ -427,7 +436,9 @@ def measure_workload(cfg, args, rank, local, world, dist, prerun, steps, warmup)
         "timed_steps": [prerun + warmup, prerun + warmup + steps],
         "charged_particles": [i0["n_particles"], i1["n_particles"]],
         "ionisation_events": events,
-        "per_kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+        # from the profiled steps after the timed ones (classes in order)
+        "per_kernel_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
+        "per_kernel_steps": [prerun + warmup + steps, prerun + warmup + steps + prof_steps],
         # a class with no algorithmic bytes (Keldysh) is bound by arithmetic:
         # no HBM fraction is claimed for it
         "roofline": {"kernel": dom, "bound": "hbm" if per_unit else "alu", "limiter": limiter,
