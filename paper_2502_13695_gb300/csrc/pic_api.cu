@@ -379,6 +379,9 @@ struct pic_ctx {
   // the step end)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // set while a batch captures this member's steps: the batch's graph runs
+  // its members side by side already, and keeps one branch per member
+  bool in_batch = false;
   bool own_arena = false;
   uint64_t seed = 0;
   long long step = 0;
@@ -642,7 +645,8 @@ int enqueue(pic_ctx *h, int mask) {
   // the material passes, which read E^{n+1} only; with profiling on, every
   // class runs in order on the simulation's stream so that each is timed.
   constexpr int kOverlapMask = PIC_PHASE_FIELDS | PIC_PHASE_WINDOW | PIC_PHASE_IONIZE;
-  const bool overlap = !h->profiling && P.nmat > 0 && (mask & kOverlapMask) == kOverlapMask;
+  const bool overlap =
+      !h->profiling && !h->in_batch && P.nmat > 0 && (mask & kOverlapMask) == kOverlapMask;
   // window and Keldysh threshold, then ionisation, on stream st
   auto material_passes = [&](cudaStream_t st, bool window, bool ionize) -> int {
     if (window && P.nmat > 0) {
@@ -1254,8 +1258,10 @@ int batch_capture(pic_batch_ctx *b) {
     e = cudaEventRecord(b->ev[0], s);
     for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q)
       e = cudaStreamWaitEvent(b->m[q]->stream, b->ev[0], 0);
+    for (pic_ctx *h : b->m) h->in_batch = true;
     for (int st = 0; st < b->period && rc == PIC_OK && e == cudaSuccess; ++st)
       for (size_t q = 0; q < b->m.size() && rc == PIC_OK; ++q) rc = enqueue_any(b->m[q], PIC_PHASE_ALL);
+    for (pic_ctx *h : b->m) h->in_batch = false;
     for (size_t q = 0; q < b->m.size() && e == cudaSuccess; ++q) {
       e = cudaEventRecord(b->ev[1 + q], b->m[q]->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev[1 + q], 0);
