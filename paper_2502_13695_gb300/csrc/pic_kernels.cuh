@@ -1110,12 +1110,16 @@ __device__ __forceinline__ bool ionises(uint32_t h16, unsigned long long T, unsi
 // when its low 48 bits must decide.
 __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32_t &lt,
                                              uint32_t &eq) {
+  lt = 0;
+  eq = 0;
+  // nearly every block has all eight halves above th: their minimum says so
+  // in a few instructions, before any per-slot comparison
+  const uint32_t m2 = __vminu2(__vminu2(w.x, w.y), __vminu2(w.z, w.w));
+  if (min(m2 & 0xFFFFu, m2 >> 16) > th) return;
   // two halves per instruction: __vcmpltu2 / __vcmpeq2 set a halfword to
   // 0xFFFF where the unsigned comparison holds
   const uint32_t v[4] = {w.x, w.y, w.z, w.w};
   const uint32_t th2 = th | (th << 16);
-  lt = 0;
-  eq = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t l = __vcmpltu2(v[q], th2), e = __vcmpeq2(v[q], th2);
@@ -1124,13 +1128,96 @@ __device__ __forceinline__ void ion_compare8(const uint4 &w, uint32_t th, uint32
   }
 }
 
+// Decisions for the neutrals of cell (i, j, k) in the bits of exc, which
+// may have crossed a face: exact position at t^{n+1}, threshold of the cell
+// it is in.
+template <class R>
+__device__ __forceinline__ uint32_t ion_exc(const Dev<R> &D, R sig, int i, int j, int k,
+                                            uint32_t c, uint32_t exc, uint32_t step, R t1) {
+  uint32_t ion = 0;
+  for (uint32_t bits = exc; bits; bits &= bits - 1) {
+    const uint32_t s = __ffs(bits) - 1;
+    Neutral<R> nu;
+    const unsigned long long Tuse = neutral_at(D, sig, i, j, k, c, s, t1, nu)
+                                        ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
+                                        : 0ull;
+    if (Tuse == 0ull) continue;
+    const uint4 w = draw(D.seed, step, c, s >> 3, kStreamIon);
+    if (ionises(ion_h16(w, s), Tuse, D.seed, step, c, s)) ion |= 1u << s;
+  }
+  return ion;
+}
+
+// Electron + hole for each neutral in the bits of ion of cell r of the
+// plane (material index m, alive word alive): pool slots reserved once per
+// warp (every lane of the warp calls this; most warps ionise nothing).
+template <class R>
+__device__ __forceinline__ void ion_append(const Ctx<R> &X, long long m, int r, int k, int L,
+                                           uint32_t c, uint32_t alive, uint32_t ion, R t1) {
+  const Dev<R> &D = X.d;
+  if (__ballot_sync(0xffffffffu, ion != 0u) == 0u) return;
+  const int npair = __popc(ion);
+  int incl = npair;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, sft);
+    if (lane >= sft) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long basew = 0;
+  if (lane == 31 && total) basew = atomicAdd(D.nslots, 2ull * (unsigned long long)total);
+  basew = __shfl_sync(0xffffffffu, basew, 31);
+  if (!npair) return;
+  const int j = r / D.nx, i = r - j * D.nx;
+  unsigned long long slot = basew + 2ull * (unsigned long long)(incl - npair);
+  const LayerR<R> &Ly = X.lr[L];
+  const int ppc = Ly.ppc;
+  uint32_t done = 0;
+  for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
+    const uint32_t s = __ffs(bits) - 1;
+    if (slot + 1 >= D.cap) {
+      atomicOr(D.err, kErrPool);
+      break;
+    }
+    Neutral<R> nu;
+    neutral_at(D, Ly.sig_v, i, j, k, c, s, t1, nu);
+    const int ncell = (nu.cell[2] * D.ny + nu.cell[1]) * D.nx + nu.cell[0];
+    const unsigned long long gid = (unsigned long long)c * ppc + s;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      const unsigned long long q = slot + sp;
+      D.pid[q] = 2ull * gid + sp;
+      D.pcell[q] = ncell;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        D.po[d][q] = nu.off[d];
+        D.pu[d][q] = nu.u[d];
+      }
+      D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
+    }
+    done |= 1u << s;
+  }
+  D.alive[m] = alive & ~done;
+  const double nd = (double)__popc(done);
+  const LayerK &LK = D.layers[L];
+  atomicAdd(D.acc + 1, nd * LK.wmac);
+  atomicAdd(D.acc + 2, nd * LK.wmac * LK.gapJ);
+  atomicAdd(D.acc + 3, nd);
+}
+
 // Each thread takes kIonizeCells material cells of a plane, a grid row of
 // threads apart, and loads the next cell's three words while it draws for
 // the current one.  (A thread per slot pair measured twice as
 // slow as a thread per cell: four threads repeat the cell's index and
 // threshold loads.)  FP32: six blocks per SM (40 registers): the kernel
 // waits on its loads, and 64 registers (four blocks) measured 22% slower.
+// The cells with neutrals that may have crossed a face (under 1% of them)
+// are queued in shared memory and decided after the block's other cells,
+// one per thread, so that a warp no longer runs that long path for one lane
+// while the other 31 wait; a full queue sends the rest down the path at once.
 constexpr int kIonizeCells = 4;
+constexpr int kExcQueue = 256;
 
 template <class R>
 __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
@@ -1145,11 +1232,17 @@ __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
         (mp + 1 == bk.gy || D.hot[mp + 1] != stamp))
       return;
   }
+  __shared__ int xq_r[kExcQueue];
+  __shared__ uint32_t xq_bits[kExcQueue];
+  __shared__ int xq_n;
+  if (threadIdx.x == 0) xq_n = 0;
+  __syncthreads();
   const int nx = D.nx, nxy = D.nxy;
   const long long step = *D.step;
   const int k = D.kplane[mp], L = D.layer_of_plane[k];
   const long long mbase = (long long)mp * nxy;
   const int stride = bk.gx * blockDim.x;
+  const R sig = X.lr[L].sig_v;
   R t1;
   if constexpr (sizeof(R) == 4)
     t1 = R((int)(step + 1)) * D.dt;
@@ -1177,10 +1270,7 @@ __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
       leave_n = D.leave_step[m + stride];
     }
     uint32_t ion = 0, c = 0;
-    int i = 0, j = 0;
     if (alive) {
-      j = r / nx;
-      i = r - j * nx;
       c = (uint32_t)((long long)k * nxy + r);
       // neutrals that may have left the birth cell by t^{n+1}: their own
       // leave step (64-step units, rounded down) has been reached
@@ -1216,70 +1306,34 @@ __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
           if (lo48 < (Town & 0xFFFFFFFFFFFFull)) ion |= 1u << s;
         }
       }
-      // the few neutrals that may have crossed a face: exact position,
-      // threshold of that cell
-      const R sig = X.lr[L].sig_v;
-      for (uint32_t bits = exc; bits; bits &= bits - 1) {
-        const uint32_t s = __ffs(bits) - 1;
-        Neutral<R> nu;
-        const unsigned long long Tuse =
-            neutral_at(D, sig, i, j, k, c, s, t1, nu)
-                ? threshold_at(D, nu.cell[0], nu.cell[1], nu.cell[2])
-                : 0ull;
-        if (Tuse == 0ull) continue;
-        const uint4 w = draw(D.seed, (uint32_t)step, c, s >> 3, kStreamIon);
-        if (ionises(ion_h16(w, s), Tuse, D.seed, (uint32_t)step, c, s)) ion |= 1u << s;
-      }
-    }
-    // warp-aggregated reservation of pool slots (most warps ionise nothing)
-    if (__ballot_sync(0xffffffffu, ion != 0u) == 0u) continue;
-    const int npair = __popc(ion);
-    int incl = npair;
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int sft = 1; sft < 32; sft <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, sft);
-      if (lane >= sft) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long basew = 0;
-    if (lane == 31 && total) basew = atomicAdd(D.nslots, 2ull * (unsigned long long)total);
-    basew = __shfl_sync(0xffffffffu, basew, 31);
-    if (!npair) continue;
-    unsigned long long slot = basew + 2ull * (unsigned long long)(incl - npair);
-    const LayerR<R> &Ly = X.lr[L];
-    const int ppc = Ly.ppc;
-    uint32_t done = 0;
-    for (uint32_t bits = ion; bits; bits &= bits - 1, slot += 2) {
-      const uint32_t s = __ffs(bits) - 1;
-      if (slot + 1 >= D.cap) {
-        atomicOr(D.err, kErrPool);
-        break;
-      }
-      Neutral<R> nu;
-      neutral_at(D, Ly.sig_v, i, j, k, c, s, t1, nu);
-      const int ncell = (nu.cell[2] * D.ny + nu.cell[1]) * D.nx + nu.cell[0];
-      const unsigned long long gid = (unsigned long long)c * ppc + s;
-#pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        const unsigned long long q = slot + sp;
-        D.pid[q] = 2ull * gid + sp;
-        D.pcell[q] = ncell;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          D.po[d][q] = nu.off[d];
-          D.pu[d][q] = nu.u[d];
+      if (exc) {
+        const int q = atomicAdd(&xq_n, 1);
+        if (q < kExcQueue) {
+          xq_r[q] = r;
+          xq_bits[q] = exc;
+        } else {
+          const int j = r / nx, i = r - j * nx;
+          ion |= ion_exc(D, sig, i, j, k, c, exc, (uint32_t)step, t1);
         }
-        D.ptag[q] = ((uint32_t)L << 1) | (uint32_t)sp;
       }
-      done |= 1u << s;
     }
-    D.alive[m] = alive & ~done;
-    const double nd = (double)__popc(done);
-    const LayerK &LK = D.layers[L];
-    atomicAdd(D.acc + 1, nd * LK.wmac);
-    atomicAdd(D.acc + 2, nd * LK.wmac * LK.gapJ);
-    atomicAdd(D.acc + 3, nd);
+    ion_append(X, m, r, k, L, c, alive, ion, t1);
+  }
+  // the queued cells: their alive words as this block's appends left them
+  __syncthreads();
+  const int nq = min(xq_n, kExcQueue);
+  for (int q0 = 0; q0 < nq; q0 += blockDim.x) {
+    const int q = q0 + threadIdx.x;
+    uint32_t ion = 0, c = 0, alive = 0;
+    int r = 0;
+    if (q < nq) {
+      r = xq_r[q];
+      alive = D.alive[mbase + r];
+      c = (uint32_t)((long long)k * nxy + r);
+      const int j = r / nx, i = r - j * nx;
+      ion = ion_exc(D, sig, i, j, k, c, xq_bits[q] & alive, (uint32_t)step, t1);
+    }
+    ion_append(X, mbase + r, r, k, L, c, alive, ion, t1);
   }
 }
 
