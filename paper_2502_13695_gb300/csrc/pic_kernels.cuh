@@ -1268,6 +1268,11 @@ __device__ __forceinline__ void ionize_body(const Ctx<R> &X, Blk bk) {
       alive_n = D.alive[m + stride];
       T_n = D.T[m + stride];
       leave_n = D.leave_step[m + stride];
+    } else {
+      // past the plane's last cell (a ragged last row of threads): nothing
+      alive_n = 0;
+      T_n = 0;
+      leave_n = 0;
     }
     uint32_t ion = 0, c = 0;
     if (alive) {

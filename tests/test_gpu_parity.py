@@ -180,13 +180,18 @@ def test_fp32_single_steps_from_oracle_states(pic, oracle_mod, nx):
     assert flips_total <= 3 + 1e-4 * draws_total
 
 
+@pytest.mark.parametrize("n", [8, 24])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_hot_neutrals_crossing_faces(pic, oracle_mod, precision):
+def test_hot_neutrals_crossing_faces(pic, oracle_mod, precision, n):
     """Neutrals at ~0.01 c thermal speed move about a third of a cell in 60
     steps, so most are drawn against a neighbour cell's threshold (or leave
     the grid): the per-neutral crossing steps must switch every one of them
-    to its exact position in time."""
-    cfg = wl.small_slab(temp_eV=5e6, fluence=3.0, precision="fp64", seed=21)
+    to its exact position in time.  The ionisation pass decides such cells
+    after the rest of its block, from a queue of 256 cells: an 8 x 8 plane
+    (64 cells) fits it; a 24 x 24 plane (576 cells, one block, about 490 of
+    them with such a neutral at two per cell) overflows it, and the cells
+    past the queue are decided in the block's main loop."""
+    cfg = wl.small_slab(nx=n, ny=n, temp_eV=5e6, fluence=3.0, precision="fp64", seed=21)
     o = oracle_mod.Sim(cfg)
     g = pic.Simulation(dict(cfg, precision=precision))
     o.step(60)
